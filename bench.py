@@ -1,0 +1,486 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched RAMBO query path (arXiv 1910.02611) on one or more
+GB300s.
+
+A step is one batch of the genome-like workload: 10^5 DNA query sequences of
+U[100,1000] bases (substrings of 2000 synthetic genomes with 0-2% base
+substitutions) answered against a resident index of 2000 genomes x ~10^6
+31-mers (B=64, R=6, m=2^27, eta=2): 2-bit packing, k-mer hashing, row probes,
+AND across tables' cells and across the sequence's k-mers, set-level
+intersection and compaction of the set-ID lists, all in the library's kernels.
+The index is built once per run with the construction kernel (timed and
+reported beside the query numbers).
+
+  value   k-mers (query keys submitted) per second, inputs already in device
+          memory, summed over ranks, time = max over ranks of the CUDA-event
+          time of the K timed steps (L2 flushed before every step);
+  e2e     the same metric through the same C-ABI call with host (pinned)
+          inputs and outputs: host-to-device copy of the batch, the kernels,
+          device-to-host copy of the results, all inside the timed region.
+
+--impl reference times the CPU oracle (plain C, Algorithms 1 and 2 of the
+paper on B*R separate Bloom filters) on a bounded sample of the same
+workload on the host cores.  Multi-GPU: every rank holds a replica of the
+index and answers its own batches (no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "k-mer queries/s and achieved HBM GB/s vs roofline; p50/p99 query latency"
+UNIT = "k-mers/s"
+SECTOR = 32
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="genome", choices=["genome", "uneven", "document", "tiny"])
+    ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = the full configuration)")
+    ap.add_argument("--batches", type=int, default=6, help="distinct query batches rotated over the steps")
+    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--json-out", default=None)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_workload(config: str, scale: float):
+    return synth.make(config, scale)
+
+
+def extra_batches(w, n_batches: int, rank: int):
+    """Distinct query batches of the workload's shape (the first is the
+    workload's own when rank == 0)."""
+    out = [w.queries] if rank == 0 else []
+    b = 0
+    while len(out) < n_batches:
+        rng = np.random.default_rng(10_000 + 97 * rank + b)
+        b += 1
+        n = len(w.queries)
+        if w.name == "genome":
+            lengths = rng.integers(100, 1001, n)
+            out.append(synth.substring_queries(rng, w.sets, lengths))
+        elif w.name == "uneven":
+            lengths = np.clip(np.round(rng.lognormal(np.log(300), 1.0, n)), 31, 10_000).astype(np.int64)
+            out.append(synth.substring_queries(rng, w.sets, lengths))
+        else:
+            idx = rng.permutation(n)
+            out.append(w.queries.subset(idx))
+    return out
+
+
+def keys_in(q, k: int) -> int:
+    if q.kind == "keys":
+        return int(q.offsets[-1] - q.offsets[0])
+    return int(q.offsets[-1] - q.offsets[0]) - len(q) * (k - 1)
+
+
+# ---------------------------------------------------------------------------
+# measurement helpers
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max((num(r[3]) or 0) for r in rows)}
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("k_query.cuh", "k_query_inst.cuh", "rambo_impl.cuh"):
+        with open(os.path.join(ROOT, "paper_1910_02611_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(config: str):
+    """Per-launch DRAM bytes of the query kernel from the committed ncu summary,
+    valid only while the kernel source is the one that was profiled."""
+    p = os.path.join(ROOT, "profiles", f"query_kernel_{config}_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    with open(p) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_index(w, nthreads: int):
+    from oracle.oracle import Oracle
+
+    o = Oracle(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    t0 = time.perf_counter()
+    if w.sets.kind == "keys":
+        o.insert_keys_batch(w.sets.ids, w.sets.data, w.sets.offsets, nthreads=nthreads)
+    else:
+        o.insert_seq_batch(w.sets.ids, w.sets.data, w.sets.offsets, w.k, nthreads=nthreads)
+    return o, time.perf_counter() - t0
+
+
+def oracle_rate(o, q, k: int, nthreads: int, target_s: float):
+    """keys/s of the oracle on a prefix of batch q sized to ~target_s seconds."""
+    n = min(len(q), 64)
+    while True:
+        sub = q.subset(np.arange(n))
+        t0 = time.perf_counter()
+        o.query_batch_counts(sub.kind, sub.data, sub.offsets, k=k, nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or n >= len(q):
+            return keys_in(sub, k) / dt, n, dt
+        n = min(len(q), max(n * 2, int(n * target_s / max(dt, 1e-3) * 1.05)))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    nthreads = os.cpu_count() or 1
+    w = make_workload(args.config, args.scale)
+    o, build_s = oracle_index(w, nthreads)
+    q = w.queries
+    # size one step to a bounded sample so the whole run stays within minutes
+    rate, n, dt = oracle_rate(o, q, w.k, nthreads, target_s=min(5.0, args.cpu_seconds))
+    per_step_n = max(1, int(n * 2.0 / max(dt, 1e-3)))  # about 2 s of oracle work per step
+    per_step_n = min(per_step_n, len(q))
+    times, keys = [], 0
+    for s in range(args.warmup + args.steps):
+        idx = (np.arange(per_step_n) + s * per_step_n) % len(q)
+        sub = q.subset(idx)
+        t0 = time.perf_counter()
+        o.query_batch_counts(sub.kind, sub.data, sub.offsets, k=w.k, nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            keys += keys_in(sub, w.k)
+    total = sum(times)
+    value = keys / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"{w.name}: K={w.K} B={w.B} R={w.R} m=2^{int(np.log2(w.m))} eta={w.eta}, "
+                               f"{len(q)} query sequences (scale {args.scale})",
+                   "step": f"{per_step_n} queries of the workload per step (bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                         "sample": f"{per_step_n} queries per step x {args.steps} steps; oracle index built in "
+                                   f"{build_s:.1f} s"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    from paper_1910_02611_gb300 import Rambo
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    t_gen = time.perf_counter()
+    w = make_workload(args.config, args.scale)
+    batches = extra_batches(w, args.batches, rank)
+    t_gen = time.perf_counter() - t_gen
+
+    # ---- construction (Algorithm 1) ----
+    g = Rambo(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    sets = w.sets
+    d_ids = torch.from_numpy(sets.ids.view(np.int64)).to(dev)
+    d_data = torch.from_numpy(sets.data.view(np.int64) if sets.kind == "keys" else sets.data).to(dev)
+    d_off = torch.from_numpy(sets.offsets.view(np.int64)).to(dev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.insert(d_ids, d_data, d_off, kind=sets.kind, k=w.k)
+    e1.record(stream)
+    e1.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    build_keys = keys_in(sets, w.k)
+    del d_ids, d_data, d_off
+    torch.cuda.empty_cache()
+
+    # ---- query batches resident in device memory ----
+    dev_batches = []
+    for q in batches:
+        qd = torch.from_numpy(q.data.view(np.int64) if q.kind == "keys" else q.data).to(dev)
+        qo = torch.from_numpy(q.offsets.view(np.int64)).to(dev)
+        dev_batches.append((qd, qo, keys_in(q, w.k), len(q)))
+    out_cap = 1 << 24
+    out_ids = torch.empty(out_cap, dtype=torch.int32, device=dev)
+    out_off = torch.empty(max(len(q) for q in batches) + 1, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def one_step(i):
+        qd, qo, nk, nq = dev_batches[i % len(dev_batches)]
+        g.query_into(qd, qo, out_ids, out_off[: nq + 1], kind=batches[0].kind, k=w.k)
+        return nk
+
+    for i in range(args.warmup):
+        flush.zero_()
+        one_step(i)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, keys, probed, qk_ms, launches, n_ids = [], 0, 0, [], 0, 0
+    for i in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        nk = one_step(i)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = g.last_query_stats()
+        keys += nk
+        probed += st["keys_probed"]
+        qk_ms.append(st["query_kernel_ms"])
+        launches += st["kernel_launches"]
+        n_ids += st["n_results"]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    total_ms = sum(step_ms)
+
+    # ---- end to end through the same call with host buffers ----
+    host_batches = []
+    for q in batches:
+        hd = torch.from_numpy(q.data.view(np.int64) if q.kind == "keys" else q.data).pin_memory().numpy()
+        ho = torch.from_numpy(q.offsets.view(np.int64)).pin_memory().numpy().view(np.uint64)
+        host_batches.append((hd.view(np.uint64) if q.kind == "keys" else hd, ho, keys_in(q, w.k), len(q)))
+    e2e_s, e2e_keys, h2d, d2h = 0.0, 0, 0, 0
+    n_e2e = max(1, min(args.e2e_steps, args.steps))
+    for i in range(n_e2e):
+        hd, ho, nk, nq = host_batches[i % len(host_batches)]
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids, offs = g.query(hd, ho, kind=batches[0].kind, k=w.k)
+        e2e_s += time.perf_counter() - t0
+        e2e_keys += nk
+        h2d += hd.nbytes + ho.nbytes
+        d2h += offs.nbytes + ids.nbytes
+
+    # ---- reduce over ranks ----
+    if dist:
+        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms_max, e2e_s_max = float(t[0]), float(t[1])
+        c = torch.tensor([keys, e2e_keys], dtype=torch.float64, device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        keys_all, e2e_keys_all = float(c[0]), float(c[1])
+    else:
+        total_ms_max, e2e_s_max, keys_all, e2e_keys_all = total_ms, e2e_s, float(keys), float(e2e_keys)
+
+    # ---- roofline of the query kernel ----
+    peaks = load_peaks()
+    rows_per_key = w.R * w.eta
+    row_bytes = g.row_stride * 4
+    sectors_per_row = (row_bytes + SECTOR - 1) // SECTOR if row_bytes <= SECTOR else -(-row_bytes // SECTOR)
+    alg_bytes = probed * rows_per_key * sectors_per_row * SECTOR
+    qk_total = sum(qk_ms)
+    achieved = alg_bytes / (qk_total / 1000) / 1e9
+    # random-row ceiling on a buffer the size of the index
+    rr = None
+    try:
+        from paper_1910_02611_gb300 import random_row_probe
+
+        n_rows = w.R * w.m
+        buf = torch.empty(n_rows * g.row_stride, dtype=torch.int32, device=dev)
+        buf.zero_()
+        reads = 1024
+        blocks = torch.cuda.get_device_properties(dev).multi_processor_count * 8
+        random_row_probe(buf, n_rows, g.row_stride, reads, blocks, 256)
+        ms = random_row_probe(buf, n_rows, g.row_stride, reads, blocks, 256, seed=7)
+        rr_gbs = blocks * 256 * reads * SECTOR * sectors_per_row / (ms / 1000) / 1e9
+        rr = {"gbs": rr_gbs, "row_bytes": row_bytes, "buffer_bytes": n_rows * row_bytes,
+              "frac_of_roofline": achieved / rr_gbs}
+        del buf
+    except Exception as ex:  # measurement helper only
+        rr = {"error": str(ex)}
+
+    # ---- CPU oracle baseline (rank 0, N=1) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nthreads = os.cpu_count() or 1
+        o, ob_s = oracle_index(w, nthreads)
+        rate, n, dt = oracle_rate(o, batches[0], w.k, nthreads, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+               "sample": f"first {n} queries of the timed batch ({dt:.1f} s, {nthreads} threads); oracle index "
+                         f"built from the same sets in {ob_s:.1f} s"}
+        del o
+
+    if rank != 0:
+        return 0
+    lat = sorted(step_ms)
+    line = {
+        "metric": METRIC,
+        "value": keys_all / (total_ms_max / 1000),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic",
+        "config": {
+            "workload": f"{w.name}: K={w.K} sets, B={w.B}, R={w.R}, m=2^{int(np.log2(w.m))}, eta={w.eta}, k={w.k}; "
+                        f"{len(batches[0])} query sequences per step (scale {args.scale})",
+            "parallelism": f"replicas x{world} (one index per GPU, disjoint batches)",
+            "l2": "flushed before every step (256 MiB write); index 6 GiB > L2" if w.name == "genome" else
+                  "flushed before every step (256 MiB write)",
+            "batches": len(batches),
+        },
+        "batch_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "keys_probed_frac": probed / max(keys, 1),
+        "results_per_step": n_ids / args.steps,
+        "e2e": {"value": e2e_keys_all / e2e_s_max, "unit": UNIT, "h2d_bytes_per_step": h2d // n_e2e,
+                "d2h_bytes_per_step": d2h // n_e2e},
+        "gpu_launches": launches,
+        "roofline": {
+            "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(w.name),
+            "kernel": "k_query", "peak_source": peaks["source"],
+            "bytes_model": f"{rows_per_key} rows x {sectors_per_row} sector(s) x 32 B per probed key",
+            "query_kernel_ms_per_step": qk_total / args.steps,
+        },
+        "random_row_roofline": rr,
+        "construction": {"keys": build_keys, "ms": build_ms, "keys_per_s": build_keys / (build_ms / 1000)},
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "setup_s": {"workload_generation": t_gen},
+    }
+    print(json.dumps(line), flush=True)
+    if args.json_out:
+        with open(args.json_out, "w") as f:
+            json.dump(line, f, indent=1)
+    if dist:
+        dist.destroy_process_group()
+    g.close()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

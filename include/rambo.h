@@ -1,0 +1,240 @@
+/*
+ * rambo.h -- C ABI of librambo, a GB300 (sm_103a) implementation of RAMBO
+ * (Repeated And Merged BloOm filters; Gupta et al., arXiv 1910.02611) for
+ * multiple set membership testing (MSMT, Sec. 1): given K sets S_0..S_{K-1}
+ * of 64-bit keys and a query, return the IDs of the sets that contain it.
+ *
+ * Structure (Sec. 3): R tables ("repetitions") of B cells; a 2-universal
+ * partition hash phi_r sends each set ID to one cell per table; each cell is a
+ * Bloom filter (Sec. 2) of m = 2^L bits over the union of its sets, probed at
+ * eta positions h_{r,j}(x).  Stored bit-sliced in device memory: one row of B
+ * bits per (table r, position p), so one row read tests all B cells of a table.
+ *
+ * Hash specification (the paper only asks for universal / 2-universal hashes):
+ *   SplitMix64 (Steele, Lea, Flood 2014) with state = seed draws, in order,
+ *   a_r = 1 + next() mod (P-1), c_r = next() mod P for r < R, then
+ *   s_{r,j} = next() | 1 for r < R, j < eta, where P = 2^61 - 1, and
+ *     phi_r(i)   = ((a_r * i + c_r) mod P) mod B
+ *     h_{r,j}(x) = (s_{r,j} * mix64(x) mod 2^64) >> (64 - L)
+ *   mix64 being SplitMix64's output finalizer.  DNA k-mers (1 <= k <= 32) are
+ *   keys of 2 bits per base, A/a=0 C/c=1 G/g=2 T/t=3, first base most
+ *   significant; every length-k window of a sequence is one key.
+ *
+ * Conventions for every entry point:
+ *   - Return RAMBO_OK (0) or a negative RAMBO_E* code; rambo_strerror names it.
+ *     A failed call leaves the index as it was (inputs are validated on the
+ *     device before anything is written), except RAMBO_ECUDA, after which the
+ *     handle should be destroyed.
+ *   - `on_device` = 1: every pointer argument (inputs and caller-provided
+ *     outputs) is device memory; 0: host memory (pageable or pinned).
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     enqueue their work on it and return once it has finished (they
+ *     synchronise the stream), so inputs may be freed on return.
+ *   - CSR batches: item t is data[offsets[t] .. offsets[t+1]) (uint64
+ *     offsets, n+1 of them, non-decreasing; offsets[0] need not be 0).
+ *   - Results are ascending, duplicate-free uint32 set IDs per query, in CSR
+ *     form.  Result pointers returned by the query calls point into an arena
+ *     owned by the handle: device memory when on_device = 1, pinned host
+ *     memory otherwise; they stay valid until the next query call on the
+ *     same handle or rambo_destroy.
+ *   - A handle may be used from one host thread at a time.
+ */
+#ifndef RAMBO_H
+#define RAMBO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rambo rambo_t;
+
+enum {
+    RAMBO_OK = 0,
+    RAMBO_EINVAL = -1,   /* bad parameter, decreasing offsets, empty key query */
+    RAMBO_ERANGE = -2,   /* set ID >= K */
+    RAMBO_EBADSEQ = -3,  /* base outside ACGTacgt, or query sequence shorter than k */
+    RAMBO_ENOMEM = -4,   /* device or pinned host allocation failed */
+    RAMBO_ENOSPC = -5,   /* caller-provided output too small (see *needed) */
+    RAMBO_ECUDA = -6,    /* a CUDA runtime call failed */
+    RAMBO_ETIMEOUT = -7, /* a bounded device-side wait gave up */
+    RAMBO_EIO = -8,      /* file error in save/load */
+    RAMBO_ESTATE = -9    /* call not valid in the object's current state */
+};
+
+/* Limits of this implementation. */
+#define RAMBO_MAX_R 8        /* repetitions (tables) */
+#define RAMBO_MAX_ETA 4      /* hashes per Bloom filter */
+#define RAMBO_MAX_B 4096     /* cells per table */
+#define RAMBO_MAX_L 32       /* m = 2^L bits per Bloom filter */
+
+typedef struct rambo_info {
+    uint64_t K;            /* set-ID capacity */
+    uint32_t B, R, eta, L; /* cells, tables, hashes, log2(m) */
+    uint64_t m;            /* bits per Bloom filter */
+    uint64_t seed;
+    uint32_t row_words;    /* W = ceil(B/32): 32-bit words holding one row's B bits */
+    uint32_t row_stride;   /* S >= W: words between consecutive rows in memory */
+    uint64_t index_bytes;  /* R * m * S * 4 */
+    uint64_t n_registered; /* sets inserted so far (ID registered) */
+} rambo_info_t;
+
+/* Creates an empty index (Sec. 3: R tables x B cells of m-bit Bloom filters,
+ * all zero) for set IDs 0..K-1.  Constraints: 1 <= K <= 2^32, 1 <= B <=
+ * RAMBO_MAX_B, 1 <= R <= RAMBO_MAX_R, 1 <= eta <= RAMBO_MAX_ETA, m a power of
+ * two with 2 <= m <= 2^32.  Allocates the index (R*m*S*4 bytes) and the
+ * partition table on the current CUDA device.  Errors: RAMBO_EINVAL,
+ * RAMBO_ENOMEM, RAMBO_ECUDA.  *out receives the handle (owned by the caller,
+ * released with rambo_destroy). */
+int rambo_create(uint64_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta,
+                 uint64_t seed, rambo_t **out);
+
+/* Releases all device and host memory of the handle (NULL is ignored). */
+void rambo_destroy(rambo_t *h);
+
+int rambo_get_info(const rambo_t *h, rambo_info_t *out);
+
+/* Algorithm 1 (Sec. 3.1), for n_sets sets in one call: set t has ID
+ * set_ids[t] and keys keys[offsets[t] .. offsets[t+1]); every key is inserted
+ * into the Bloom filter of cell phi_r(set_ids[t]) of every table r.  An ID may
+ * appear several times and in several calls (insertion only sets bits, so the
+ * resulting bits do not depend on order or split).  Every listed ID becomes
+ * registered (reported by queries), even with no keys.
+ * Errors: RAMBO_ERANGE (an ID >= K), RAMBO_EINVAL (decreasing offsets). */
+int rambo_insert_batch(rambo_t *h, const uint64_t *set_ids, const uint64_t *keys,
+                       const uint64_t *offsets, uint64_t n_sets, int on_device,
+                       void *stream);
+
+/* Algorithm 1 for sets given as DNA: set t's keys are the k-mers of
+ * bases[offsets[t] .. offsets[t+1]) (Sec. 5.2: overlapping windows, k = 31).
+ * A sequence shorter than k contributes no keys but its ID is registered.
+ * Errors: RAMBO_ERANGE, RAMBO_EINVAL (offsets, k outside [1,32]),
+ * RAMBO_EBADSEQ (a byte outside ACGTacgt). */
+int rambo_insert_seq_batch(rambo_t *h, const uint64_t *set_ids, const uint8_t *bases,
+                           const uint64_t *offsets, uint64_t n_sets, uint32_t k,
+                           int on_device, void *stream);
+
+/* Algorithm 2 (Sec. 3.2) for a batch of conjunctive queries: query q's terms
+ * are keys[offsets[q] .. offsets[q+1]); the answer is the IDs i of registered
+ * sets such that, in every table r, every term is in the Bloom filter of cell
+ * phi_r(i) (per table, the union of the hit cells' sets; across tables, the
+ * intersection; across terms, the conjunction of Sec. 3.2.1).  Results: set
+ * IDs of query q are (*ids)[(*id_offsets)[q] .. (*id_offsets)[q+1]), ascending.
+ * Errors: RAMBO_EINVAL (decreasing offsets or a query with no terms). */
+int rambo_query_batch(rambo_t *h, const uint64_t *keys, const uint64_t *offsets,
+                      uint64_t n_queries, int on_device, const uint32_t **ids,
+                      const uint64_t **id_offsets, void *stream);
+
+/* Large sequence query (Sec. 3.2.1): query q is the DNA sequence
+ * bases[offsets[q] .. offsets[q+1]); its terms are all its k-mers and the
+ * answer is the sets that hold every one of them.  Errors: RAMBO_EBADSEQ (a
+ * byte outside ACGTacgt, or a sequence shorter than k), RAMBO_EINVAL. */
+int rambo_query_seq_batch(rambo_t *h, const uint8_t *bases, const uint64_t *offsets,
+                          uint64_t n_queries, uint32_t k, int on_device,
+                          const uint32_t **ids, const uint64_t **id_offsets,
+                          void *stream);
+
+/* Same as rambo_query_batch / rambo_query_seq_batch but the results go to
+ * caller-owned buffers: ids (capacity ids_cap entries) and id_offsets
+ * (n_queries + 1 entries), device or host per on_device.  If the results do
+ * not fit, returns RAMBO_ENOSPC and stores the needed number of IDs in
+ * *needed (ids untouched; the call may be repeated with a larger buffer). */
+int rambo_query_batch_into(rambo_t *h, const uint64_t *keys, const uint64_t *offsets,
+                           uint64_t n_queries, int on_device, uint32_t *ids,
+                           uint64_t ids_cap, uint64_t *id_offsets, uint64_t *needed,
+                           void *stream);
+int rambo_query_seq_batch_into(rambo_t *h, const uint8_t *bases, const uint64_t *offsets,
+                               uint64_t n_queries, uint32_t k, int on_device,
+                               uint32_t *ids, uint64_t ids_cap, uint64_t *id_offsets,
+                               uint64_t *needed, void *stream);
+
+/* Copies the bit-sliced index to host memory: n_words must equal
+ * R * m * row_stride; word (r*m + p)*row_stride + w holds bits 32w..32w+31 of
+ * row (r, p), bit b of the row being bit p of the Bloom filter of cell b of
+ * table r (padding words are zero).  Errors: RAMBO_EINVAL (wrong n_words). */
+int rambo_export_index(const rambo_t *h, uint32_t *host_words, uint64_t n_words);
+
+/* Copies the registered-set bitmap (ceil(K/32) words, bit i = set i) and
+ * the partition table (K*R values, phi_r(i) at [i*R + r]) to host memory. */
+int rambo_export_registered(const rambo_t *h, uint32_t *host_words, uint64_t n_words);
+int rambo_export_partition(const rambo_t *h, uint16_t *host_phi, uint64_t n);
+
+/* Number of set bits of every Bloom filter, out[r*B + b] (host memory, R*B
+ * entries); fill/m is the quantity Sec. 2's false-positive formula predicts. */
+int rambo_cell_popcount(const rambo_t *h, uint64_t *host_out, void *stream);
+
+/* Work and time of the last query call on this handle.  keys_probed counts
+ * the keys whose rows were read: once a query's per-table mask is empty its
+ * answer is empty and its remaining keys are skipped (Sec. 3.2.1, the first
+ * FALSE is conclusive).  Times come from CUDA events recorded on the call's
+ * stream around the query kernel and around all of the call's kernels. */
+typedef struct rambo_query_stats {
+    uint64_t n_queries;
+    uint64_t keys_submitted;
+    uint64_t keys_probed;
+    uint64_t rows_read;        /* keys_probed * R * eta */
+    uint64_t n_results;        /* set IDs returned */
+    uint64_t kernel_launches;  /* kernels this library launched for the call */
+    float query_kernel_ms;
+    float device_ms;
+} rambo_query_stats_t;
+
+int rambo_last_query_stats(const rambo_t *h, rambo_query_stats_t *out);
+
+/* Tuning knobs of the query kernel; results never depend on them.
+ *   lanes_per_key G, words_per_lane V (V divides the row stride, G*V >= stride),
+ *   warps_per_block, blocks_per_sm (0 = as many as fit),
+ *   set_stage: 0 = auto, 1 = dense scan of the partition table,
+ *              2 = sparse enumeration of the hit cells' members. */
+typedef struct rambo_query_config {
+    uint32_t lanes_per_key;
+    uint32_t words_per_lane;
+    uint32_t warps_per_block;
+    uint32_t blocks_per_sm;
+    uint32_t set_stage;
+} rambo_query_config_t;
+
+int rambo_get_query_config(const rambo_t *h, rambo_query_config_t *out);
+/* Errors: RAMBO_EINVAL for a combination the kernels do not implement. */
+int rambo_set_query_config(rambo_t *h, const rambo_query_config_t *cfg);
+
+/* Construction tiling (results never depend on it): mode 0 = choose per
+ * call from the input and index sizes, 1 = always run the build window by
+ * window (each window of tile_bytes of the index stays resident in L2 while
+ * the input streams past), 2 = one pass with every update going to device
+ * memory.  tile_bytes = 0 keeps the current window size (64 MiB initially). */
+int rambo_set_build_tiling(rambo_t *h, uint64_t tile_bytes, int mode);
+
+/* Lists the query-kernel configurations valid for this handle (at most cap),
+ * returns how many there are. */
+int rambo_list_query_configs(const rambo_t *h, rambo_query_config_t *out, int cap);
+
+/* Checkpoint (no counterpart in the paper, which keeps its index in memory):
+ * writes the parameters, the registered-set bitmap and the rows to a file;
+ * rambo_load recreates an identical handle on the current device.
+ * Errors: RAMBO_EIO, RAMBO_EINVAL (not a file written by rambo_save). */
+int rambo_save(const rambo_t *h, const char *path);
+int rambo_load(const char *path, rambo_t **out);
+
+/* Measurement helper (no counterpart in the paper): every thread of
+ * blocks x threads reads reads_per_thread random rows of a device buffer of
+ * n_rows rows (a power of two) spaced row_words 32-bit words apart (the first
+ * min(row_words, 4) words of each), as the query's row probes do.  *ms gets
+ * the kernel time.  Gives the random-row throughput ceiling of the device. */
+int rambo_random_row_probe(const uint32_t *dev_buf, uint64_t n_rows, uint32_t row_words,
+                           uint64_t reads_per_thread, uint32_t blocks, uint32_t threads,
+                           uint64_t seed, float *ms, void *stream);
+
+/* Index of the item (query or set) that caused the last RAMBO_EINVAL,
+ * RAMBO_ERANGE or RAMBO_EBADSEQ returned on this handle. */
+uint64_t rambo_last_error_item(const rambo_t *h);
+
+const char *rambo_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RAMBO_H */

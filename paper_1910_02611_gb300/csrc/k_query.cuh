@@ -1,0 +1,299 @@
+// k_query.cuh -- the batched RAMBO query kernel (Algorithm 2, Sec. 3.2, with
+// the sequence rule of Sec. 3.2.1), as a template over its register tiling.
+//
+// One warp answers one query at a time, taking query indices from a device
+// work queue (an atomic ticket), so queries of very uneven length balance
+// themselves across a persistent grid.
+//
+// Per query (terms Q = its keys, or the k-mers of its sequence):
+//   A1/A2  each lane group (G lanes) takes one term per step, builds the key
+//          (from 2-bit packed DNA for sequences) and its R*eta positions;
+//   A3     every lane reads V consecutive words of each of the term's R*eta
+//          rows (one coalesced vector read per probe; all reads of a step are
+//          issued before any is used) and ANDs the eta rows of each table: the
+//          result is the term's B-bit cell mask per table (bit b set = the
+//          term is in the Bloom filter of cell b);
+//   A4     masks are AND-reduced across the warp's terms and into the running
+//          per-table mask M_r; as soon as some M_r is empty no set can hold
+//          every term (Sec. 3.2.1: the first FALSE is conclusive) and the
+//          query stops reading rows;
+//   A5     a surviving query keeps the registered sets i with bit phi_r(i) of
+//          M_r set in every table: per table the union of the hit cells'
+//          sets, across tables the intersection (Algorithm 2).  "dense" scans
+//          the partition table over all IDs; "sparse" enumerates the members
+//          of the hit cells of the table with the fewest hit cells, tests the
+//          other tables, and marks survivors in a per-warp bitmap;
+//   A6     survivors are written in ascending ID order to a staging arena
+//          (one atomic reservation per query); a scan + gather then lays the
+//          lists out in query order.
+#pragma once
+
+#include "rambo_impl.cuh"
+
+namespace rgb {
+
+constexpr int QK_THREADS_MAX = 256;
+constexpr int QK_ID_CAP = 128;  // per-warp staging of dense-stage survivors
+
+__host__ __device__ inline uint32_t qk_bitmap_words(uint64_t K) { return (uint32_t)((K + 31) / 32); }
+
+template <int V>
+__device__ __forceinline__ void qk_load(const uint32_t* __restrict__ p, uint32_t (&out)[V]) {
+    if constexpr (V == 1) {
+        out[0] = __ldg(p);
+    } else if constexpr (V == 2) {
+        uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+        out[0] = t.x;
+        out[1] = t.y;
+    } else {
+        uint4 t = __ldg(reinterpret_cast<const uint4*>(p));
+        out[0] = t.x;
+        out[1] = t.y;
+        out[2] = t.z;
+        out[3] = t.w;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ uint32_t qk_and_groups(uint32_t x) {
+    if constexpr (G == 1) {
+        return __reduce_and_sync(FULL, x);
+    } else {
+#pragma unroll
+        for (int off = G; off < 32; off <<= 1) x &= __shfl_xor_sync(FULL, x, off);
+        return x;
+    }
+}
+
+__device__ __forceinline__ bool qk_set_passes(const IndexView& ix, const uint32_t* sM, uint64_t i,
+                                              int skip_r) {
+    if (!((__ldg(ix.reg + (i >> 5)) >> (i & 31)) & 1u)) return false;
+    uint4 ph = __ldg(reinterpret_cast<const uint4*>(ix.phi) + i);
+    uint32_t cell[8] = {ph.x & 0xffffu, ph.x >> 16, ph.y & 0xffffu, ph.y >> 16,
+                        ph.z & 0xffffu, ph.z >> 16, ph.w & 0xffffu, ph.w >> 16};
+    bool ok = true;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+        if (r < (int)ix.R && r != skip_r) {
+            uint32_t b = cell[r];
+            ok &= (sM[r * ix.S + (b >> 5)] >> (b & 31)) & 1u;
+        }
+    }
+    return ok;
+}
+
+template <int V, int G, int ETA>
+__global__ void __launch_bounds__(QK_THREADS_MAX)
+    k_query(IndexView ix, HashParams hp, BatchView b, QueryOut o, int set_stage, int batch,
+            uint32_t smem_per_warp, int use_bitmap, DevStatus* st) {
+    extern __shared__ uint32_t qk_smem[];
+    constexpr int KPS = 32 / G;  // terms per warp step
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned grp = lane / G;
+    const unsigned slot = lane % G;
+    const uint32_t w0 = slot * V;
+    const bool has_words = w0 < ix.S;
+    const int R = (int)ix.R;
+    const int eta = (int)ix.eta;
+    const uint32_t rmask = (1u << R) - 1u;
+    uint32_t* sM = qk_smem + (threadIdx.x >> 5) * smem_per_warp;  // [R][S] running masks
+    uint32_t* sIds = sM + R * ix.S;                                // [QK_ID_CAP]
+    uint32_t* sBits = sIds + QK_ID_CAP;                            // [ceil(K/32)] sparse-stage bitmap
+    const uint32_t bw = qk_bitmap_words(ix.K);
+    const uint32_t* __restrict__ rows = ix.rows;
+
+    if (*(volatile unsigned long long*)&st->err != NO_ERR) return;
+    if (use_bitmap)
+        for (uint32_t w = lane; w < bw; w += 32) sBits[w] = 0;
+    __syncwarp();
+
+    unsigned long long probed = 0;
+    for (;;) {
+        unsigned long long q0 = 0;
+        if (lane == 0) q0 = atomicAdd(&st->ticket, (unsigned long long)batch);
+        q0 = __shfl_sync(FULL, q0, 0);
+        if (q0 >= b.n) break;
+        const unsigned long long q1 = min(q0 + (unsigned long long)batch, (unsigned long long)b.n);
+        for (unsigned long long q = q0; q < q1; ++q) {
+            const uint64_t a = __ldg(b.offsets + q) - b.off0;
+            const uint64_t e = __ldg(b.offsets + q + 1) - b.off0;
+            const uint64_t nkeys = b.seq ? (e - a - b.k + 1) : (e - a);  // >= 1 (validated)
+
+            uint32_t M[RMAX][V];
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r)
+#pragma unroll
+                for (int v = 0; v < V; ++v) M[r][v] = has_words ? ~0u : 0u;
+
+            bool alive = true;
+            for (uint64_t base = 0; base < nkeys; base += KPS) {
+                const uint64_t idx = base + grp;
+                const bool act = idx < nkeys;
+                uint64_t key = 0;
+                if (act) key = b.seq ? kmer_at(b.packed, a + idx, b.k) : __ldg(b.keys + a + idx);
+                const uint64_t y = mix64(key);
+                // A3: issue every row read of this step, then combine
+                uint32_t val[RMAX][ETA][V];
+                const bool ld = act && has_words;
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r) {
+                    if (r < R && ld) {
+                        const uint32_t* rb = rows + (uint64_t)r * ix.m * ix.S + w0;
+#pragma unroll
+                        for (int j = 0; j < ETA; ++j) {
+                            if (j < eta) {
+                                const uint64_t pos = (hp.s[r][j] * y) >> ix.shift;
+                                qk_load<V>(rb + pos * ix.S, val[r][j]);
+                            }
+                        }
+                    }
+                }
+                uint32_t nz = 0;
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r) {
+                    if (r < R) {
+                        uint32_t any = 0;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            uint32_t x = ~0u;
+                            if (ld) {
+#pragma unroll
+                                for (int j = 0; j < ETA; ++j)
+                                    if (j < eta) x &= val[r][j][v];
+                            }
+                            x = qk_and_groups<G>(x);  // A4: across this step's terms
+                            M[r][v] &= x;             // and into the query's masks
+                            any |= M[r][v];
+                        }
+                        if (any) nz |= 1u << r;
+                    }
+                }
+                nz = __reduce_or_sync(FULL, nz);
+                probed += (nkeys - base < (uint64_t)KPS) ? (nkeys - base) : (uint64_t)KPS;
+                if (nz != rmask) {
+                    alive = false;
+                    break;
+                }
+            }
+
+            uint32_t count = 0;
+            unsigned long long start = 0;
+            if (alive) {
+                // stage the masks: row words [w0, w0+V) of table r
+                if (grp == 0 && has_words) {
+#pragma unroll
+                    for (int r = 0; r < RMAX; ++r)
+                        if (r < R)
+#pragma unroll
+                            for (int v = 0; v < V; ++v) sM[r * ix.S + w0 + v] = M[r][v];
+                }
+                __syncwarp();
+                // table with the fewest hit cells (its cells' members are the candidates)
+                int rstar = 0;
+                uint32_t pmin = 0xffffffffu;
+                {
+                    uint32_t pc[RMAX];
+#pragma unroll
+                    for (int r = 0; r < RMAX; ++r) {
+                        uint32_t c = 0;
+                        if (r < R && grp == 0 && has_words)
+#pragma unroll
+                            for (int v = 0; v < V; ++v) c += __popc(M[r][v]);
+                        pc[r] = (r < R) ? __reduce_add_sync(FULL, c) : 0xffffffffu;
+                    }
+#pragma unroll
+                    for (int r = 0; r < RMAX; ++r)
+                        if (pc[r] < pmin) {
+                            pmin = pc[r];
+                            rstar = r;
+                        }
+                }
+                bool sparse = use_bitmap && (set_stage == 2 ||
+                                             (set_stage == 0 && (uint64_t)pmin * (ix.K / ix.B + 1) * (uint64_t)R +
+                                                                        2ull * ix.K <
+                                                                    ix.K * (uint64_t)R));
+                if (!sparse) {
+                    // dense: every ID in order; ballot keeps the order
+                    for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
+                        const uint64_t i = i0 + lane;
+                        const bool ok = (i < ix.K) && qk_set_passes(ix, sM, i, -1);
+                        const unsigned bal = __ballot_sync(FULL, ok);
+                        if (bal) {
+                            const unsigned pre = __popc(bal & ((1u << lane) - 1u));
+                            if (ok && count + pre < (uint32_t)QK_ID_CAP) sIds[count + pre] = (uint32_t)i;
+                            count += __popc(bal);
+                        }
+                    }
+                    if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
+                    start = __shfl_sync(FULL, start, 0);
+                    if (count && start + count <= o.stage_cap) {
+                        if (count <= (uint32_t)QK_ID_CAP) {
+                            for (uint32_t t = lane; t < count; t += 32) o.stage[start + t] = sIds[t];
+                        } else {
+                            uint32_t at = 0;
+                            for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
+                                const uint64_t i = i0 + lane;
+                                const bool ok = (i < ix.K) && qk_set_passes(ix, sM, i, -1);
+                                const unsigned bal = __ballot_sync(FULL, ok);
+                                if (ok) o.stage[start + at + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
+                                at += __popc(bal);
+                            }
+                        }
+                    }
+                } else {
+                    // sparse: members of the hit cells of table rstar, tested on the other tables
+                    const uint32_t* cellmask = sM + rstar * ix.S;
+                    for (uint32_t w = 0; w < ix.W; ++w) {
+                        uint32_t bits = cellmask[w];
+                        while (bits) {
+                            const uint32_t cb = w * 32 + (__ffs(bits) - 1);
+                            bits &= bits - 1;
+                            const uint64_t cell = (uint64_t)rstar * ix.B + cb;
+                            const uint64_t m0 = __ldg(ix.mem_off + cell), m1 = __ldg(ix.mem_off + cell + 1);
+                            for (uint64_t u = m0 + lane; u < m1; u += 32) {
+                                const uint32_t i = __ldg(ix.mem_ids + u);
+                                if (qk_set_passes(ix, sM, i, rstar)) atomicOr(sBits + (i >> 5), 1u << (i & 31));
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    for (uint32_t w = lane; w < bw; w += 32) count += __popc(sBits[w]);
+                    count = __reduce_add_sync(FULL, count);
+                    if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
+                    start = __shfl_sync(FULL, start, 0);
+                    const bool write = count && start + count <= o.stage_cap;
+                    uint32_t at = 0;
+                    for (uint32_t w0b = 0; w0b < bw; w0b += 32) {
+                        const uint32_t w = w0b + lane;
+                        uint32_t bits = (w < bw) ? sBits[w] : 0u;
+                        uint32_t c = __popc(bits);
+                        uint32_t incl = c;
+#pragma unroll
+                        for (int off = 1; off < 32; off <<= 1) {
+                            uint32_t y = __shfl_up_sync(FULL, incl, off);
+                            if (lane >= (unsigned)off) incl += y;
+                        }
+                        if (write) {
+                            uint32_t pos = at + incl - c;
+                            while (bits) {
+                                const uint32_t bit = __ffs(bits) - 1;
+                                bits &= bits - 1;
+                                o.stage[start + pos++] = w * 32 + bit;
+                            }
+                        }
+                        if (w < bw) sBits[w] = 0;
+                        at += __shfl_sync(FULL, incl, 31);
+                    }
+                    __syncwarp();
+                }
+            }
+            if (lane == 0) {
+                o.qcount[q] = count;
+                o.qstart[q] = start;
+            }
+        }
+    }
+    if (lane == 0 && probed) atomicAdd(&st->keys_probed, probed);
+}
+
+}  // namespace rgb

@@ -1,0 +1,377 @@
+// k_util.cu -- small kernels around the RAMBO hot path: input validation and
+// 2-bit packing (batch intake), set registration, the partition table and its
+// per-cell member lists, the count scan and result gather of the compaction
+// step, and index statistics.
+#include "rambo_impl.cuh"
+
+namespace rgb {
+
+static inline int grid_for(uint64_t n, int threads, int cap = 1 << 20) {
+    uint64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > (uint64_t)cap) g = cap;
+    return (int)g;
+}
+
+// ---------------------------------------------------------------------------
+
+__global__ void k_status_reset(DevStatus* st) {
+    st->err = NO_ERR;
+    st->bad_pos = NO_ERR;
+    st->ticket = 0;
+    st->cursor = 0;
+    st->keys_probed = 0;
+    st->rows_read = 0;
+    st->spare[0] = st->spare[1] = 0;
+}
+
+cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s) {
+    k_status_reset<<<1, 1, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// partition table: phi[i*PHI_STRIDE + r] = phi_r(i)
+
+struct PhiParams {
+    uint64_t a[RMAX], c[RMAX];
+};
+
+__global__ void k_phi_init(uint16_t* phi, uint64_t K, uint32_t R, uint32_t B, PhiParams pp) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < K;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint16_t row[PHI_STRIDE];
+#pragma unroll
+        for (int r = 0; r < PHI_STRIDE; ++r)
+            row[r] = (r < (int)R) ? (uint16_t)partition_hash(pp.a[r], pp.c[r], i, B) : (uint16_t)0;
+        uint4 v;
+        v.x = row[0] | ((uint32_t)row[1] << 16);
+        v.y = row[2] | ((uint32_t)row[3] << 16);
+        v.z = row[4] | ((uint32_t)row[5] << 16);
+        v.w = row[6] | ((uint32_t)row[7] << 16);
+        reinterpret_cast<uint4*>(phi)[i] = v;
+    }
+}
+
+cudaError_t launch_phi_init(uint16_t* phi, uint64_t K, uint32_t R, uint32_t B, const uint64_t* a,
+                            const uint64_t* c, cudaStream_t s) {
+    PhiParams pp{};
+    for (uint32_t r = 0; r < R && r < (uint32_t)RMAX; ++r) {
+        pp.a[r] = a[r];
+        pp.c[r] = c[r];
+    }
+    k_phi_init<<<grid_for(K, 256, 4096), 256, 0, s>>>(phi, K, R, B, pp);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// batch validation: set IDs < K, non-decreasing offsets, minimum item length
+
+__global__ void k_validate(BatchView b, uint64_t min_len, unsigned short_prio, uint64_t K,
+                           DevStatus* st) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < b.n;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        if (b.set_ids && b.set_ids[t] >= K) {
+            record_error(st, t, PRIO_ERANGE);
+            continue;
+        }
+        uint64_t lo = b.offsets[t], hi = b.offsets[t + 1];
+        if (hi < lo) {
+            record_error(st, t, PRIO_EINVAL);
+            continue;
+        }
+        if (hi - lo < min_len) record_error(st, t, short_prio);
+    }
+}
+
+cudaError_t launch_validate_batch(const BatchView& b, uint64_t min_len, uint64_t K, DevStatus* st,
+                                  cudaStream_t s) {
+    if (b.n == 0) return cudaSuccess;
+    // a sequence query shorter than k is a bad sequence; an empty key query is invalid
+    unsigned prio = b.seq ? PRIO_EBADSEQ : PRIO_EINVAL;
+    k_validate<<<grid_for(b.n, 256, 8192), 256, 0, s>>>(b, min_len, prio, K, st);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// 2-bit packing of ASCII DNA: word w holds bases 32w..32w+31, base 32w+t in
+// bits 63-2t..62-2t; A/a=0 C/c=1 G/g=2 T/t=3.  Bytes past the end pack as 0.
+// A byte outside ACGTacgt is recorded (lowest position wins) and packs as 0.
+
+__device__ __forceinline__ int base_code(unsigned ch) {
+    unsigned u = ch | 0x20u;  // only 'A'/'a' etc. fold onto the lower-case letters
+    bool ok = (u == 'a') | (u == 'c') | (u == 'g') | (u == 't');
+    unsigned x = (u >> 1) & 3u;  // a->0, c->1, g->3, t->2
+    return ok ? (int)(x ^ (x >> 1)) : -1;
+}
+
+__global__ void k_pack(const uint8_t* __restrict__ bases, uint64_t total, uint64_t* __restrict__ packed,
+                       uint64_t n_words, DevStatus* st) {
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < n_words;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t v = 0;
+        uint64_t p0 = w * 32;
+        unsigned long long bad = NO_ERR;
+        if (p0 + 32 <= total) {
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                int c = base_code(__ldg(bases + p0 + t));
+                if (c < 0) {
+                    if (bad == NO_ERR) bad = p0 + t;
+                    c = 0;
+                }
+                v |= (uint64_t)c << (62 - 2 * t);
+            }
+        } else {
+            for (int t = 0; t < 32; ++t) {
+                uint64_t p = p0 + t;
+                if (p >= total) break;
+                int c = base_code(__ldg(bases + p));
+                if (c < 0) {
+                    if (bad == NO_ERR) bad = p;
+                    c = 0;
+                }
+                v |= (uint64_t)c << (62 - 2 * t);
+            }
+        }
+        packed[w] = v;
+        if (bad != NO_ERR) atomicMin(&st->bad_pos, bad);
+    }
+}
+
+cudaError_t launch_pack(const uint8_t* bases, uint64_t total, uint64_t* packed, uint64_t n_words,
+                        DevStatus* st, cudaStream_t s) {
+    if (n_words == 0) return cudaSuccess;
+    k_pack<<<grid_for(n_words, 256, 1 << 16), 256, 0, s>>>(bases, total, packed, n_words, st);
+    return cudaGetLastError();
+}
+
+// The item holding the lowest bad byte gets an EBADSEQ error.
+__global__ void k_resolve_bad_base(BatchView b, DevStatus* st) {
+    unsigned long long p = st->bad_pos;
+    if (p == NO_ERR || b.n == 0) return;
+    uint64_t abs_p = p + b.off0;
+    // largest t in [0, n) with offsets[t] <= abs_p
+    uint64_t lo = 0, hi = b.n;  // invariant: answer in [lo, hi)
+    while (hi - lo > 1) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (b.offsets[mid] <= abs_p) lo = mid;
+        else hi = mid;
+    }
+    record_error(st, lo, PRIO_EBADSEQ);
+}
+
+cudaError_t launch_resolve_bad_base(const BatchView& b, DevStatus* st, cudaStream_t s) {
+    k_resolve_bad_base<<<1, 1, 0, s>>>(b, st);
+    return cudaGetLastError();
+}
+
+// Every listed set ID becomes registered (Algorithm 2's SetIDs(M[b,r]) only
+// reports inserted sets).  Runs only on a clean batch.
+__global__ void k_register(BatchView b, uint32_t* reg, const DevStatus* st) {
+    if (st->err != NO_ERR) return;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < b.n;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t id = b.set_ids[t];
+        atomicOr(reg + (id >> 5), 1u << (id & 31));
+    }
+}
+
+cudaError_t launch_register(const BatchView& b, uint32_t* reg, DevStatus* st, cudaStream_t s) {
+    if (b.n == 0) return cudaSuccess;
+    k_register<<<grid_for(b.n, 256, 4096), 256, 0, s>>>(b, reg, st);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of uint32 counts into uint64 offsets (n+1 entries, the last
+// being the total).  Three passes: tile sums, scan of the tile sums, tiles.
+
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+uint64_t scan_tmp_words(uint64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* warp_tot,
+                                                         uint64_t* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint64_t t = (lane < (int)(blockDim.x >> 5)) ? warp_tot[lane] : 0;
+        uint64_t u = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t y = __shfl_up_sync(FULL, u, o);
+            if (lane >= o) u += y;
+        }
+        warp_tot[lane] = u - t;  // exclusive prefix of warp totals
+        if (lane == 31) *total = u;
+    }
+    __syncthreads();
+    uint64_t r = warp_tot[wid] + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_tiles(const uint32_t* __restrict__ counts, uint64_t n, uint64_t* __restrict__ out,
+                             uint64_t* __restrict__ tile_sums) {
+    __shared__ uint64_t warp_tot[32];
+    __shared__ uint64_t tot;
+    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+    uint64_t v[SCAN_ITEMS];
+    uint64_t sum = 0;
+#pragma unroll
+    for (int t = 0; t < SCAN_ITEMS; ++t) {
+        v[t] = (base + t < n) ? counts[base + t] : 0;
+        sum += v[t];
+    }
+    uint64_t pre = block_exclusive_scan(sum, warp_tot, &tot);
+#pragma unroll
+    for (int t = 0; t < SCAN_ITEMS; ++t) {
+        if (base + t < n) out[base + t] = pre;
+        pre += v[t];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(uint64_t* tile_sums, uint64_t n_tiles) {
+    __shared__ uint64_t warp_tot[32];
+    __shared__ uint64_t tot;
+    uint64_t carry = 0;
+    for (uint64_t b0 = 0; b0 < n_tiles; b0 += blockDim.x) {
+        uint64_t i = b0 + threadIdx.x;
+        uint64_t v = i < n_tiles ? tile_sums[i] : 0;
+        uint64_t pre = block_exclusive_scan(v, warp_tot, &tot);
+        if (i < n_tiles) tile_sums[i] = carry + pre;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tile_sums[n_tiles] = carry;
+}
+
+__global__ void k_scan_add(uint64_t* __restrict__ out, uint64_t n, const uint64_t* __restrict__ tile_sums,
+                           uint64_t n_tiles) {
+    uint64_t add = tile_sums[blockIdx.x];
+    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+    for (int t = threadIdx.x; t < SCAN_TILE; t += blockDim.x)
+        if (base + t < n) out[base + t] += add;
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_sums[n_tiles];
+}
+
+cudaError_t launch_scan_counts(const uint32_t* counts, uint64_t n, uint64_t* offsets, uint64_t* tmp,
+                               uint64_t tmp_words, cudaStream_t s) {
+    uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles == 0) tiles = 1;
+    if (tmp_words < tiles + 1) return cudaErrorInvalidValue;
+    k_scan_tiles<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(counts, n, offsets, tmp);
+    k_scan_sums<<<1, SCAN_THREADS, 0, s>>>(tmp, tiles);
+    k_scan_add<<<(unsigned)tiles, 256, 0, s>>>(offsets, n, tmp, tiles);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// gather staged result IDs into CSR order: one warp per query
+
+__global__ void k_gather(QueryOut o, const uint64_t* __restrict__ id_offsets, uint64_t n,
+                         uint32_t* __restrict__ ids, const DevStatus* st) {
+    if (st->err != NO_ERR || st->cursor > o.stage_cap) return;
+    const int lane = threadIdx.x & 31;
+    uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t q = warp; q < n; q += nwarps) {
+        uint32_t c = o.qcount[q];
+        if (!c) continue;
+        const uint32_t* src = o.stage + o.qstart[q];
+        uint32_t* dst = ids + id_offsets[q];
+        for (uint32_t t = lane; t < c; t += 32) dst[t] = src[t];
+    }
+}
+
+cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_t n, uint32_t* ids,
+                          const DevStatus* st, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int blocks = grid_for(n * 32, 256, 152 * 16);
+    k_gather<<<blocks, 256, 0, s>>>(o, id_offsets, n, ids, st);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// statistics: set bits of every Bloom filter (bit b of the rows of table r)
+
+__global__ void k_cell_popcount(IndexView ix, unsigned long long* out) {
+    extern __shared__ unsigned int cnt[];  // B counters
+    const uint32_t r = blockIdx.y;
+    for (uint32_t b = threadIdx.x; b < ix.B; b += blockDim.x) cnt[b] = 0;
+    __syncthreads();
+    const uint32_t* rows = ix.rows + (uint64_t)r * ix.m * ix.S;
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < ix.m;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t* row = rows + p * ix.S;
+        for (uint32_t w = 0; w < ix.W; ++w) {
+            uint32_t x = row[w];
+            while (x) {
+                int bit = __ffs(x) - 1;
+                atomicAdd(&cnt[w * 32 + bit], 1u);
+                x &= x - 1;
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < ix.B; b += blockDim.x)
+        if (cnt[b]) atomicAdd(out + (uint64_t)r * ix.B + b, (unsigned long long)cnt[b]);
+}
+
+cudaError_t launch_cell_popcount(const IndexView& ix, unsigned long long* out, cudaStream_t s) {
+    dim3 grid((unsigned)grid_for(ix.m, 256, 512), ix.R);
+    size_t smem = sizeof(unsigned int) * ix.B;
+    k_cell_popcount<<<grid, 256, smem, s>>>(ix, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// members of every cell (in no particular order): count, scan, place
+
+__global__ void k_member_count(const uint16_t* __restrict__ phi, uint64_t K, uint32_t R, uint32_t B,
+                               uint32_t* __restrict__ cnt) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < K;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        for (uint32_t r = 0; r < R; ++r) atomicAdd(cnt + r * B + phi[i * PHI_STRIDE + r], 1u);
+}
+
+__global__ void k_member_place(const uint16_t* __restrict__ phi, uint64_t K, uint32_t R, uint32_t B,
+                               const uint64_t* __restrict__ off, uint32_t* __restrict__ fill,
+                               uint32_t* __restrict__ ids) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < K;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        for (uint32_t r = 0; r < R; ++r) {
+            uint32_t cell = r * B + phi[i * PHI_STRIDE + r];
+            uint32_t at = atomicAdd(fill + cell, 1u);
+            ids[off[cell] + at] = (uint32_t)i;
+        }
+}
+
+cudaError_t launch_members(const IndexView& ix, uint64_t* mem_off, uint32_t* mem_ids, uint32_t* fill,
+                           cudaStream_t s) {
+    uint32_t cells = ix.R * ix.B;
+    cudaError_t e = cudaMemsetAsync(fill, 0, sizeof(uint32_t) * cells, s);
+    if (e != cudaSuccess) return e;
+    k_member_count<<<grid_for(ix.K, 256, 4096), 256, 0, s>>>(ix.phi, ix.K, ix.R, ix.B, fill);
+    // offsets from counts; tmp space: reuse the tail of mem_off (caller sized it)
+    uint64_t* tmp = mem_off + cells + 1;
+    e = launch_scan_counts(fill, cells, mem_off, tmp, scan_tmp_words(cells), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(fill, 0, sizeof(uint32_t) * cells, s);
+    if (e != cudaSuccess) return e;
+    k_member_place<<<grid_for(ix.K, 256, 4096), 256, 0, s>>>(ix.phi, ix.K, ix.R, ix.B, mem_off, fill, mem_ids);
+    return cudaGetLastError();
+}
+
+}  // namespace rgb

@@ -1,0 +1,802 @@
+// rambo_api.cu -- host side of the C ABI declared in include/rambo.h: handle
+// life cycle, parameter derivation, input staging, kernel sequencing, status
+// decoding and result hand-out.  Every step of insertion and query runs in the
+// kernels of this library; the host only moves buffers and orders launches.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rambo_impl.cuh"
+
+using namespace rgb;
+
+namespace {
+
+int map_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return RAMBO_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();  // clear the sticky-free allocation error
+        return RAMBO_ENOMEM;
+    }
+    return RAMBO_ECUDA;
+}
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) return map_cuda(e_); \
+    } while (0)
+
+#define RK(x)                    \
+    do {                         \
+        int r_ = (x);            \
+        if (r_ != RAMBO_OK) return r_; \
+    } while (0)
+
+// growable device buffer
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t cap = 0;
+    int ensure(size_t n) {
+        if (n <= cap && p) return RAMBO_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = n < 64 ? 64 : n;
+        if (cudaMalloc(&p, want * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return RAMBO_ENOMEM;
+        }
+        cap = want;
+        return RAMBO_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+// growable pinned host buffer
+template <class T>
+struct HBuf {
+    T* p = nullptr;
+    size_t cap = 0;
+    int ensure(size_t n) {
+        if (n <= cap && p) return RAMBO_OK;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = n < 64 ? 64 : n;
+        if (cudaMallocHost(&p, want * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return RAMBO_ENOMEM;
+        }
+        cap = want;
+        return RAMBO_OK;
+    }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+uint64_t splitmix_next(uint64_t& state) {
+    state += 0x9E3779B97F4A7C15ull;
+    return mix64(state);
+}
+
+uint32_t stride_for(uint32_t W) {
+    if (W <= 2) return W;
+    if (W <= 4) return 4;
+    return (W + 3) / 4 * 4;
+}
+
+// default build window: a slice of the index that stays resident in L2
+constexpr uint64_t BUILD_TILE_BYTES = 64ull << 20;
+
+}  // namespace
+
+struct rambo {
+    uint64_t K = 0, m = 0, seed = 0;
+    uint32_t B = 0, R = 0, eta = 0, L = 0, W = 0, S = 0;
+    int device = 0, num_sms = 0;
+    uint64_t a[RMAX] = {}, c[RMAX] = {};
+    HashParams hp{};
+    uint32_t* rows = nullptr;
+    uint16_t* phi = nullptr;
+    uint32_t* reg = nullptr;
+    uint64_t* mem_off = nullptr;
+    uint32_t* mem_ids = nullptr;
+    DevStatus* st = nullptr;
+    DevStatus* h_st = nullptr;  // pinned
+    uint64_t* h_small = nullptr;  // pinned, 8 words
+    // scratch
+    DBuf<uint8_t> in_data;
+    DBuf<uint64_t> in_off, in_ids, packed, qstart, scan_tmp, id_off;
+    DBuf<uint32_t> stage, qcount, ids, fill;
+    HBuf<uint32_t> h_ids;
+    HBuf<uint64_t> h_id_off;
+    rambo_query_config_t cfg{};
+    uint64_t build_tile_bytes = BUILD_TILE_BYTES;
+    int build_mode = 0;
+    rambo_query_stats_t last{};
+    uint64_t launches = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // call start, query start/end, call end
+    uint64_t last_err_item = 0;
+
+    IndexView view() const {
+        IndexView v;
+        v.rows = rows;
+        v.m = m;
+        v.R = R;
+        v.eta = eta;
+        v.shift = 64 - L;
+        v.S = S;
+        v.W = W;
+        v.K = K;
+        v.B = B;
+        v.phi = phi;
+        v.reg = reg;
+        v.mem_off = mem_off;
+        v.mem_ids = mem_ids;
+        return v;
+    }
+    uint64_t index_words() const { return (uint64_t)R * m * S; }
+};
+
+namespace {
+
+void free_handle(rambo* h) {
+    if (!h) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->device);
+    if (h->rows) cudaFree(h->rows);
+    if (h->phi) cudaFree(h->phi);
+    if (h->reg) cudaFree(h->reg);
+    if (h->mem_off) cudaFree(h->mem_off);
+    if (h->mem_ids) cudaFree(h->mem_ids);
+    if (h->st) cudaFree(h->st);
+    if (h->h_st) cudaFreeHost(h->h_st);
+    if (h->h_small) cudaFreeHost(h->h_small);
+    for (auto& e : h->ev)
+        if (e) cudaEventDestroy(e);
+    h->in_data.release();
+    h->in_off.release();
+    h->in_ids.release();
+    h->packed.release();
+    h->qstart.release();
+    h->scan_tmp.release();
+    h->id_off.release();
+    h->stage.release();
+    h->qcount.release();
+    h->ids.release();
+    h->fill.release();
+    h->h_ids.release();
+    h->h_id_off.release();
+    cudaSetDevice(cur);
+    delete h;
+}
+
+void default_config(rambo* h) {
+    // one vector read per probe where the row allows it
+    int V = h->S % 4 == 0 ? 4 : (h->S % 2 == 0 ? 2 : 1);
+    int G = 1;
+    while ((uint32_t)(G * V) < h->S) G *= 2;
+    h->cfg.words_per_lane = (uint32_t)V;
+    h->cfg.lanes_per_key = (uint32_t)G;
+    h->cfg.warps_per_block = 8;
+    h->cfg.blocks_per_sm = 0;
+    h->cfg.set_stage = 0;
+}
+
+int decode_err(rambo* h, unsigned long long e) {
+    if (e == NO_ERR) return RAMBO_OK;
+    h->last_err_item = e >> 8;
+    switch ((unsigned)(e & 0xff)) {
+        case PRIO_ERANGE: return RAMBO_ERANGE;
+        case PRIO_EINVAL: return RAMBO_EINVAL;
+        case PRIO_EBADSEQ: return RAMBO_EBADSEQ;
+        default: return RAMBO_ECUDA;
+    }
+}
+
+// Staged view of a CSR batch on the device.  elem = bytes per data item.
+int stage_batch(rambo* h, const void* data, size_t elem, const uint64_t* offsets, const uint64_t* set_ids,
+                uint64_t n, int on_device, cudaStream_t s, BatchView& b, const void** d_data) {
+    uint64_t off0, offN;
+    if (on_device) {
+        CK(cudaMemcpyAsync(h->h_small, offsets, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h->h_small + 1, offsets + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        off0 = h->h_small[0];
+        offN = h->h_small[1];
+    } else {
+        off0 = offsets[0];
+        offN = offsets[n];
+    }
+    if (offN < off0) {
+        h->last_err_item = 0;
+        return RAMBO_EINVAL;
+    }
+    const uint64_t total = offN - off0;
+    b.off0 = off0;
+    b.total = total;
+    b.n = n;
+    if (on_device) {
+        b.offsets = offsets;
+        b.set_ids = set_ids;
+        *d_data = static_cast<const uint8_t*>(data) + off0 * elem;
+    } else {
+        RK(h->in_off.ensure(n + 1));
+        CK(cudaMemcpyAsync(h->in_off.p, offsets, (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+        b.offsets = h->in_off.p;
+        if (set_ids) {
+            RK(h->in_ids.ensure(n));
+            CK(cudaMemcpyAsync(h->in_ids.p, set_ids, n * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+            b.set_ids = h->in_ids.p;
+        } else {
+            b.set_ids = nullptr;
+        }
+        RK(h->in_data.ensure(total * elem + 16));
+        if (total)
+            CK(cudaMemcpyAsync(h->in_data.p, static_cast<const uint8_t*>(data) + off0 * elem, total * elem,
+                               cudaMemcpyHostToDevice, s));
+        *d_data = h->in_data.p;
+    }
+    return RAMBO_OK;
+}
+
+int pack_bases(rambo* h, BatchView& b, const void* d_bases, cudaStream_t s) {
+    const uint64_t n_words = b.total / 32 + 2;  // one spare word for windows crossing the last word
+    RK(h->packed.ensure(n_words));
+    CK(launch_pack(static_cast<const uint8_t*>(d_bases), b.total, h->packed.p, n_words, h->st, s));
+    CK(launch_resolve_bad_base(b, h->st, s));
+    b.packed = h->packed.p;
+    return RAMBO_OK;
+}
+
+int run_insert(rambo* h, int seq, const uint64_t* set_ids, const void* data, const uint64_t* offsets,
+               uint64_t n, uint32_t k, int on_device, cudaStream_t s) {
+    if (!h || !offsets || !set_ids || (!data && n)) return RAMBO_EINVAL;
+    if (seq && (k < 1 || k > 32)) return RAMBO_EINVAL;
+    if (n == 0) return RAMBO_OK;
+    CK(cudaSetDevice(h->device));
+    BatchView b{};
+    b.seq = seq;
+    b.k = k;
+    const void* d_data = nullptr;
+    RK(stage_batch(h, data, seq ? 1 : 8, offsets, set_ids, n, on_device, s, b, &d_data));
+    CK(launch_status_reset(h->st, s));
+    CK(launch_validate_batch(b, 0, h->K, h->st, s));
+    if (seq) RK(pack_bases(h, b, d_data, s));
+    else b.keys = static_cast<const uint64_t*>(d_data);
+    CK(launch_register(b, h->reg, h->st, s));
+    // keys in the batch and the bytes one pass over the input streams
+    const uint64_t n_keys = b.total;  // upper bound for sequences
+    const uint64_t in_bytes = seq ? b.total / 4 : b.total * 8;
+    const uint64_t index_bytes = h->index_words() * 4;
+    const uint64_t rows_total = (uint64_t)h->R * h->m;
+    uint64_t tile_rows = h->build_tile_bytes / ((uint64_t)h->S * 4);
+    if (tile_rows < 1) tile_rows = 1;
+    const uint64_t n_tiles = (rows_total + tile_rows - 1) / tile_rows;
+    const double untiled = (double)n_keys * h->R * h->eta * 64.0;      // a sector RMW per atomic
+    const double tiled = (double)n_tiles * in_bytes + 2.0 * index_bytes;  // input per tile + rows once
+    const bool use_tiles = h->build_mode == 1 || (h->build_mode == 0 && n_tiles > 1 && tiled < untiled);
+    if (use_tiles) {
+        for (uint64_t lo = 0; lo < rows_total; lo += tile_rows) {
+            uint64_t hi = lo + tile_rows < rows_total ? lo + tile_rows : rows_total;
+            CK(launch_insert(h->view(), h->hp, b, lo, hi, h->st, h->num_sms, s));
+        }
+    } else {
+        CK(launch_insert(h->view(), h->hp, b, 0, rows_total, h->st, h->num_sms, s));
+    }
+    CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return decode_err(h, h->h_st->err);
+}
+
+struct QueryDest {
+    int arena;              // 1: handle-owned arena
+    uint32_t* ids;          // caller buffers (into variants)
+    uint64_t ids_cap;
+    uint64_t* id_offsets;
+    uint64_t* needed;
+    const uint32_t** out_ids;  // arena variants
+    const uint64_t** out_off;
+};
+
+int resolve_tuning(rambo* h, uint64_t n, int& use_bitmap, QueryTuning& t) {
+    t.V = (int)h->cfg.words_per_lane;
+    t.G = (int)h->cfg.lanes_per_key;
+    t.warps_per_block = (int)h->cfg.warps_per_block;
+    t.set_stage = (int)h->cfg.set_stage;
+    use_bitmap = (h->mem_off && t.set_stage != 1 && (h->K + 31) / 32 <= 4096) ? 1 : 0;
+    const size_t smem =
+        (size_t)query_smem_words_per_warp(h->R, h->S, h->K, use_bitmap) * 4 * (size_t)t.warps_per_block;
+    int per_sm = query_max_blocks_per_sm(t.V, t.G, h->eta, t.warps_per_block, smem);
+    if (per_sm < 1) return RAMBO_EINVAL;
+    if (h->cfg.blocks_per_sm && (int)h->cfg.blocks_per_sm < per_sm) per_sm = (int)h->cfg.blocks_per_sm;
+    uint64_t blocks = (uint64_t)per_sm * h->num_sms;
+    uint64_t need = (n + t.warps_per_block - 1) / t.warps_per_block;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    t.blocks = (int)blocks;
+    uint64_t warps = blocks * t.warps_per_block;
+    uint64_t batch = n / (warps * 32);
+    if (batch < 1) batch = 1;
+    if (batch > 16) batch = 16;
+    t.batch = (int)batch;
+    return RAMBO_OK;
+}
+
+int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint64_t n, uint32_t k,
+              int on_device, cudaStream_t s, QueryDest& d) {
+    if (!h || !offsets || (!data && n)) return RAMBO_EINVAL;
+    if (seq && (k < 1 || k > 32)) return RAMBO_EINVAL;
+    CK(cudaSetDevice(h->device));
+    h->last = rambo_query_stats_t{};
+    h->launches = 0;
+    if (n == 0) {
+        if (d.arena) {
+            if (on_device) {
+                RK(h->id_off.ensure(1));
+                CK(cudaMemsetAsync(h->id_off.p, 0, sizeof(uint64_t), s));
+                CK(cudaStreamSynchronize(s));
+                *d.out_off = h->id_off.p;
+                *d.out_ids = reinterpret_cast<const uint32_t*>(h->ids.p);
+            } else {
+                RK(h->h_id_off.ensure(1));
+                h->h_id_off.p[0] = 0;
+                *d.out_off = h->h_id_off.p;
+                *d.out_ids = h->h_ids.p;
+            }
+        } else if (on_device) {
+            CK(cudaMemsetAsync(d.id_offsets, 0, sizeof(uint64_t), s));
+            CK(cudaStreamSynchronize(s));
+        } else {
+            d.id_offsets[0] = 0;
+        }
+        if (d.needed) *d.needed = 0;
+        return RAMBO_OK;
+    }
+    BatchView b{};
+    b.seq = seq;
+    b.k = k;
+    const void* d_data = nullptr;
+    RK(stage_batch(h, data, seq ? 1 : 8, offsets, nullptr, n, on_device, s, b, &d_data));
+    int use_bitmap = 0;
+    QueryTuning t{};
+    RK(resolve_tuning(h, n, use_bitmap, t));
+    RK(h->qcount.ensure(n));
+    RK(h->qstart.ensure(n));
+    RK(h->scan_tmp.ensure(scan_tmp_words(n)));
+    if (h->stage.cap < (1u << 20)) RK(h->stage.ensure(1u << 20));
+    // device-side destination of the CSR offsets
+    uint64_t* d_off;
+    if (!d.arena && on_device) {
+        d_off = d.id_offsets;
+    } else {
+        RK(h->id_off.ensure(n + 1));
+        d_off = h->id_off.p;
+    }
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        CK(cudaEventRecord(h->ev[0], s));
+        CK(launch_status_reset(h->st, s));
+        CK(launch_validate_batch(b, seq ? k : 1, h->K, h->st, s));
+        h->launches += 2;
+        if (seq) {
+            RK(pack_bases(h, b, d_data, s));
+            h->launches += 2;
+        } else {
+            b.keys = static_cast<const uint64_t*>(d_data);
+        }
+        QueryOut o{h->stage.p, h->stage.cap, h->qstart.p, h->qcount.p};
+        CK(cudaEventRecord(h->ev[1], s));
+        CK(launch_query(h->view(), h->hp, b, o, t, use_bitmap, h->st, s));
+        CK(cudaEventRecord(h->ev[2], s));
+        CK(launch_scan_counts(h->qcount.p, n, d_off, h->scan_tmp.p, h->scan_tmp.cap, s));
+        h->launches += 4;
+        CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h->h_small, d_off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        RK(decode_err(h, h->h_st->err));
+        if (h->h_st->cursor <= h->stage.cap) break;
+        if (attempt == 1) return RAMBO_ECUDA;  // the second run needs exactly the first's count
+        RK(h->stage.ensure(h->h_st->cursor + (h->h_st->cursor >> 3)));
+    }
+    const uint64_t total_ids = h->h_small[0];
+    h->last.n_queries = n;
+    h->last.keys_submitted = seq ? (b.total - n * (uint64_t)(k - 1)) : b.total;
+    h->last.keys_probed = h->h_st->keys_probed;
+    h->last.rows_read = h->last.keys_probed * h->R * h->eta;
+    h->last.n_results = total_ids;
+    CK(cudaEventElapsedTime(&h->last.query_kernel_ms, h->ev[1], h->ev[2]));
+    if (d.needed) *d.needed = total_ids;
+    if (!d.arena && total_ids > d.ids_cap) return RAMBO_ENOSPC;
+    QueryOut o{h->stage.p, h->stage.cap, h->qstart.p, h->qcount.p};
+    uint32_t* d_ids;
+    if (!d.arena && on_device) {
+        d_ids = d.ids;
+    } else {
+        RK(h->ids.ensure(total_ids + 1));
+        d_ids = h->ids.p;
+    }
+    CK(launch_gather(o, d_off, n, d_ids, h->st, s));
+    CK(cudaEventRecord(h->ev[3], s));
+    h->launches += 1;
+    h->last.kernel_launches = h->launches;
+    if (on_device) {
+        CK(cudaStreamSynchronize(s));
+        CK(cudaEventElapsedTime(&h->last.device_ms, h->ev[0], h->ev[3]));
+        if (d.arena) {
+            *d.out_ids = d_ids;
+            *d.out_off = d_off;
+        }
+        return RAMBO_OK;
+    }
+    uint32_t* hid;
+    uint64_t* hoff;
+    if (d.arena) {
+        RK(h->h_ids.ensure(total_ids + 1));
+        RK(h->h_id_off.ensure(n + 1));
+        hid = h->h_ids.p;
+        hoff = h->h_id_off.p;
+    } else {
+        hid = d.ids;
+        hoff = d.id_offsets;
+    }
+    CK(cudaMemcpyAsync(hoff, d_off, (n + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    if (total_ids) CK(cudaMemcpyAsync(hid, d_ids, total_ids * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaEventElapsedTime(&h->last.device_ms, h->ev[0], h->ev[3]));
+    if (d.arena) {
+        *d.out_ids = hid;
+        *d.out_off = hoff;
+    }
+    return RAMBO_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+int rambo_create(uint64_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, uint64_t seed, rambo_t** out) {
+    if (!out) return RAMBO_EINVAL;
+    *out = nullptr;
+    if (K < 1 || K > (1ull << 32) || B < 1 || B > RAMBO_MAX_B || R < 1 || R > RAMBO_MAX_R || eta < 1 ||
+        eta > RAMBO_MAX_ETA || m < 2 || m > (1ull << 32) || (m & (m - 1)))
+        return RAMBO_EINVAL;
+    rambo* h = new (std::nothrow) rambo();
+    if (!h) return RAMBO_ENOMEM;
+    h->K = K;
+    h->B = B;
+    h->R = R;
+    h->m = m;
+    h->eta = eta;
+    h->seed = seed;
+    while ((1ull << h->L) < m) ++h->L;
+    h->W = (B + 31) / 32;
+    h->S = stride_for(h->W);
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return map_cuda(e);
+    }
+    // hash parameters, drawn from SplitMix64 in the specified order
+    const uint64_t P = (1ull << 61) - 1;
+    uint64_t state = seed;
+    for (uint32_t r = 0; r < R; ++r) {
+        h->a[r] = 1 + splitmix_next(state) % (P - 1);
+        h->c[r] = splitmix_next(state) % P;
+    }
+    for (uint32_t r = 0; r < R; ++r)
+        for (uint32_t j = 0; j < eta; ++j) h->hp.s[r][j] = splitmix_next(state) | 1ull;
+    int rc = RAMBO_OK;
+    auto fail = [&](int code) {
+        free_handle(h);
+        return code;
+    };
+    if (cudaMalloc(&h->rows, h->index_words() * 4) != cudaSuccess) return fail(RAMBO_ENOMEM);
+    if (cudaMalloc(&h->phi, K * PHI_STRIDE * sizeof(uint16_t)) != cudaSuccess) return fail(RAMBO_ENOMEM);
+    if (cudaMalloc(&h->reg, ((K + 31) / 32) * 4) != cudaSuccess) return fail(RAMBO_ENOMEM);
+    if (cudaMalloc(&h->st, sizeof(DevStatus)) != cudaSuccess) return fail(RAMBO_ENOMEM);
+    if (cudaMallocHost(&h->h_st, sizeof(DevStatus)) != cudaSuccess) return fail(RAMBO_ENOMEM);
+    if (cudaMallocHost(&h->h_small, 8 * sizeof(uint64_t)) != cudaSuccess) return fail(RAMBO_ENOMEM);
+    for (auto& ev : h->ev)
+        if (cudaEventCreate(&ev) != cudaSuccess) return fail(RAMBO_ECUDA);
+    cudaStream_t s = 0;
+    if (cudaMemsetAsync(h->rows, 0, h->index_words() * 4, s) != cudaSuccess) return fail(RAMBO_ECUDA);
+    if (cudaMemsetAsync(h->reg, 0, ((K + 31) / 32) * 4, s) != cudaSuccess) return fail(RAMBO_ECUDA);
+    if (launch_phi_init(h->phi, K, R, B, h->a, h->c, s) != cudaSuccess) return fail(RAMBO_ECUDA);
+    if (launch_status_reset(h->st, s) != cudaSuccess) return fail(RAMBO_ECUDA);
+    // members of every cell, for the sparse set stage (skipped for huge K)
+    const uint64_t cells = (uint64_t)R * B;
+    if ((uint64_t)R * K * 4 <= (1ull << 30)) {
+        if (cudaMalloc(&h->mem_off, (cells + 1 + scan_tmp_words(cells)) * sizeof(uint64_t)) != cudaSuccess ||
+            cudaMalloc(&h->mem_ids, (uint64_t)R * K * sizeof(uint32_t)) != cudaSuccess)
+            return fail(RAMBO_ENOMEM);
+        rc = h->fill.ensure(cells);
+        if (rc) return fail(rc);
+        if (launch_members(h->view(), h->mem_off, h->mem_ids, h->fill.p, s) != cudaSuccess)
+            return fail(RAMBO_ECUDA);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(RAMBO_ECUDA);
+    default_config(h);
+    *out = h;
+    return RAMBO_OK;
+}
+
+void rambo_destroy(rambo_t* h) { free_handle(h); }
+
+int rambo_get_info(const rambo_t* h, rambo_info_t* out) {
+    if (!h || !out) return RAMBO_EINVAL;
+    out->K = h->K;
+    out->B = h->B;
+    out->R = h->R;
+    out->eta = h->eta;
+    out->L = h->L;
+    out->m = h->m;
+    out->seed = h->seed;
+    out->row_words = h->W;
+    out->row_stride = h->S;
+    out->index_bytes = h->index_words() * 4;
+    std::vector<uint32_t> regw((h->K + 31) / 32);
+    if (cudaMemcpy(regw.data(), h->reg, regw.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return RAMBO_ECUDA;
+    uint64_t n = 0;
+    for (uint32_t w : regw) n += (uint64_t)__builtin_popcount(w);
+    out->n_registered = n;
+    return RAMBO_OK;
+}
+
+int rambo_insert_batch(rambo_t* h, const uint64_t* set_ids, const uint64_t* keys, const uint64_t* offsets,
+                       uint64_t n_sets, int on_device, void* stream) {
+    return run_insert(h, 0, set_ids, keys, offsets, n_sets, 0, on_device, (cudaStream_t)stream);
+}
+
+int rambo_insert_seq_batch(rambo_t* h, const uint64_t* set_ids, const uint8_t* bases, const uint64_t* offsets,
+                           uint64_t n_sets, uint32_t k, int on_device, void* stream) {
+    return run_insert(h, 1, set_ids, bases, offsets, n_sets, k, on_device, (cudaStream_t)stream);
+}
+
+int rambo_query_batch(rambo_t* h, const uint64_t* keys, const uint64_t* offsets, uint64_t n_queries, int on_device,
+                      const uint32_t** ids, const uint64_t** id_offsets, void* stream) {
+    if (!ids || !id_offsets) return RAMBO_EINVAL;
+    QueryDest d{1, nullptr, 0, nullptr, nullptr, ids, id_offsets};
+    return run_query(h, 0, keys, offsets, n_queries, 0, on_device, (cudaStream_t)stream, d);
+}
+
+int rambo_query_seq_batch(rambo_t* h, const uint8_t* bases, const uint64_t* offsets, uint64_t n_queries, uint32_t k,
+                          int on_device, const uint32_t** ids, const uint64_t** id_offsets, void* stream) {
+    if (!ids || !id_offsets) return RAMBO_EINVAL;
+    QueryDest d{1, nullptr, 0, nullptr, nullptr, ids, id_offsets};
+    return run_query(h, 1, bases, offsets, n_queries, k, on_device, (cudaStream_t)stream, d);
+}
+
+int rambo_query_batch_into(rambo_t* h, const uint64_t* keys, const uint64_t* offsets, uint64_t n_queries,
+                           int on_device, uint32_t* ids, uint64_t ids_cap, uint64_t* id_offsets, uint64_t* needed,
+                           void* stream) {
+    if (!id_offsets || (!ids && ids_cap)) return RAMBO_EINVAL;
+    QueryDest d{0, ids, ids_cap, id_offsets, needed, nullptr, nullptr};
+    return run_query(h, 0, keys, offsets, n_queries, 0, on_device, (cudaStream_t)stream, d);
+}
+
+int rambo_query_seq_batch_into(rambo_t* h, const uint8_t* bases, const uint64_t* offsets, uint64_t n_queries,
+                               uint32_t k, int on_device, uint32_t* ids, uint64_t ids_cap, uint64_t* id_offsets,
+                               uint64_t* needed, void* stream) {
+    if (!id_offsets || (!ids && ids_cap)) return RAMBO_EINVAL;
+    QueryDest d{0, ids, ids_cap, id_offsets, needed, nullptr, nullptr};
+    return run_query(h, 1, bases, offsets, n_queries, k, on_device, (cudaStream_t)stream, d);
+}
+
+int rambo_export_index(const rambo_t* h, uint32_t* host_words, uint64_t n_words) {
+    if (!h || !host_words || n_words != h->index_words()) return RAMBO_EINVAL;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpy(host_words, h->rows, n_words * 4, cudaMemcpyDeviceToHost));
+    return RAMBO_OK;
+}
+
+int rambo_export_registered(const rambo_t* h, uint32_t* host_words, uint64_t n_words) {
+    if (!h || !host_words || n_words != (h->K + 31) / 32) return RAMBO_EINVAL;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpy(host_words, h->reg, n_words * 4, cudaMemcpyDeviceToHost));
+    return RAMBO_OK;
+}
+
+int rambo_export_partition(const rambo_t* h, uint16_t* host_phi, uint64_t n) {
+    if (!h || !host_phi || n != h->K * h->R) return RAMBO_EINVAL;
+    CK(cudaSetDevice(h->device));
+    std::vector<uint16_t> tmp(h->K * PHI_STRIDE);
+    CK(cudaMemcpy(tmp.data(), h->phi, tmp.size() * 2, cudaMemcpyDeviceToHost));
+    for (uint64_t i = 0; i < h->K; ++i)
+        for (uint32_t r = 0; r < h->R; ++r) host_phi[i * h->R + r] = tmp[i * PHI_STRIDE + r];
+    return RAMBO_OK;
+}
+
+int rambo_cell_popcount(const rambo_t* h, uint64_t* host_out, void* stream) {
+    if (!h || !host_out) return RAMBO_EINVAL;
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t cells = (uint64_t)h->R * h->B;
+    unsigned long long* d = nullptr;
+    CK(cudaMalloc(&d, cells * sizeof(unsigned long long)));
+    cudaError_t e = cudaMemsetAsync(d, 0, cells * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = launch_cell_popcount(h->view(), d, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, d, cells * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    return map_cuda(e);
+}
+
+int rambo_last_query_stats(const rambo_t* h, rambo_query_stats_t* out) {
+    if (!h || !out) return RAMBO_EINVAL;
+    *out = h->last;
+    return RAMBO_OK;
+}
+
+int rambo_get_query_config(const rambo_t* h, rambo_query_config_t* out) {
+    if (!h || !out) return RAMBO_EINVAL;
+    *out = h->cfg;
+    return RAMBO_OK;
+}
+
+int rambo_set_query_config(rambo_t* h, const rambo_query_config_t* cfg) {
+    if (!h || !cfg) return RAMBO_EINVAL;
+    if (!query_config_supported((int)cfg->words_per_lane, (int)cfg->lanes_per_key, h->S)) return RAMBO_EINVAL;
+    if (cfg->warps_per_block < 1 || cfg->warps_per_block > 8) return RAMBO_EINVAL;
+    if (cfg->set_stage > 2) return RAMBO_EINVAL;
+    if (cfg->set_stage == 2 && !h->mem_off) return RAMBO_EINVAL;
+    h->cfg = *cfg;
+    return RAMBO_OK;
+}
+
+int rambo_list_query_configs(const rambo_t* h, rambo_query_config_t* out, int cap) {
+    if (!h) return RAMBO_EINVAL;
+    static const int vg[][2] = {{1, 1}, {2, 1}, {1, 2}, {4, 1}, {2, 2}, {4, 2},
+                                {2, 4}, {4, 4}, {2, 8}, {4, 8}, {4, 16}, {4, 32}};
+    static const int wpb[] = {2, 4, 8};
+    int n = 0;
+    for (auto& p : vg) {
+        if (!query_config_supported(p[0], p[1], h->S)) continue;
+        for (int w : wpb) {
+            if (out && n < cap) {
+                out[n].words_per_lane = (uint32_t)p[0];
+                out[n].lanes_per_key = (uint32_t)p[1];
+                out[n].warps_per_block = (uint32_t)w;
+                out[n].blocks_per_sm = 0;
+                out[n].set_stage = 0;
+            }
+            ++n;
+        }
+    }
+    return n;
+}
+
+int rambo_set_build_tiling(rambo_t* h, uint64_t tile_bytes, int mode) {
+    if (!h || mode < 0 || mode > 2) return RAMBO_EINVAL;
+    if (tile_bytes) {
+        if (tile_bytes < (uint64_t)h->S * 4) return RAMBO_EINVAL;
+        h->build_tile_bytes = tile_bytes;
+    }
+    h->build_mode = mode;
+    return RAMBO_OK;
+}
+
+uint64_t rambo_last_error_item(const rambo_t* h) { return h ? h->last_err_item : 0; }
+
+// checkpoint: "RAMBOGB1", params, registered bitmap, rows
+int rambo_save(const rambo_t* h, const char* path) {
+    if (!h || !path) return RAMBO_EINVAL;
+    CK(cudaSetDevice(h->device));
+    FILE* f = fopen(path, "wb");
+    if (!f) return RAMBO_EIO;
+    uint64_t hdr[8] = {0x31424753424D4152ull, h->K, h->B, h->R, h->m, h->eta, h->seed, h->S};
+    bool ok = fwrite(hdr, sizeof(hdr), 1, f) == 1;
+    std::vector<uint32_t> buf((h->K + 31) / 32);
+    if (ok && cudaMemcpy(buf.data(), h->reg, buf.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess) ok = false;
+    if (ok) ok = fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+    const uint64_t chunk = 1ull << 24;  // words
+    buf.resize(chunk);
+    for (uint64_t w = 0; ok && w < h->index_words(); w += chunk) {
+        uint64_t c = h->index_words() - w < chunk ? h->index_words() - w : chunk;
+        if (cudaMemcpy(buf.data(), h->rows + w, c * 4, cudaMemcpyDeviceToHost) != cudaSuccess) ok = false;
+        if (ok) ok = fwrite(buf.data(), 4, c, f) == c;
+    }
+    if (fclose(f) != 0) ok = false;
+    return ok ? RAMBO_OK : RAMBO_EIO;
+}
+
+int rambo_load(const char* path, rambo_t** out) {
+    if (!path || !out) return RAMBO_EINVAL;
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return RAMBO_EIO;
+    uint64_t hdr[8];
+    if (fread(hdr, sizeof(hdr), 1, f) != 1 || hdr[0] != 0x31424753424D4152ull) {
+        fclose(f);
+        return RAMBO_EINVAL;
+    }
+    rambo_t* h = nullptr;
+    int rc = rambo_create(hdr[1], (uint32_t)hdr[2], (uint32_t)hdr[3], hdr[4], (uint32_t)hdr[5], hdr[6], &h);
+    if (rc) {
+        fclose(f);
+        return rc;
+    }
+    if (h->S != hdr[7]) {
+        fclose(f);
+        rambo_destroy(h);
+        return RAMBO_EINVAL;
+    }
+    bool ok = true;
+    std::vector<uint32_t> buf((h->K + 31) / 32);
+    ok = fread(buf.data(), 4, buf.size(), f) == buf.size();
+    if (ok && cudaMemcpy(h->reg, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) ok = false;
+    const uint64_t chunk = 1ull << 24;
+    buf.resize(chunk);
+    for (uint64_t w = 0; ok && w < h->index_words(); w += chunk) {
+        uint64_t c = h->index_words() - w < chunk ? h->index_words() - w : chunk;
+        ok = fread(buf.data(), 4, c, f) == c;
+        if (ok && cudaMemcpy(h->rows + w, buf.data(), c * 4, cudaMemcpyHostToDevice) != cudaSuccess) ok = false;
+    }
+    fclose(f);
+    if (!ok) {
+        rambo_destroy(h);
+        return RAMBO_EIO;
+    }
+    *out = h;
+    return RAMBO_OK;
+}
+
+int rambo_random_row_probe(const uint32_t* dev_buf, uint64_t n_rows, uint32_t row_words, uint64_t reads_per_thread,
+                           uint32_t blocks, uint32_t threads, uint64_t seed, float* ms, void* stream) {
+    if (!dev_buf || !ms || !blocks || !threads || threads > 256 || (n_rows & (n_rows - 1)) || !n_rows)
+        return RAMBO_EINVAL;
+    if (!(row_words == 1 || row_words == 2 || row_words % 4 == 0)) return RAMBO_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaMalloc(&sink, 4));
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess)
+        e = launch_random_rows(dev_buf, n_rows, row_words, reads_per_thread, seed, sink, (int)blocks, (int)threads, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    return map_cuda(e);
+}
+
+const char* rambo_strerror(int code) {
+    switch (code) {
+        case RAMBO_OK: return "ok";
+        case RAMBO_EINVAL: return "invalid argument";
+        case RAMBO_ERANGE: return "set ID out of range";
+        case RAMBO_EBADSEQ: return "bad sequence (byte outside ACGTacgt, or shorter than k)";
+        case RAMBO_ENOMEM: return "out of memory";
+        case RAMBO_ENOSPC: return "output buffer too small";
+        case RAMBO_ECUDA: return "CUDA error";
+        case RAMBO_ETIMEOUT: return "device wait timed out";
+        case RAMBO_EIO: return "file I/O error";
+        case RAMBO_ESTATE: return "invalid state";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// rambo_impl.cuh -- internal declarations shared by the librambo translation
+// units: device-side hash helpers, parameter blocks, kernel launchers.
+//
+// Everything here follows the hash/layout specification stated in
+// include/rambo.h; nothing is shared with the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rambo.h"
+
+namespace rgb {
+
+constexpr int RMAX = RAMBO_MAX_R;
+constexpr int EMAX = RAMBO_MAX_ETA;
+constexpr int PHI_STRIDE = 8;  // partition table row: 8 uint16 per set ID (16 B)
+constexpr unsigned FULL = 0xffffffffu;
+constexpr unsigned long long NO_ERR = ~0ull;
+
+// Device error word: (index << 8) | priority; the smallest value wins, so the
+// lowest-numbered bad item is reported.  Priorities, lowest first, follow the
+// order in which items are checked: set ID range, offsets, content.
+constexpr unsigned PRIO_ERANGE = 1;
+constexpr unsigned PRIO_EINVAL = 2;
+constexpr unsigned PRIO_EBADSEQ = 3;
+
+struct DevStatus {
+    unsigned long long err;          // see above; NO_ERR when clean
+    unsigned long long bad_pos;      // lowest position of a byte outside ACGTacgt
+    unsigned long long ticket;       // next query index handed out to a warp
+    unsigned long long cursor;       // staged result IDs handed out so far
+    unsigned long long keys_probed;  // keys whose rows were read
+    unsigned long long rows_read;    // row reads issued
+    unsigned long long spare[2];
+};
+
+// Position multipliers s_{r,j}, passed by value so every warp reads them from
+// the kernel-parameter bank (uniform across the warp).
+struct HashParams {
+    uint64_t s[RMAX][EMAX];
+};
+
+// SplitMix64's output finalizer (Steele, Lea, Flood 2014).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// phi_r(i) = ((a*i + c) mod (2^61-1)) mod B, for a < 2^61, c < 2^61, i < 2^32.
+// The 128-bit value a*i + c is folded with 2^64 = 8 and 2^61 = 1 (mod 2^61-1).
+__host__ __device__ __forceinline__ uint32_t partition_hash(uint64_t a, uint64_t c, uint64_t i,
+                                                            uint32_t B) {
+    const uint64_t P = (1ull << 61) - 1;
+    uint64_t lo = a * i;
+#ifdef __CUDA_ARCH__
+    uint64_t hi = __umul64hi(a, i);
+#else
+    uint64_t hi = (uint64_t)(((unsigned __int128)a * i) >> 64);
+#endif
+    lo += c;
+    hi += (lo < c) ? 1 : 0;
+    uint64_t h8 = hi << 3;               // hi < 2^29 here, so no bits are lost
+    h8 = (h8 & P) + (h8 >> 61);
+    uint64_t t = (lo & P) + (lo >> 61) + h8;  // < 2^63
+    t = (t & P) + (t >> 61);
+    if (t >= P) t -= P;
+    return (uint32_t)(t % B);
+}
+
+// Key of the k-mer whose first base is base number p of a 2-bit packed stream
+// (32 bases per word, base 32w+t in bits 63-2t..62-2t of word w).  Reads word
+// p/32 and, when the window crosses into it, word p/32 + 1.
+__device__ __forceinline__ uint64_t kmer_at(const uint64_t* __restrict__ packed, uint64_t p,
+                                            uint32_t k) {
+    const uint64_t wi = p >> 5;
+    const uint32_t o = (uint32_t)(p & 31) * 2;
+    uint64_t win = __ldg(packed + wi) << o;
+    if (o) win |= __ldg(packed + wi + 1) >> (64 - o);
+    return win >> (64 - 2 * k);
+}
+
+__device__ __forceinline__ void record_error(DevStatus* st, uint64_t index, unsigned prio) {
+    atomicMin(&st->err, (unsigned long long)((index << 8) | prio));
+}
+
+// ---------------------------------------------------------------------------
+// parameter blocks
+// ---------------------------------------------------------------------------
+
+struct IndexView {
+    uint32_t* rows;        // [R][m][S] words
+    uint64_t m;            // rows per table
+    uint32_t R, eta, shift;  // shift = 64 - L
+    uint32_t S, W;         // row stride / words holding bits
+    uint64_t K;
+    uint32_t B;
+    const uint16_t* phi;   // [K][PHI_STRIDE]
+    uint32_t* reg;         // ceil(K/32) words
+    const uint64_t* mem_off;  // [R*B + 1] offsets of each cell's members (sparse stage)
+    const uint32_t* mem_ids;  // members of each cell (unordered)
+};
+
+struct BatchView {
+    int seq;                       // 0: 64-bit keys, 1: packed DNA
+    const uint64_t* keys;          // item data, index 0 = offsets[0]
+    const uint64_t* packed;        // packed bases, base 0 = offsets[0]
+    const uint64_t* offsets;       // n+1 absolute offsets
+    uint64_t off0;                 // offsets[0]
+    uint64_t total;                // offsets[n] - offsets[0]
+    uint64_t n;                    // items
+    uint32_t k;
+    const uint64_t* set_ids;       // insert batches only
+};
+
+struct QueryOut {
+    uint32_t* stage;       // staged IDs (arena)
+    uint64_t stage_cap;
+    uint64_t* qstart;      // per query: first staged ID
+    uint32_t* qcount;      // per query: number of IDs
+};
+
+struct QueryTuning {
+    int V, G;              // words per lane, lanes per key
+    int warps_per_block;
+    int blocks;            // grid size
+    int set_stage;         // 1 dense, 2 sparse, 0 auto
+    int batch;             // queries taken per ticket
+};
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+
+// k_util.cu
+cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s);
+cudaError_t launch_phi_init(uint16_t* phi, uint64_t K, uint32_t R, uint32_t B, const uint64_t* a,
+                            const uint64_t* c, cudaStream_t s);
+cudaError_t launch_validate_batch(const BatchView& b, uint64_t min_len, uint64_t K, DevStatus* st,
+                                  cudaStream_t s);
+cudaError_t launch_pack(const uint8_t* bases, uint64_t total, uint64_t* packed, uint64_t n_words,
+                        DevStatus* st, cudaStream_t s);
+cudaError_t launch_resolve_bad_base(const BatchView& b, DevStatus* st, cudaStream_t s);
+cudaError_t launch_register(const BatchView& b, uint32_t* reg, DevStatus* st, cudaStream_t s);
+cudaError_t launch_scan_counts(const uint32_t* counts, uint64_t n, uint64_t* offsets,
+                               uint64_t* tmp, uint64_t tmp_words, cudaStream_t s);
+uint64_t scan_tmp_words(uint64_t n);
+cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_t n, uint32_t* ids,
+                          const DevStatus* st, cudaStream_t s);
+cudaError_t launch_cell_popcount(const IndexView& ix, unsigned long long* out, cudaStream_t s);
+cudaError_t launch_members(const IndexView& ix, uint64_t* mem_off, uint32_t* mem_ids,
+                           uint32_t* fill, cudaStream_t s);
+
+// k_build.cu
+cudaError_t launch_insert(const IndexView& ix, const HashParams& hp, const BatchView& b,
+                          uint64_t row_lo, uint64_t row_hi, DevStatus* st, int num_sms,
+                          cudaStream_t s);
+
+// k_query*.cu
+bool query_config_supported(int V, int G, uint32_t S);
+uint32_t query_smem_words_per_warp(uint32_t R, uint32_t S, uint64_t K, int use_bitmap);
+int query_max_blocks_per_sm(int V, int G, uint32_t eta, int warps_per_block, size_t smem_per_block);
+cudaError_t launch_query(const IndexView& ix, const HashParams& hp, const BatchView& b, const QueryOut& o,
+                         const QueryTuning& t, int use_bitmap, DevStatus* st, cudaStream_t s);
+
+// k_roofline.cu
+cudaError_t launch_random_rows(const uint32_t* buf, uint64_t n_rows, uint32_t row_words,
+                               uint64_t reads_per_thread, uint64_t seed, uint32_t* sink,
+                               int blocks, int threads, cudaStream_t s);
+
+}  // namespace rgb

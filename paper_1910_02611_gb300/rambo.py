@@ -1,0 +1,350 @@
+"""Python binding of librambo (include/rambo.h): argument marshalling only.
+
+Every step of insertion and query runs in the library's CUDA kernels.  Inputs
+are numpy arrays (host memory) or CUDA torch tensors (device memory); PyTorch
+is used only to hold device buffers and to name the current stream.  There is
+no CPU fallback: if the library is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ERANGE, EBADSEQ, ENOMEM, ENOSPC, ECUDA, ETIMEOUT, EIO, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+
+_u64, _u32, _u16, _i32, _p = C.c_uint64, C.c_uint32, C.c_uint16, C.c_int, C.c_void_p
+
+
+class RamboInfo(C.Structure):
+    _fields_ = [("K", _u64), ("B", _u32), ("R", _u32), ("eta", _u32), ("L", _u32), ("m", _u64), ("seed", _u64),
+                ("row_words", _u32), ("row_stride", _u32), ("index_bytes", _u64), ("n_registered", _u64)]
+
+
+class QueryStats(C.Structure):
+    _fields_ = [("n_queries", _u64), ("keys_submitted", _u64), ("keys_probed", _u64), ("rows_read", _u64),
+                ("n_results", _u64), ("kernel_launches", _u64), ("query_kernel_ms", C.c_float),
+                ("device_ms", C.c_float)]
+
+
+class QueryConfig(C.Structure):
+    _fields_ = [("lanes_per_key", _u32), ("words_per_lane", _u32), ("warps_per_block", _u32),
+                ("blocks_per_sm", _u32), ("set_stage", _u32)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+# every symbol the header declares, with (restype, argtypes)
+SIGNATURES = {
+    "rambo_create": (_i32, [_u64, _u32, _u32, _u64, _u32, _u64, C.POINTER(_p)]),
+    "rambo_destroy": (None, [_p]),
+    "rambo_get_info": (_i32, [_p, C.POINTER(RamboInfo)]),
+    "rambo_insert_batch": (_i32, [_p, _p, _p, _p, _u64, _i32, _p]),
+    "rambo_insert_seq_batch": (_i32, [_p, _p, _p, _p, _u64, _u32, _i32, _p]),
+    "rambo_query_batch": (_i32, [_p, _p, _p, _u64, _i32, C.POINTER(_p), C.POINTER(_p), _p]),
+    "rambo_query_seq_batch": (_i32, [_p, _p, _p, _u64, _u32, _i32, C.POINTER(_p), C.POINTER(_p), _p]),
+    "rambo_query_batch_into": (_i32, [_p, _p, _p, _u64, _i32, _p, _u64, _p, C.POINTER(_u64), _p]),
+    "rambo_query_seq_batch_into": (_i32, [_p, _p, _p, _u64, _u32, _i32, _p, _u64, _p, C.POINTER(_u64), _p]),
+    "rambo_export_index": (_i32, [_p, _p, _u64]),
+    "rambo_export_registered": (_i32, [_p, _p, _u64]),
+    "rambo_export_partition": (_i32, [_p, _p, _u64]),
+    "rambo_cell_popcount": (_i32, [_p, _p, _p]),
+    "rambo_last_query_stats": (_i32, [_p, C.POINTER(QueryStats)]),
+    "rambo_get_query_config": (_i32, [_p, C.POINTER(QueryConfig)]),
+    "rambo_set_query_config": (_i32, [_p, C.POINTER(QueryConfig)]),
+    "rambo_list_query_configs": (_i32, [_p, _p, _i32]),
+    "rambo_set_build_tiling": (_i32, [_p, _u64, _i32]),
+    "rambo_save": (_i32, [_p, C.c_char_p]),
+    "rambo_load": (_i32, [C.c_char_p, C.POINTER(_p)]),
+    "rambo_random_row_probe": (_i32, [_p, _u64, _u32, _u64, _u32, _u32, _u64, C.POINTER(C.c_float), _p]),
+    "rambo_last_error_item": (_u64, [_p]),
+    "rambo_strerror": (C.c_char_p, [_i32]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Loads librambo.so (building it with nvcc first if it is missing)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"librambo.so is not built ({_build.LIB}); run __graft_entry__.build()")
+        L = C.CDLL(_build.LIB)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class RamboError(RuntimeError):
+    def __init__(self, code: int, where: str = "", item: int | None = None):
+        msg = load_library().rambo_strerror(code).decode()
+        super().__init__(f"{where}: {msg} ({code})" + (f" at item {item}" if item is not None else ""))
+        self.code = code
+        self.item = item
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _is_cuda_tensor(x) -> bool:
+    try:
+        torch = _torch()
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(x, torch.Tensor) and x.is_cuda
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        try:
+            torch = _torch()
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:  # pragma: no cover
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class _CudaArray:
+    """Exposes a device pointer through __cuda_array_interface__ so torch can
+    copy it into a tensor it owns."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
+def _device_copy(ptr: int, n: int, dtype: str):
+    torch = _torch()
+    tdt = {"<u4": torch.int32, "<u8": torch.int64}[dtype]
+    if n == 0:
+        return torch.zeros(0, dtype=tdt, device="cuda")
+    t = torch.as_tensor(_CudaArray(ptr, n, "<i4" if dtype == "<u4" else "<i8"), device="cuda")
+    return t.clone()
+
+
+def _host_arr(x, dtype) -> np.ndarray:
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+class Rambo:
+    """A RAMBO index resident in GPU memory (Secs. 2-3 of arXiv 1910.02611)."""
+
+    def __init__(self, K: int, B: int, R: int, m: int, eta: int, seed: int = 42, *, _handle=None):
+        L = load_library()
+        if _handle is None:
+            h = _p()
+            rc = L.rambo_create(K, B, R, m, eta, seed, C.byref(h))
+            if rc:
+                raise RamboError(rc, "rambo_create")
+            self._h = h
+        else:
+            self._h = _handle
+        info = self.info()
+        self.K, self.B, self.R, self.m, self.eta, self.seed = info.K, info.B, info.R, info.m, info.eta, info.seed
+        self.row_stride = info.row_stride
+        self.row_words = info.row_words
+
+    @classmethod
+    def load(cls, path: str) -> "Rambo":
+        h = _p()
+        rc = load_library().rambo_load(path.encode(), C.byref(h))
+        if rc:
+            raise RamboError(rc, "rambo_load")
+        return cls(0, 0, 0, 0, 0, _handle=h)
+
+    def close(self) -> None:
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load_library().rambo_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int, where: str):
+        if rc:
+            item = None
+            if rc in (EINVAL, ERANGE, EBADSEQ):
+                item = int(load_library().rambo_last_error_item(self._h))
+            raise RamboError(rc, where, item)
+
+    # -- info ---------------------------------------------------------------
+    def info(self) -> RamboInfo:
+        out = RamboInfo()
+        rc = load_library().rambo_get_info(self._h, C.byref(out))
+        if rc:
+            raise RamboError(rc, "rambo_get_info")
+        return out
+
+    # -- Algorithm 1 --------------------------------------------------------------
+    def insert(self, set_ids, data, offsets, kind: str = "keys", k: int = 31, stream=None) -> None:
+        """Inserts sets (keys, or DNA whose k-mers are the keys) given in CSR form."""
+        L = load_library()
+        dev = _is_cuda_tensor(data)
+        if dev:
+            ids_p, data_p, off_p = set_ids.data_ptr(), data.data_ptr(), offsets.data_ptr()
+            n = offsets.numel() - 1
+            keep = None
+        else:
+            ids = _host_arr(set_ids, np.uint64)
+            d = _host_arr(data, np.uint64 if kind == "keys" else np.uint8)
+            off = _host_arr(offsets, np.uint64)
+            keep = (ids, d, off)
+            ids_p, data_p, off_p = ids.ctypes.data, d.ctypes.data, off.ctypes.data
+            n = off.size - 1
+        s = _stream_handle(stream)
+        if kind == "keys":
+            rc = L.rambo_insert_batch(self._h, ids_p, data_p, off_p, n, int(dev), s)
+        else:
+            rc = L.rambo_insert_seq_batch(self._h, ids_p, data_p, off_p, n, k, int(dev), s)
+        del keep
+        self._check(rc, "insert")
+
+    # -- Algorithm 2 ----------------------------------------------------------------
+    def query(self, data, offsets, kind: str = "keys", k: int = 31, stream=None):
+        """Returns (ids, id_offsets): numpy arrays for host inputs, torch CUDA
+        tensors for device inputs.  Query q's answer is ids[id_offsets[q]:id_offsets[q+1]]."""
+        L = load_library()
+        dev = _is_cuda_tensor(data)
+        if dev:
+            data_p, off_p, n = data.data_ptr(), offsets.data_ptr(), offsets.numel() - 1
+            keep = None
+        else:
+            d = _host_arr(data, np.uint64 if kind == "keys" else np.uint8)
+            off = _host_arr(offsets, np.uint64)
+            keep = (d, off)
+            data_p, off_p, n = d.ctypes.data, off.ctypes.data, off.size - 1
+        ids_p, offo_p = _p(), _p()
+        s = _stream_handle(stream)
+        if kind == "keys":
+            rc = L.rambo_query_batch(self._h, data_p, off_p, n, int(dev), C.byref(ids_p), C.byref(offo_p), s)
+        else:
+            rc = L.rambo_query_seq_batch(self._h, data_p, off_p, n, k, int(dev), C.byref(ids_p), C.byref(offo_p), s)
+        del keep
+        self._check(rc, "query")
+        if dev:
+            off_t = _device_copy(offo_p.value, n + 1, "<u8")
+            total = int(off_t[-1].item())
+            return _device_copy(ids_p.value or 0, total, "<u4"), off_t
+        offs = np.ctypeslib.as_array(C.cast(offo_p, C.POINTER(_u64)), shape=(n + 1,)).copy()
+        total = int(offs[-1])
+        if total == 0:
+            return np.zeros(0, np.uint32), offs
+        ids = np.ctypeslib.as_array(C.cast(ids_p, C.POINTER(_u32)), shape=(total,)).copy()
+        return ids, offs
+
+    def query_into(self, data, offsets, ids_out, id_offsets_out, kind: str = "keys", k: int = 31, stream=None) -> int:
+        """Writes results into caller buffers (numpy or CUDA tensors).  Returns
+        the number of IDs; raises RamboError(ENOSPC) if ids_out is too small."""
+        L = load_library()
+        dev = _is_cuda_tensor(data)
+        needed = _u64(0)
+        s = _stream_handle(stream)
+        if dev:
+            args = (data.data_ptr(), offsets.data_ptr(), offsets.numel() - 1)
+            ids_p, cap, oo = ids_out.data_ptr(), ids_out.numel(), id_offsets_out.data_ptr()
+        else:
+            d = _host_arr(data, np.uint64 if kind == "keys" else np.uint8)
+            off = _host_arr(offsets, np.uint64)
+            args = (d.ctypes.data, off.ctypes.data, off.size - 1)
+            assert ids_out.dtype == np.uint32 and id_offsets_out.dtype == np.uint64
+            ids_p, cap, oo = ids_out.ctypes.data, ids_out.size, id_offsets_out.ctypes.data
+        if kind == "keys":
+            rc = L.rambo_query_batch_into(self._h, *args, int(dev), ids_p, cap, oo, C.byref(needed), s)
+        else:
+            rc = L.rambo_query_seq_batch_into(self._h, *args, k, int(dev), ids_p, cap, oo, C.byref(needed), s)
+        self._check(rc, "query_into")
+        return int(needed.value)
+
+    def last_query_stats(self) -> dict:
+        st = QueryStats()
+        self._check(load_library().rambo_last_query_stats(self._h, C.byref(st)), "last_query_stats")
+        return {f: (float(getattr(st, f)) if f.endswith("_ms") else int(getattr(st, f))) for f, _ in st._fields_}
+
+    # -- configuration ------------------------------------------------------------
+    def get_config(self) -> dict:
+        c = QueryConfig()
+        load_library().rambo_get_query_config(self._h, C.byref(c))
+        return c.as_dict()
+
+    def set_config(self, **kw) -> None:
+        cur = self.get_config()
+        cur.update(kw)
+        c = QueryConfig(**cur)
+        self._check(load_library().rambo_set_query_config(self._h, C.byref(c)), "set_config")
+
+    def set_build_tiling(self, tile_bytes: int = 0, mode: int = 0) -> None:
+        """mode 0 auto, 1 always window by window (L2-resident slices of
+        tile_bytes), 2 single pass."""
+        self._check(load_library().rambo_set_build_tiling(self._h, tile_bytes, mode), "set_build_tiling")
+
+    def list_configs(self) -> list[dict]:
+        L = load_library()
+        n = L.rambo_list_query_configs(self._h, None, 0)
+        arr = (QueryConfig * max(n, 1))()
+        L.rambo_list_query_configs(self._h, C.cast(arr, _p), n)
+        return [arr[i].as_dict() for i in range(n)]
+
+    # -- inspection -----------------------------------------------------------------
+    def export_index(self) -> np.ndarray:
+        """Rows as uint32 [R, m, row_stride] (bit b of row (r,p) = bit p of cell b's filter)."""
+        n = self.R * self.m * self.row_stride
+        out = np.empty(n, np.uint32)
+        self._check(load_library().rambo_export_index(self._h, out.ctypes.data, n), "export_index")
+        return out.reshape(self.R, self.m, self.row_stride)
+
+    def export_registered(self) -> np.ndarray:
+        n = (self.K + 31) // 32
+        out = np.empty(n, np.uint32)
+        self._check(load_library().rambo_export_registered(self._h, out.ctypes.data, n), "export_registered")
+        return np.unpackbits(out.view(np.uint8), bitorder="little")[: self.K].astype(bool)
+
+    def export_partition(self) -> np.ndarray:
+        n = self.K * self.R
+        out = np.empty(n, np.uint16)
+        self._check(load_library().rambo_export_partition(self._h, out.ctypes.data, n), "export_partition")
+        return out.reshape(self.K, self.R)
+
+    def cell_popcount(self, stream=None) -> np.ndarray:
+        out = np.zeros(self.R * self.B, np.uint64)
+        self._check(load_library().rambo_cell_popcount(self._h, out.ctypes.data, _stream_handle(stream)),
+                    "cell_popcount")
+        return out.reshape(self.R, self.B)
+
+    def save(self, path: str) -> None:
+        self._check(load_library().rambo_save(self._h, path.encode()), "save")
+
+
+def random_row_probe(buf, n_rows: int, row_words: int, reads_per_thread: int, blocks: int, threads: int = 256,
+                     seed: int = 1, stream=None) -> float:
+    """Times the random-row read microbenchmark over a CUDA tensor; returns ms."""
+    ms = C.c_float(0)
+    rc = load_library().rambo_random_row_probe(buf.data_ptr(), n_rows, row_words, reads_per_thread, blocks, threads,
+                                               seed, C.byref(ms), _stream_handle(stream))
+    if rc:
+        raise RamboError(rc, "random_row_probe")
+    return float(ms.value)

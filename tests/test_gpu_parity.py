@@ -1,0 +1,304 @@
+"""GPU parity: the CUDA library (called through the C ABI) against the CPU
+oracle, element by element, on seeded synthetic workloads shaped like the
+paper's (scaled so the oracle finishes in seconds, with several tiles and
+ragged tails), plus edge cases.  Index bits, registered sets, the partition
+table and every query's ID list must be identical."""
+import numpy as np
+import pytest
+
+import synth
+from tests.parity import assert_index_equal, assert_partition_equal, assert_query_equal, build_pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    from oracle.oracle import Oracle
+    from paper_1910_02611_gb300 import Rambo
+
+    return Rambo, Oracle
+
+
+def _w(name, scale, **kw):
+    return synth.make(name, scale, **kw)
+
+
+WORKLOADS = {
+    "tiny_full": lambda: _w("tiny", 1.0),
+    "genome_small": lambda: _w("genome", 0.02, m=1 << 18),
+    "uneven_small": lambda: _w("uneven", 0.004, m=1 << 16, n_queries=3000),
+    "document_small": lambda: _w("document", 0.01, m=1 << 16),
+}
+
+
+@pytest.fixture(scope="module", params=list(WORKLOADS))
+def pair(request, mods):
+    Rambo, Oracle = mods
+    w = WORKLOADS[request.param]()
+    g, o = build_pair(w, Rambo, Oracle, insert_chunks=3)
+    yield w, g, o
+    g.close()
+
+
+def test_index_bits_identical(pair):
+    w, g, o = pair
+    assert_index_equal(g, o)
+    assert_partition_equal(g, o)
+
+
+def test_cell_popcount_identical(pair):
+    w, g, o = pair
+    assert np.array_equal(g.cell_popcount(), o.cell_popcount())
+
+
+def test_queries_identical_default_config(pair):
+    w, g, o = pair
+    assert_query_equal(g, o, w.queries, k=w.k)
+    st = g.last_query_stats()
+    assert st["keys_probed"] <= st["keys_submitted"]
+    assert st["rows_read"] == st["keys_probed"] * w.R * w.eta
+
+
+def test_queries_identical_every_kernel_config(pair):
+    w, g, o = pair
+    base = g.get_config()
+    q = w.queries.subset(np.arange(min(len(w.queries), 800)))
+    try:
+        for cfg in g.list_configs():
+            for stage in (1, 2):
+                g.set_config(**{**cfg, "set_stage": stage})
+                assert_query_equal(g, o, q, k=w.k)
+    finally:
+        g.set_config(**base)
+
+
+def test_device_inputs_match_host_inputs(pair):
+    import torch
+
+    w, g, o = pair
+    q = w.queries.subset(np.arange(min(len(w.queries), 500)))
+    hid, hoff = g.query(q.data, q.offsets, kind=q.kind, k=w.k)
+    dt = torch.from_numpy(q.data.view(np.int64) if q.kind == "keys" else q.data).cuda()
+    do = torch.from_numpy(q.offsets.view(np.int64)).cuda()
+    did, doff = g.query(dt, do, kind=q.kind, k=w.k)
+    assert np.array_equal(hoff, doff.cpu().numpy().view(np.uint64))
+    assert np.array_equal(hid, did.cpu().numpy().view(np.uint32))
+
+
+def test_query_into_and_nospc(pair):
+    from paper_1910_02611_gb300 import ENOSPC, RamboError
+
+    w, g, o = pair
+    q = w.queries.subset(np.arange(min(len(w.queries), 300)))
+    ids, off = g.query(q.data, q.offsets, kind=q.kind, k=w.k)
+    n = len(q)
+    out_ids = np.zeros(ids.size + 5, np.uint32)
+    out_off = np.zeros(n + 1, np.uint64)
+    got = g.query_into(q.data, q.offsets, out_ids, out_off, kind=q.kind, k=w.k)
+    assert got == ids.size
+    assert np.array_equal(out_off, off) and np.array_equal(out_ids[:got], ids)
+    if ids.size:
+        with pytest.raises(RamboError) as e:
+            g.query_into(q.data, q.offsets, np.zeros(ids.size - 1, np.uint32), out_off, kind=q.kind, k=w.k)
+        assert e.value.code == ENOSPC
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def _rand_seq(rng, n):
+    return np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, n)]
+
+
+@pytest.mark.parametrize("B,R,m,eta", [(1, 1, 1 << 10, 1), (33, 2, 2, 3), (100, 8, 1 << 12, 4), (320, 5, 1 << 11, 2),
+                                       (4096, 1, 1 << 8, 2), (7, 8, 1 << 14, 3)])
+def test_edge_parameters(mods, B, R, m, eta):
+    Rambo, Oracle = mods
+    rng = np.random.default_rng(B * 1000 + R)
+    K = 37  # not a multiple of 32
+    lens = rng.integers(0, 400, K)
+    lens[3] = 0   # empty set
+    lens[5] = 30  # shorter than k: registered, no k-mers
+    seqs = [_rand_seq(rng, int(n)) for n in lens]
+    bases = np.concatenate(seqs)
+    off = np.zeros(K + 1, np.uint64)
+    np.cumsum(lens, out=off[1:])
+    ids = rng.permutation(np.arange(K, dtype=np.uint64))  # sets inserted in shuffled ID order
+    perm_seqs = [seqs[int(i)] for i in ids]
+    pb = np.concatenate(perm_seqs)
+    poff = np.zeros(K + 1, np.uint64)
+    np.cumsum([s.size for s in perm_seqs], out=poff[1:])
+    g = Rambo(K + 3, B, R, m, eta, 7)  # capacity beyond the inserted IDs
+    o = Oracle(K + 3, B, R, m, eta, 7)
+    g.insert(ids, pb, poff, kind="seq", k=31)
+    o.insert_seq_batch(ids, pb, poff, 31)
+    assert_index_equal(g, o)
+    # queries: substrings of exactly k bases, long ones, lower case, fresh random
+    qs = []
+    for t in range(120):
+        i = int(rng.integers(0, K))
+        s = seqs[i]
+        if s.size >= 31 and t % 4:
+            a = int(rng.integers(0, s.size - 30))
+            b = int(rng.integers(a + 31, min(s.size, a + 200) + 1))
+            q = s[a:b].copy()
+        else:
+            q = _rand_seq(rng, int(rng.integers(31, 90)))
+        if t % 7 == 0:
+            q = np.frombuffer(bytes(q).lower(), np.uint8)
+        qs.append(q)
+    qd = np.concatenate(qs)
+    qo = np.zeros(len(qs) + 1, np.uint64)
+    np.cumsum([q.size for q in qs], out=qo[1:])
+    assert_query_equal(g, o, synth.Collection("seq", qd, qo), k=31)
+    # key queries of 1..6 keys, some repeated
+    keys = rng.integers(0, 1 << 62, 300, dtype=np.uint64)
+    g2 = Rambo(K, B, R, m, eta, 9)
+    o2 = Oracle(K, B, R, m, eta, 9)
+    koff = np.linspace(0, keys.size, K + 1).astype(np.uint64)
+    g2.insert(np.arange(K, dtype=np.uint64), keys, koff)
+    o2.insert_keys_batch(np.arange(K, dtype=np.uint64), keys, koff)
+    assert_index_equal(g2, o2)
+    ql = [np.concatenate([rng.choice(keys, int(rng.integers(1, 6))), rng.choice(keys, int(rng.integers(0, 2)))])
+          for _ in range(200)]
+    ql += [rng.integers(0, 1 << 62, 1, dtype=np.uint64) for _ in range(50)]
+    qk = np.concatenate(ql).astype(np.uint64)
+    qko = np.zeros(len(ql) + 1, np.uint64)
+    np.cumsum([q.size for q in ql], out=qko[1:])
+    assert_query_equal(g2, o2, synth.Collection("keys", qk, qko))
+
+
+def test_kmer_lengths_other_than_31(mods):
+    Rambo, Oracle = mods
+    rng = np.random.default_rng(5)
+    for k in (1, 5, 16, 32):
+        K, B, R, m, eta = 12, 9, 3, 1 << 12, 2
+        lens = rng.integers(k, 300, K)
+        bases = _rand_seq(rng, int(lens.sum()))
+        off = np.zeros(K + 1, np.uint64)
+        np.cumsum(lens, out=off[1:])
+        g = Rambo(K, B, R, m, eta, k)
+        o = Oracle(K, B, R, m, eta, k)
+        g.insert(np.arange(K, dtype=np.uint64), bases, off, kind="seq", k=k)
+        o.insert_seq_batch(np.arange(K, dtype=np.uint64), bases, off, k)
+        assert_index_equal(g, o)
+        qo = np.arange(0, 40 * 60 + 1, 60, dtype=np.uint64)
+        qd = bases[: int(qo[-1])]
+        assert_query_equal(g, o, synth.Collection("seq", qd.copy(), qo), k=k)
+
+
+def test_offsets_not_starting_at_zero_and_empty_batch(mods):
+    Rambo, Oracle = mods
+    rng = np.random.default_rng(6)
+    K = 20
+    keys = rng.integers(0, 1 << 62, 1000, dtype=np.uint64)
+    g = Rambo(K, 16, 3, 1 << 12, 2, 3)
+    o = Oracle(K, 16, 3, 1 << 12, 2, 3)
+    off = np.linspace(100, 900, K + 1).astype(np.uint64)  # uses keys[100:900]
+    g.insert(np.arange(K, dtype=np.uint64), keys, off)
+    o.insert_keys_batch(np.arange(K, dtype=np.uint64), keys, off)
+    assert_index_equal(g, o)
+    qo = np.arange(50, 251, 2, dtype=np.uint64)
+    assert_query_equal(g, o, synth.Collection("keys", keys, qo))
+    ids, offs = g.query(keys, np.array([7], np.uint64))  # no queries
+    assert ids.size == 0 and list(offs) == [0]
+    g.insert(np.zeros(0, np.uint64), keys, np.array([0], np.uint64))  # no sets: nothing happens
+    assert_index_equal(g, o)
+
+
+def test_errors_leave_the_index_unchanged(mods):
+    from paper_1910_02611_gb300 import EBADSEQ, EINVAL, ERANGE, RamboError
+
+    Rambo, Oracle = mods
+    rng = np.random.default_rng(8)
+    K = 10
+    g = Rambo(K, 8, 2, 1 << 10, 2, 1)
+    o = Oracle(K, 8, 2, 1 << 10, 2, 1)
+    seqs = _rand_seq(rng, 500)
+    off = np.array([0, 100, 250, 500], np.uint64)
+    g.insert(np.array([1, 2, 3], np.uint64), seqs, off, kind="seq")
+    o.insert_seq_batch(np.array([1, 2, 3], np.uint64), seqs, off, 31)
+    before = g.export_index().copy()
+
+    def expect(code, item, fn):
+        with pytest.raises(RamboError) as e:
+            fn()
+        assert e.value.code == code
+        if item is not None:
+            assert e.value.item == item
+
+    bad = seqs.copy()
+    bad[260] = ord("N")
+    expect(EBADSEQ, 2, lambda: g.insert(np.array([4, 5, 6], np.uint64), bad, off, kind="seq"))
+    expect(ERANGE, 1, lambda: g.insert(np.array([4, 10, 6], np.uint64), seqs, off, kind="seq"))
+    expect(EINVAL, 1, lambda: g.insert(np.array([4, 5, 6], np.uint64), seqs, np.array([0, 300, 250, 500], np.uint64),
+                                       kind="seq"))
+    assert np.array_equal(before, g.export_index())
+    assert not g.export_registered()[4]
+    # queries
+    qoff = np.array([0, 40, 100, 131], np.uint64)
+    expect(EBADSEQ, 1, lambda: g.query(bad[220:351], qoff, kind="seq"))  # bad base at 260-220=40 -> query 1
+    expect(EBADSEQ, 2, lambda: g.query(seqs, np.array([0, 40, 100, 120], np.uint64), kind="seq"))  # 20 < k
+    expect(EINVAL, 1, lambda: g.query(rng.integers(0, 9, 10, dtype=np.uint64), np.array([0, 3, 3, 10], np.uint64)))
+    expect(EINVAL, None, lambda: g.query(rng.integers(0, 9, 10, dtype=np.uint64), np.array([0, 5, 3, 10], np.uint64)))
+    # a good query afterwards still works
+    q = synth.Collection("seq", seqs[:200].copy(), np.array([0, 60, 200], np.uint64))
+    assert_query_equal(g, o, q)
+
+
+def test_duplicate_and_repeated_inserts(mods):
+    Rambo, Oracle = mods
+    rng = np.random.default_rng(9)
+    K = 40
+    keys = rng.integers(0, 1 << 62, 2000, dtype=np.uint64)
+    off = np.linspace(0, 2000, 21).astype(np.uint64)
+    ids = rng.integers(0, K, 20).astype(np.uint64)  # repeated IDs
+    g = Rambo(K, 12, 4, 1 << 13, 3, 5)
+    o = Oracle(K, 12, 4, 1 << 13, 3, 5)
+    for _ in range(2):  # inserting twice changes nothing
+        g.insert(ids, keys, off)
+    o.insert_keys_batch(ids, keys, off)
+    assert_index_equal(g, o)
+
+
+def test_save_load_roundtrip(mods, tmp_path):
+    Rambo, Oracle = mods
+    w = synth.make("genome", 0.01, m=1 << 14)
+    g = Rambo(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    g.insert(w.sets.ids, w.sets.data, w.sets.offsets, kind="seq")
+    p = str(tmp_path / "idx.rambo")
+    g.save(p)
+    h = Rambo.load(p)
+    assert np.array_equal(g.export_index(), h.export_index())
+    assert np.array_equal(g.export_registered(), h.export_registered())
+    a = g.query(w.queries.data, w.queries.offsets, kind="seq")
+    b = h.query(w.queries.data, w.queries.offsets, kind="seq")
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("tile_bytes", [1 << 20, 3 << 20])
+def test_tiled_construction_matches_oracle(mods, tile_bytes):
+    # the build forced to run window by window over the index (L2-sized
+    # windows in production; small ones here so many tiles and a ragged last
+    # tile are exercised)
+    Rambo, Oracle = mods
+    w = synth.make("genome", 0.02, m=1 << 18)
+    g = Rambo(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    g.set_build_tiling(tile_bytes, mode=1)
+    g.insert(w.sets.ids, w.sets.data, w.sets.offsets, kind="seq")
+    o = Oracle(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    o.insert_seq_batch(w.sets.ids, w.sets.data, w.sets.offsets, 31, nthreads=8)
+    assert_index_equal(g, o)
+    assert_query_equal(g, o, w.queries.subset(np.arange(1000)))
+    # keys input, forced untiled, same bits
+    keys = np.random.default_rng(3).integers(0, 1 << 62, 50000, dtype=np.uint64)
+    off = np.linspace(0, keys.size, 11).astype(np.uint64)
+    for mode in (1, 2):
+        g2 = Rambo(10, 40, 3, 1 << 17, 2, 5)
+        g2.set_build_tiling(tile_bytes, mode=mode)
+        g2.insert(np.arange(10, dtype=np.uint64), keys, off)
+        o2 = Oracle(10, 40, 3, 1 << 17, 2, 5)
+        o2.insert_keys_batch(np.arange(10, dtype=np.uint64), keys, off)
+        assert_index_equal(g2, o2)

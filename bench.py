@@ -60,6 +60,9 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--m-log2", type=int, default=None, help="override the Bloom filter size m = 2^L")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the query steps only (no e2e, random-row or CPU legs): the profiling case")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -68,8 +71,9 @@ def parse_args():
 # workload
 # ---------------------------------------------------------------------------
 
-def make_workload(config: str, scale: float):
-    return synth.make(config, scale)
+def make_workload(config: str, scale: float, m_log2=None):
+    kw = {} if m_log2 is None else {"m": 1 << m_log2}
+    return synth.make(config, scale, **kw)
 
 
 def extra_batches(w, n_batches: int, rank: int):
@@ -228,7 +232,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     nthreads = os.cpu_count() or 1
-    w = make_workload(args.config, args.scale)
+    w = make_workload(args.config, args.scale, args.m_log2)
     o, build_s = oracle_index(w, nthreads)
     q = w.queries
     # size one step to a bounded sample so the whole run stays within minutes
@@ -285,7 +289,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     t_gen = time.perf_counter()
-    w = make_workload(args.config, args.scale)
+    w = make_workload(args.config, args.scale, args.m_log2)
     batches = extra_batches(w, args.batches, rank)
     t_gen = time.perf_counter() - t_gen
 
@@ -361,7 +365,7 @@ def run_ours(args):
         ho = torch.from_numpy(q.offsets.view(np.int64)).pin_memory().numpy().view(np.uint64)
         host_batches.append((hd.view(np.uint64) if q.kind == "keys" else hd, ho, keys_in(q, w.k), len(q)))
     e2e_s, e2e_keys, h2d, d2h = 0.0, 0, 0, 0
-    n_e2e = max(1, min(args.e2e_steps, args.steps))
+    n_e2e = 0 if args.no_extras else max(1, min(args.e2e_steps, args.steps))
     for i in range(n_e2e):
         hd, ho, nk, nq = host_batches[i % len(host_batches)]
         flush.zero_()
@@ -395,6 +399,8 @@ def run_ours(args):
     # random-row ceiling on a buffer the size of the index
     rr = None
     try:
+        if args.no_extras:
+            raise RuntimeError("skipped (--no-extras)")
         from paper_1910_02611_gb300 import random_row_probe
 
         n_rows = w.R * w.m
@@ -413,7 +419,7 @@ def run_ours(args):
 
     # ---- CPU oracle baseline (rank 0, N=1) ----
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_extras:
         nthreads = os.cpu_count() or 1
         o, ob_s = oracle_index(w, nthreads)
         rate, n, dt = oracle_rate(o, batches[0], w.k, nthreads, args.cpu_seconds)
@@ -449,8 +455,8 @@ def run_ours(args):
         "batch_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "keys_probed_frac": probed / max(keys, 1),
         "results_per_step": n_ids / args.steps,
-        "e2e": {"value": e2e_keys_all / e2e_s_max, "unit": UNIT, "h2d_bytes_per_step": h2d // n_e2e,
-                "d2h_bytes_per_step": d2h // n_e2e},
+        "e2e": ({"value": e2e_keys_all / e2e_s_max, "unit": UNIT, "h2d_bytes_per_step": h2d // n_e2e,
+                 "d2h_bytes_per_step": d2h // n_e2e} if n_e2e else None),
         "gpu_launches": launches,
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",

@@ -220,7 +220,7 @@ int rambo_load(const char *path, rambo_t **out);
 
 /* Measurement helper (no counterpart in the paper): every thread of
  * blocks x threads reads reads_per_thread random rows of a device buffer of
- * n_rows rows (a power of two) spaced row_words 32-bit words apart (the first
+ * n_rows rows spaced row_words 32-bit words apart (the first
  * min(row_words, 4) words of each), as the query's row probes do.  *ms gets
  * the kernel time.  Gives the random-row throughput ceiling of the device. */
 int rambo_random_row_probe(const uint32_t *dev_buf, uint64_t n_rows, uint32_t row_words,

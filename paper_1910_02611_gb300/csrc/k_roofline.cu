@@ -8,7 +8,7 @@
 namespace rgb {
 
 template <int V>
-__global__ void __launch_bounds__(256) k_random_rows(const uint32_t* __restrict__ buf, uint64_t row_mask,
+__global__ void __launch_bounds__(256) k_random_rows(const uint32_t* __restrict__ buf, uint64_t n_rows,
                                                      uint32_t stride, uint64_t reads_per_thread, uint64_t seed,
                                                      uint32_t* sink) {
     constexpr int U = 16;  // independent reads in flight per thread
@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(256) k_random_rows(const uint32_t* __restrict_
         uint32_t v[U][V];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const uint64_t row = mix64(ctr + u) & row_mask;
+            const uint64_t row = __umul64hi(mix64(ctr + u), n_rows);  // uniform in [0, n_rows)
             const uint32_t* p = buf + row * stride;
             if constexpr (V == 1) {
                 v[u][0] = __ldg(p);
@@ -46,14 +46,14 @@ __global__ void __launch_bounds__(256) k_random_rows(const uint32_t* __restrict_
 
 cudaError_t launch_random_rows(const uint32_t* buf, uint64_t n_rows, uint32_t row_words, uint64_t reads_per_thread,
                                uint64_t seed, uint32_t* sink, int blocks, int threads, cudaStream_t s) {
-    if (n_rows == 0 || (n_rows & (n_rows - 1))) return cudaErrorInvalidValue;
-    const uint64_t mask = n_rows - 1;
+    if (n_rows == 0) return cudaErrorInvalidValue;
+    const uint64_t rows = n_rows;
     if (row_words == 1)
-        k_random_rows<1><<<blocks, threads, 0, s>>>(buf, mask, 1, reads_per_thread, seed, sink);
+        k_random_rows<1><<<blocks, threads, 0, s>>>(buf, rows, 1, reads_per_thread, seed, sink);
     else if (row_words == 2)
-        k_random_rows<2><<<blocks, threads, 0, s>>>(buf, mask, 2, reads_per_thread, seed, sink);
+        k_random_rows<2><<<blocks, threads, 0, s>>>(buf, rows, 2, reads_per_thread, seed, sink);
     else if (row_words % 4 == 0)
-        k_random_rows<4><<<blocks, threads, 0, s>>>(buf, mask, row_words, reads_per_thread, seed, sink);
+        k_random_rows<4><<<blocks, threads, 0, s>>>(buf, rows, row_words, reads_per_thread, seed, sink);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -762,7 +762,7 @@ int rambo_load(const char* path, rambo_t** out) {
 
 int rambo_random_row_probe(const uint32_t* dev_buf, uint64_t n_rows, uint32_t row_words, uint64_t reads_per_thread,
                            uint32_t blocks, uint32_t threads, uint64_t seed, float* ms, void* stream) {
-    if (!dev_buf || !ms || !blocks || !threads || threads > 256 || (n_rows & (n_rows - 1)) || !n_rows)
+    if (!dev_buf || !ms || !blocks || !threads || threads > 256 || !n_rows)
         return RAMBO_EINVAL;
     if (!(row_words == 1 || row_words == 2 || row_words % 4 == 0)) return RAMBO_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;

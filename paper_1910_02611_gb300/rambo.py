@@ -147,6 +147,15 @@ def _host_arr(x, dtype) -> np.ndarray:
     return np.ascontiguousarray(x, dtype=dtype)
 
 
+def _check_csr(data: np.ndarray, off: np.ndarray, what: str) -> None:
+    """The C ABI reads data[offsets[0] .. offsets[n]); refuse host arrays that
+    are shorter than that before handing pointers over."""
+    if off.size < 1:
+        raise ValueError(f"{what}: offsets must have n+1 >= 1 entries")
+    if off.size > 1 and int(off[-1]) > data.size and int(off[-1]) >= int(off[0]):
+        raise ValueError(f"{what}: offsets[-1]={int(off[-1])} exceeds the data length {data.size}")
+
+
 class Rambo:
     """A RAMBO index resident in GPU memory (Secs. 2-3 of arXiv 1910.02611)."""
 
@@ -213,6 +222,9 @@ class Rambo:
             ids = _host_arr(set_ids, np.uint64)
             d = _host_arr(data, np.uint64 if kind == "keys" else np.uint8)
             off = _host_arr(offsets, np.uint64)
+            _check_csr(d, off, "insert")
+            if ids.size != off.size - 1:
+                raise ValueError("insert: need one set ID per CSR item")
             keep = (ids, d, off)
             ids_p, data_p, off_p = ids.ctypes.data, d.ctypes.data, off.ctypes.data
             n = off.size - 1
@@ -236,6 +248,7 @@ class Rambo:
         else:
             d = _host_arr(data, np.uint64 if kind == "keys" else np.uint8)
             off = _host_arr(offsets, np.uint64)
+            _check_csr(d, off, "query")
             keep = (d, off)
             data_p, off_p, n = d.ctypes.data, off.ctypes.data, off.size - 1
         ids_p, offo_p = _p(), _p()
@@ -270,6 +283,7 @@ class Rambo:
         else:
             d = _host_arr(data, np.uint64 if kind == "keys" else np.uint8)
             off = _host_arr(offsets, np.uint64)
+            _check_csr(d, off, "query_into")
             args = (d.ctypes.data, off.ctypes.data, off.size - 1)
             assert ids_out.dtype == np.uint32 and id_offsets_out.dtype == np.uint64
             ids_p, cap, oo = ids_out.ctypes.data, ids_out.size, id_offsets_out.ctypes.data

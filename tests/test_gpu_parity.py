@@ -184,7 +184,8 @@ def test_kmer_lengths_other_than_31(mods):
         g.insert(np.arange(K, dtype=np.uint64), bases, off, kind="seq", k=k)
         o.insert_seq_batch(np.arange(K, dtype=np.uint64), bases, off, k)
         assert_index_equal(g, o)
-        qo = np.arange(0, 40 * 60 + 1, 60, dtype=np.uint64)
+        n_q = int(bases.size // 60)
+        qo = np.arange(0, n_q * 60 + 1, 60, dtype=np.uint64)
         qd = bases[: int(qo[-1])]
         assert_query_equal(g, o, synth.Collection("seq", qd.copy(), qo), k=k)
 

@@ -187,13 +187,21 @@ int rambo_last_query_stats(const rambo_t *h, rambo_query_stats_t *out);
  *   lanes_per_key G, words_per_lane V (V divides the row stride, G*V >= stride),
  *   warps_per_block, blocks_per_sm (0 = as many as fit),
  *   set_stage: 0 = auto, 1 = dense scan of the partition table,
- *              2 = sparse enumeration of the hit cells' members. */
+ *              2 = sparse enumeration of the hit cells' members,
+ *   visit_order and l2_fetch_bytes as described in the struct. */
 typedef struct rambo_query_config {
     uint32_t lanes_per_key;
     uint32_t words_per_lane;
     uint32_t warps_per_block;
     uint32_t blocks_per_sm;
     uint32_t set_stage;
+    uint32_t visit_order;     /* 0 = keys in input order; 1 = strided: the warp's
+                               * first step spreads its terms evenly over the
+                               * query, so a run of absent k-mers (a substitution
+                               * touches k consecutive windows) is met at once */
+    uint32_t l2_fetch_bytes;  /* 0 = leave the context's L2 fetch granularity;
+                               * 32/64/128 = set it for the query kernel and
+                               * restore it afterwards */
 } rambo_query_config_t;
 
 int rambo_get_query_config(const rambo_t *h, rambo_query_config_t *out);
@@ -226,6 +234,12 @@ int rambo_load(const char *path, rambo_t **out);
 int rambo_random_row_probe(const uint32_t *dev_buf, uint64_t n_rows, uint32_t row_words,
                            uint64_t reads_per_thread, uint32_t blocks, uint32_t threads,
                            uint64_t seed, float *ms, void *stream);
+
+/* The current CUDA context's L2 fetch granularity hint
+ * (cudaLimitMaxL2FetchGranularity): stores the present value in *prev (if not
+ * NULL) and, when bytes > 0, sets it to bytes (32, 64 or 128).  A context-wide
+ * performance hint; results never depend on it. */
+int rambo_l2_fetch_granularity(uint32_t bytes, uint32_t *prev);
 
 /* Index of the item (query or set) that caused the last RAMBO_EINVAL,
  * RAMBO_ERANGE or RAMBO_EBADSEQ returned on this handle. */

@@ -85,7 +85,7 @@ __device__ __forceinline__ bool qk_set_passes(const IndexView& ix, const uint32_
 template <int V, int G, int ETA>
 __global__ void __launch_bounds__(QK_THREADS_MAX)
     k_query(IndexView ix, HashParams hp, BatchView b, QueryOut o, int set_stage, int batch,
-            uint32_t smem_per_warp, int use_bitmap, DevStatus* st) {
+            uint32_t smem_per_warp, int use_bitmap, int order, DevStatus* st) {
     extern __shared__ uint32_t qk_smem[];
     constexpr int KPS = 32 / G;  // terms per warp step
     const unsigned lane = threadIdx.x & 31;
@@ -126,8 +126,11 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                 for (int v = 0; v < V; ++v) M[r][v] = has_words ? ~0u : 0u;
 
             bool alive = true;
-            for (uint64_t base = 0; base < nkeys; base += KPS) {
-                const uint64_t idx = base + grp;
+            // step s visits terms s*KPS + g (input order) or g*nsteps + s
+            // (strided: the first step samples the whole query evenly)
+            const uint64_t nsteps = (nkeys + KPS - 1) / KPS;
+            for (uint64_t s = 0; s < nsteps; ++s) {
+                const uint64_t idx = order ? (uint64_t)grp * nsteps + s : s * KPS + grp;
                 const bool act = idx < nkeys;
                 uint64_t key = 0;
                 if (act) key = b.seq ? kmer_at(b.packed, a + idx, b.k) : __ldg(b.keys + a + idx);
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                     }
                 }
                 nz = __reduce_or_sync(FULL, nz);
-                probed += (nkeys - base < (uint64_t)KPS) ? (nkeys - base) : (uint64_t)KPS;
+                probed += __popc(__ballot_sync(FULL, act && slot == 0));
                 if (nz != rmask) {
                     alive = false;
                     break;

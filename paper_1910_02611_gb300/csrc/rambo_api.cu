@@ -195,6 +195,8 @@ void default_config(rambo* h) {
     h->cfg.warps_per_block = 8;
     h->cfg.blocks_per_sm = 0;
     h->cfg.set_stage = 0;
+    h->cfg.visit_order = 1;
+    h->cfg.l2_fetch_bytes = 0;
 }
 
 int decode_err(rambo* h, unsigned long long e) {
@@ -318,6 +320,7 @@ int resolve_tuning(rambo* h, uint64_t n, int& use_bitmap, QueryTuning& t) {
     t.G = (int)h->cfg.lanes_per_key;
     t.warps_per_block = (int)h->cfg.warps_per_block;
     t.set_stage = (int)h->cfg.set_stage;
+    t.order = (int)h->cfg.visit_order;
     use_bitmap = (h->mem_off && t.set_stage != 1 && (h->K + 31) / 32 <= 4096) ? 1 : 0;
     const size_t smem =
         (size_t)query_smem_words_per_warp(h->R, h->S, h->K, use_bitmap) * 4 * (size_t)t.warps_per_block;
@@ -399,9 +402,15 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
             b.keys = static_cast<const uint64_t*>(d_data);
         }
         QueryOut o{h->stage.p, h->stage.cap, h->qstart.p, h->qcount.p};
+        size_t l2_prev = 0;
+        if (h->cfg.l2_fetch_bytes) {
+            CK(cudaDeviceGetLimit(&l2_prev, cudaLimitMaxL2FetchGranularity));
+            CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, h->cfg.l2_fetch_bytes));
+        }
         CK(cudaEventRecord(h->ev[1], s));
         CK(launch_query(h->view(), h->hp, b, o, t, use_bitmap, h->st, s));
         CK(cudaEventRecord(h->ev[2], s));
+        if (h->cfg.l2_fetch_bytes) CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, l2_prev));
         CK(launch_scan_counts(h->qcount.p, n, d_off, h->scan_tmp.p, h->scan_tmp.cap, s));
         h->launches += 4;
         CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
@@ -659,6 +668,9 @@ int rambo_set_query_config(rambo_t* h, const rambo_query_config_t* cfg) {
     if (cfg->warps_per_block < 1 || cfg->warps_per_block > 8) return RAMBO_EINVAL;
     if (cfg->set_stage > 2) return RAMBO_EINVAL;
     if (cfg->set_stage == 2 && !h->mem_off) return RAMBO_EINVAL;
+    if (cfg->visit_order > 1) return RAMBO_EINVAL;
+    if (cfg->l2_fetch_bytes && cfg->l2_fetch_bytes != 32 && cfg->l2_fetch_bytes != 64 && cfg->l2_fetch_bytes != 128)
+        return RAMBO_EINVAL;
     h->cfg = *cfg;
     return RAMBO_OK;
 }
@@ -678,6 +690,8 @@ int rambo_list_query_configs(const rambo_t* h, rambo_query_config_t* out, int ca
                 out[n].warps_per_block = (uint32_t)w;
                 out[n].blocks_per_sm = 0;
                 out[n].set_stage = 0;
+                out[n].visit_order = 1;
+                out[n].l2_fetch_bytes = 0;
             }
             ++n;
         }
@@ -692,6 +706,17 @@ int rambo_set_build_tiling(rambo_t* h, uint64_t tile_bytes, int mode) {
         h->build_tile_bytes = tile_bytes;
     }
     h->build_mode = mode;
+    return RAMBO_OK;
+}
+
+int rambo_l2_fetch_granularity(uint32_t bytes, uint32_t* prev) {
+    size_t v = 0;
+    CK(cudaDeviceGetLimit(&v, cudaLimitMaxL2FetchGranularity));
+    if (prev) *prev = (uint32_t)v;
+    if (bytes) {
+        if (bytes != 32 && bytes != 64 && bytes != 128) return RAMBO_EINVAL;
+        CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, bytes));
+    }
     return RAMBO_OK;
 }
 

@@ -127,6 +127,7 @@ struct QueryTuning {
     int blocks;            // grid size
     int set_stage;         // 1 dense, 2 sparse, 0 auto
     int batch;             // queries taken per ticket
+    int order;             // 0 input order, 1 strided
 };
 
 // ---------------------------------------------------------------------------

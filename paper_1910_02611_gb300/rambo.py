@@ -32,7 +32,7 @@ class QueryStats(C.Structure):
 
 class QueryConfig(C.Structure):
     _fields_ = [("lanes_per_key", _u32), ("words_per_lane", _u32), ("warps_per_block", _u32),
-                ("blocks_per_sm", _u32), ("set_stage", _u32)]
+                ("blocks_per_sm", _u32), ("set_stage", _u32), ("visit_order", _u32), ("l2_fetch_bytes", _u32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -61,6 +61,7 @@ SIGNATURES = {
     "rambo_save": (_i32, [_p, C.c_char_p]),
     "rambo_load": (_i32, [C.c_char_p, C.POINTER(_p)]),
     "rambo_random_row_probe": (_i32, [_p, _u64, _u32, _u64, _u32, _u32, _u64, C.POINTER(C.c_float), _p]),
+    "rambo_l2_fetch_granularity": (_i32, [_u32, C.POINTER(_u32)]),
     "rambo_last_error_item": (_u64, [_p]),
     "rambo_strerror": (C.c_char_p, [_i32]),
 }
@@ -351,6 +352,16 @@ class Rambo:
 
     def save(self, path: str) -> None:
         self._check(load_library().rambo_save(self._h, path.encode()), "save")
+
+
+def l2_fetch_granularity(bytes_: int = 0) -> int:
+    """Reads (and, if bytes_ > 0, sets) the CUDA context's L2 fetch
+    granularity hint; returns the value before the call."""
+    prev = _u32(0)
+    rc = load_library().rambo_l2_fetch_granularity(bytes_, C.byref(prev))
+    if rc:
+        raise RamboError(rc, "l2_fetch_granularity")
+    return int(prev.value)
 
 
 def random_row_probe(buf, n_rows: int, row_words: int, reads_per_thread: int, blocks: int, threads: int = 256,

@@ -67,8 +67,11 @@ def test_queries_identical_every_kernel_config(pair):
     try:
         for cfg in g.list_configs():
             for stage in (1, 2):
-                g.set_config(**{**cfg, "set_stage": stage})
-                assert_query_equal(g, o, q, k=w.k)
+                for order in (0, 1):
+                    g.set_config(**{**cfg, "set_stage": stage, "visit_order": order})
+                    assert_query_equal(g, o, q, k=w.k)
+        g.set_config(**{**base, "l2_fetch_bytes": 32})
+        assert_query_equal(g, o, q, k=w.k)
     finally:
         g.set_config(**base)
 

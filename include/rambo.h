@@ -174,7 +174,7 @@ typedef struct rambo_query_stats {
     uint64_t n_queries;
     uint64_t keys_submitted;
     uint64_t keys_probed;
-    uint64_t rows_read;        /* keys_probed * R * eta */
+    uint64_t rows_read;        /* index rows read */
     uint64_t n_results;        /* set IDs returned */
     uint64_t kernel_launches;  /* kernels this library launched for the call */
     float query_kernel_ms;
@@ -198,10 +198,15 @@ typedef struct rambo_query_config {
     uint32_t visit_order;     /* 0 = keys in input order; 1 = strided: the warp's
                                * first step spreads its terms evenly over the
                                * query, so a run of absent k-mers (a substitution
-                               * touches k consecutive windows) is met at once */
+                               * touches k consecutive windows) is met at once;
+                               * 2 = strided, and the first step reads table 0
+                               * alone before the other tables */
     uint32_t l2_fetch_bytes;  /* 0 = leave the context's L2 fetch granularity;
                                * 32/64/128 = set it for the query kernel and
                                * restore it afterwards */
+    uint32_t cluster;         /* 1 = hand queries to warps grouped by their
+                               * minimizer (smallest term hash), so overlapping
+                               * queries run together and share cached rows */
 } rambo_query_config_t;
 
 int rambo_get_query_config(const rambo_t *h, rambo_query_config_t *out);

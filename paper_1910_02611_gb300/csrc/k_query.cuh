@@ -107,14 +107,15 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
         for (uint32_t w = lane; w < bw; w += 32) sBits[w] = 0;
     __syncwarp();
 
-    unsigned long long probed = 0;
+    unsigned long long probed = 0, rows_read = 0;
     for (;;) {
         unsigned long long q0 = 0;
         if (lane == 0) q0 = atomicAdd(&st->ticket, (unsigned long long)batch);
         q0 = __shfl_sync(FULL, q0, 0);
         if (q0 >= b.n) break;
         const unsigned long long q1 = min(q0 + (unsigned long long)batch, (unsigned long long)b.n);
-        for (unsigned long long q = q0; q < q1; ++q) {
+        for (unsigned long long t = q0; t < q1; ++t) {
+            const unsigned long long q = b.perm ? (unsigned long long)__ldg(b.perm + t) : t;
             const uint64_t a = __ldg(b.offsets + q) - b.off0;
             const uint64_t e = __ldg(b.offsets + q + 1) - b.off0;
             const uint64_t nkeys = b.seq ? (e - a - b.k + 1) : (e - a);  // >= 1 (validated)
@@ -127,9 +128,18 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
 
             bool alive = true;
             // step s visits terms s*KPS + g (input order) or g*nsteps + s
-            // (strided: the first step samples the whole query evenly)
+            // (strided: the first step samples the whole query evenly).
+            // With screening, the first step reads table 0 only (phase 0) and
+            // the other tables for the same terms only if the query is still
+            // alive (phase 1); a query holding an absent term usually dies in
+            // phase 0 at eta rows per term instead of R*eta.
             const uint64_t nsteps = (nkeys + KPS - 1) / KPS;
-            for (uint64_t s = 0; s < nsteps; ++s) {
+            const bool screen = order >= 2 && R > 1;
+            const uint64_t nphases = nsteps + (screen ? 1 : 0);
+            for (uint64_t ph = 0; ph < nphases; ++ph) {
+                const uint64_t s = screen ? (ph == 0 ? 0 : ph - 1) : ph;
+                const int rlo = (screen && ph == 1) ? 1 : 0;
+                const int rhi = (screen && ph == 0) ? 1 : R;
                 const uint64_t idx = order ? (uint64_t)grp * nsteps + s : s * KPS + grp;
                 const bool act = idx < nkeys;
                 uint64_t key = 0;
@@ -140,7 +150,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                 const bool ld = act && has_words;
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r) {
-                    if (r < R && ld) {
+                    if (r >= rlo && r < rhi && ld) {
                         const uint32_t* rb = rows + (uint64_t)r * ix.m * ix.S + w0;
 #pragma unroll
                         for (int j = 0; j < ETA; ++j) {
@@ -156,23 +166,30 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                 for (int r = 0; r < RMAX; ++r) {
                     if (r < R) {
                         uint32_t any = 0;
+                        const bool probed_r = r >= rlo && r < rhi;
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
                             uint32_t x = ~0u;
-                            if (ld) {
+                            if (ld && probed_r) {
 #pragma unroll
                                 for (int j = 0; j < ETA; ++j)
                                     if (j < eta) x &= val[r][j][v];
                             }
-                            x = qk_and_groups<G>(x);  // A4: across this step's terms
-                            M[r][v] &= x;             // and into the query's masks
+                            if (probed_r) {
+                                x = qk_and_groups<G>(x);  // A4: across this step's terms
+                                M[r][v] &= x;             // and into the query's masks
+                            }
                             any |= M[r][v];
                         }
                         if (any) nz |= 1u << r;
                     }
                 }
                 nz = __reduce_or_sync(FULL, nz);
-                probed += __popc(__ballot_sync(FULL, act && slot == 0));
+                {
+                    const unsigned nact = __popc(__ballot_sync(FULL, act && slot == 0));
+                    if (!(screen && ph == 1)) probed += nact;  // the screened terms were counted in phase 0
+                    rows_read += (unsigned long long)nact * (unsigned)(rhi - rlo) * (unsigned)eta;
+                }
                 if (nz != rmask) {
                     alive = false;
                     break;
@@ -297,6 +314,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
         }
     }
     if (lane == 0 && probed) atomicAdd(&st->keys_probed, probed);
+    if (lane == 0 && rows_read) atomicAdd(&st->rows_read, rows_read);
 }
 
 }  // namespace rgb

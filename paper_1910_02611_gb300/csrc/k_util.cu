@@ -278,6 +278,64 @@ cudaError_t launch_scan_counts(const uint32_t* counts, uint64_t n, uint64_t* off
 }
 
 // ---------------------------------------------------------------------------
+// query clustering for cache locality: each query's locality key is the
+// smallest hash over its terms (its minimizer); queries are bucketed by the
+// key's top 16 bits, so queries sharing a minimizer (overlapping substrings
+// of the same region) are handed out together and their common rows are read
+// from L2.  Only the processing order changes; every query's answer is the same.
+
+__global__ void k_minimizer(BatchView b, uint64_t* __restrict__ keys, uint32_t* __restrict__ hist,
+                            const DevStatus* st) {
+    if (st->err != NO_ERR) return;
+    const int lane = threadIdx.x & 31;
+    uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t q = warp; q < b.n; q += nwarps) {
+        const uint64_t a = __ldg(b.offsets + q) - b.off0;
+        const uint64_t e = __ldg(b.offsets + q + 1) - b.off0;
+        const uint64_t nkeys = b.seq ? (e - a - b.k + 1) : (e - a);
+        uint64_t mn = ~0ull;
+        for (uint64_t t = lane; t < nkeys; t += 32) {
+            const uint64_t key = b.seq ? kmer_at(b.packed, a + t, b.k) : __ldg(b.keys + a + t);
+            const uint64_t h = mix64(key ^ 0x5851F42D4C957F2Dull);
+            mn = h < mn ? h : mn;
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            const uint64_t o = __shfl_xor_sync(FULL, mn, off);
+            mn = o < mn ? o : mn;
+        }
+        if (lane == 0) {
+            keys[q] = mn;
+            atomicAdd(hist + (mn >> 48), 1u);
+        }
+    }
+}
+
+__global__ void k_bucket_scatter(const uint64_t* __restrict__ keys, uint64_t n, const uint64_t* __restrict__ off,
+                                 uint32_t* __restrict__ fill, uint32_t* __restrict__ perm, const DevStatus* st) {
+    if (st->err != NO_ERR) return;
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n; q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t bk = (uint32_t)(keys[q] >> 48);
+        perm[off[bk] + atomicAdd(fill + bk, 1u)] = (uint32_t)q;
+    }
+}
+
+cudaError_t launch_cluster_order(const BatchView& b, uint64_t* keys, uint32_t* hist, uint64_t* bucket_off,
+                                 uint64_t* scan_tmp, uint64_t scan_tmp_words, uint32_t* perm, const DevStatus* st,
+                                 cudaStream_t s) {
+    // hist holds 2 * CLUSTER_BUCKETS counters: counts, then fill cursors
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 2 * CLUSTER_BUCKETS, s);
+    if (e != cudaSuccess) return e;
+    if (b.n == 0) return cudaSuccess;
+    k_minimizer<<<grid_for(b.n * 32, 256, 152 * 32), 256, 0, s>>>(b, keys, hist, st);
+    e = launch_scan_counts(hist, CLUSTER_BUCKETS, bucket_off, scan_tmp, scan_tmp_words, s);
+    if (e != cudaSuccess) return e;
+    k_bucket_scatter<<<grid_for(b.n, 256, 4096), 256, 0, s>>>(keys, b.n, bucket_off, hist + CLUSTER_BUCKETS, perm, st);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // gather staged result IDs into CSR order: one warp per query
 
 __global__ void k_gather(QueryOut o, const uint64_t* __restrict__ id_offsets, uint64_t n,

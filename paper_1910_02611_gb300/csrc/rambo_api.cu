@@ -120,7 +120,8 @@ struct rambo {
     // scratch
     DBuf<uint8_t> in_data;
     DBuf<uint64_t> in_off, in_ids, packed, qstart, scan_tmp, id_off;
-    DBuf<uint32_t> stage, qcount, ids, fill;
+    DBuf<uint32_t> stage, qcount, ids, fill, perm, chist;
+    DBuf<uint64_t> ckeys, coff;
     HBuf<uint32_t> h_ids;
     HBuf<uint64_t> h_id_off;
     rambo_query_config_t cfg{};
@@ -179,6 +180,10 @@ void free_handle(rambo* h) {
     h->qcount.release();
     h->ids.release();
     h->fill.release();
+    h->perm.release();
+    h->chist.release();
+    h->ckeys.release();
+    h->coff.release();
     h->h_ids.release();
     h->h_id_off.release();
     cudaSetDevice(cur);
@@ -195,8 +200,9 @@ void default_config(rambo* h) {
     h->cfg.warps_per_block = 8;
     h->cfg.blocks_per_sm = 0;
     h->cfg.set_stage = 0;
-    h->cfg.visit_order = 1;
+    h->cfg.visit_order = 2;
     h->cfg.l2_fetch_bytes = 0;
+    h->cfg.cluster = 0;
 }
 
 int decode_err(rambo* h, unsigned long long e) {
@@ -401,6 +407,18 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
         } else {
             b.keys = static_cast<const uint64_t*>(d_data);
         }
+        b.perm = nullptr;
+        if (h->cfg.cluster) {
+            RK(h->ckeys.ensure(n));
+            RK(h->perm.ensure(n));
+            RK(h->chist.ensure(2 * CLUSTER_BUCKETS));
+            RK(h->coff.ensure(CLUSTER_BUCKETS + 1));
+            RK(h->scan_tmp.ensure(scan_tmp_words(n > CLUSTER_BUCKETS ? n : CLUSTER_BUCKETS)));
+            CK(launch_cluster_order(b, h->ckeys.p, h->chist.p, h->coff.p, h->scan_tmp.p, h->scan_tmp.cap, h->perm.p,
+                                    h->st, s));
+            b.perm = h->perm.p;
+            h->launches += 5;
+        }
         QueryOut o{h->stage.p, h->stage.cap, h->qstart.p, h->qcount.p};
         size_t l2_prev = 0;
         if (h->cfg.l2_fetch_bytes) {
@@ -425,7 +443,7 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
     h->last.n_queries = n;
     h->last.keys_submitted = seq ? (b.total - n * (uint64_t)(k - 1)) : b.total;
     h->last.keys_probed = h->h_st->keys_probed;
-    h->last.rows_read = h->last.keys_probed * h->R * h->eta;
+    h->last.rows_read = h->h_st->rows_read;
     h->last.n_results = total_ids;
     CK(cudaEventElapsedTime(&h->last.query_kernel_ms, h->ev[1], h->ev[2]));
     if (d.needed) *d.needed = total_ids;
@@ -668,7 +686,7 @@ int rambo_set_query_config(rambo_t* h, const rambo_query_config_t* cfg) {
     if (cfg->warps_per_block < 1 || cfg->warps_per_block > 8) return RAMBO_EINVAL;
     if (cfg->set_stage > 2) return RAMBO_EINVAL;
     if (cfg->set_stage == 2 && !h->mem_off) return RAMBO_EINVAL;
-    if (cfg->visit_order > 1) return RAMBO_EINVAL;
+    if (cfg->visit_order > 2 || cfg->cluster > 1) return RAMBO_EINVAL;
     if (cfg->l2_fetch_bytes && cfg->l2_fetch_bytes != 32 && cfg->l2_fetch_bytes != 64 && cfg->l2_fetch_bytes != 128)
         return RAMBO_EINVAL;
     h->cfg = *cfg;
@@ -690,8 +708,9 @@ int rambo_list_query_configs(const rambo_t* h, rambo_query_config_t* out, int ca
                 out[n].warps_per_block = (uint32_t)w;
                 out[n].blocks_per_sm = 0;
                 out[n].set_stage = 0;
-                out[n].visit_order = 1;
+                out[n].visit_order = 2;
                 out[n].l2_fetch_bytes = 0;
+                out[n].cluster = 0;
             }
             ++n;
         }

@@ -112,6 +112,7 @@ struct BatchView {
     uint64_t n;                    // items
     uint32_t k;
     const uint64_t* set_ids;       // insert batches only
+    const uint32_t* perm;          // queries only: processing order (NULL = 0..n-1)
 };
 
 struct QueryOut {
@@ -152,6 +153,11 @@ cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_
 cudaError_t launch_cell_popcount(const IndexView& ix, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_members(const IndexView& ix, uint64_t* mem_off, uint32_t* mem_ids,
                            uint32_t* fill, cudaStream_t s);
+
+cudaError_t launch_cluster_order(const BatchView& b, uint64_t* keys, uint32_t* hist, uint64_t* bucket_off,
+                                 uint64_t* scan_tmp, uint64_t scan_tmp_words, uint32_t* perm, const DevStatus* st,
+                                 cudaStream_t s);
+constexpr uint32_t CLUSTER_BUCKETS = 1u << 16;
 
 // k_build.cu
 cudaError_t launch_insert(const IndexView& ix, const HashParams& hp, const BatchView& b,

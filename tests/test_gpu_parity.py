@@ -57,7 +57,7 @@ def test_queries_identical_default_config(pair):
     assert_query_equal(g, o, w.queries, k=w.k)
     st = g.last_query_stats()
     assert st["keys_probed"] <= st["keys_submitted"]
-    assert st["rows_read"] == st["keys_probed"] * w.R * w.eta
+    assert st["keys_probed"] * w.eta <= st["rows_read"] <= st["keys_probed"] * w.R * w.eta
 
 
 def test_queries_identical_every_kernel_config(pair):
@@ -67,11 +67,13 @@ def test_queries_identical_every_kernel_config(pair):
     try:
         for cfg in g.list_configs():
             for stage in (1, 2):
-                for order in (0, 1):
+                for order in (0, 1, 2):
                     g.set_config(**{**cfg, "set_stage": stage, "visit_order": order})
                     assert_query_equal(g, o, q, k=w.k)
         g.set_config(**{**base, "l2_fetch_bytes": 32})
         assert_query_equal(g, o, q, k=w.k)
+        g.set_config(**{**base, "cluster": 1})
+        assert_query_equal(g, o, w.queries, k=w.k)
     finally:
         g.set_config(**base)
 

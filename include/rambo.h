@@ -61,7 +61,9 @@ enum {
     RAMBO_ECUDA = -6,    /* a CUDA runtime call failed */
     RAMBO_ETIMEOUT = -7, /* a bounded device-side wait gave up */
     RAMBO_EIO = -8,      /* file error in save/load */
-    RAMBO_ESTATE = -9    /* call not valid in the object's current state */
+    RAMBO_ESTATE = -9,   /* call not valid in the object's current state */
+    RAMBO_E2BIG = -10    /* request larger than the fixed scratch of
+                            rambo_query_seq_batch_noalloc */
 };
 
 /* Limits of this implementation. */
@@ -149,6 +151,31 @@ int rambo_query_seq_batch_into(rambo_t *h, const uint8_t *bases, const uint64_t 
                                uint64_t n_queries, uint32_t k, int on_device,
                                uint32_t *ids, uint64_t ids_cap, uint64_t *id_offsets,
                                uint64_t *needed, void *stream);
+
+/* Sequence query that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory while
+ * they query -- code that runs where cudaMalloc/cudaFree are forbidden or
+ * would stall (a real-time serving thread, a host callback, a process whose
+ * memory budget is fixed up front) -- but can still launch kernels.  It
+ * computes exactly what rambo_query_seq_batch_into computes; every pointer
+ * (bases, offsets, ids, id_offsets) is device memory owned by the caller.
+ * Its working memory (2-bit packed bases, per-query counts and staged IDs)
+ * is one array of 30 MiB (31,459,584 bytes) in device global memory that the
+ * library reserves on every GPU it is loaded on, held until the process exits.  Limits: at most
+ * 2^19 queries, 2^25 bases (offsets[n] - offsets[0]) and 4,194,304 result IDs
+ * staged per call; larger requests return RAMBO_E2BIG before any kernel runs
+ * (results beyond the staging limit are detected after the query kernel and
+ * also return RAMBO_E2BIG).  The first call on each device finds the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the one array: each
+ * call first clears the counters that must start at zero, so results never
+ * depend on earlier calls, but calls that overlap on the GPU (several streams
+ * or threads at once) race on it and must be serialised by the caller.
+ * Returns RAMBO_ENOSPC with *needed set when ids_cap is too small, and the
+ * errors of rambo_query_seq_batch otherwise. */
+int rambo_query_seq_batch_noalloc(rambo_t *h, const uint8_t *bases, const uint64_t *offsets,
+                                  uint64_t n_queries, uint32_t k, uint32_t *ids, uint64_t ids_cap,
+                                  uint64_t *id_offsets, uint64_t *needed, void *stream);
 
 /* Copies the bit-sliced index to host memory: n_words must equal
  * R * m * row_stride; word (r*m + p)*row_stride + w holds bits 32w..32w+31 of

@@ -493,6 +493,21 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
 
 }  // namespace
 
+namespace rgb {
+// Read-only view of a handle for the fixed-scratch query entry point
+// (rambo_noalloc.cu): index, hash parameters and the kernel tuning the handle
+// would use for n queries.  Allocates nothing.
+int handle_query_view(rambo_t* h, uint64_t n, IndexView* ix, HashParams* hp, QueryTuning* t, int* use_bitmap,
+                      int* device) {
+    if (!h || !ix || !hp || !t || !use_bitmap || !device) return RAMBO_EINVAL;
+    RK(resolve_tuning(h, n, *use_bitmap, *t));
+    *ix = h->view();
+    *hp = h->hp;
+    *device = h->device;
+    return RAMBO_OK;
+}
+}  // namespace rgb
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -839,6 +854,7 @@ const char* rambo_strerror(int code) {
         case RAMBO_ETIMEOUT: return "device wait timed out";
         case RAMBO_EIO: return "file I/O error";
         case RAMBO_ESTATE: return "invalid state";
+        case RAMBO_E2BIG: return "request exceeds the fixed scratch of the no-allocation query";
         default: return "unknown error";
     }
 }

@@ -171,6 +171,10 @@ int query_max_blocks_per_sm(int V, int G, uint32_t eta, int warps_per_block, siz
 cudaError_t launch_query(const IndexView& ix, const HashParams& hp, const BatchView& b, const QueryOut& o,
                          const QueryTuning& t, int use_bitmap, DevStatus* st, cudaStream_t s);
 
+// rambo_api.cu: what the fixed-scratch entry point needs from a handle
+int handle_query_view(rambo_t* h, uint64_t n, IndexView* ix, HashParams* hp, QueryTuning* t, int* use_bitmap,
+                      int* device);
+
 // k_roofline.cu
 cudaError_t launch_random_rows(const uint32_t* buf, uint64_t n_rows, uint32_t row_words,
                                uint64_t reads_per_thread, uint64_t seed, uint32_t* sink,

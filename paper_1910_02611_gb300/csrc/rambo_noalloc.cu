@@ -1,0 +1,162 @@
+// rambo_noalloc.cu -- rambo_query_seq_batch_noalloc: the sequence query for
+// callers that cannot allocate device memory while they query.
+//
+// It runs the same kernels as rambo_query_seq_batch_into, but every byte of
+// working memory comes from one file-scope __device__ array reserved when the
+// library is loaded, instead of buffers the handle grows with cudaMalloc.  The
+// call itself allocates nothing (no cudaMalloc, cudaFree or allocating library
+// routine); it only launches kernels and copies a few words back to the stack.
+//
+// The array is shared by every call on a device and keeps the previous call's
+// contents; the status reset at the start of each call clears everything that
+// must start at zero (error word, work-queue ticket, result cursor, counters),
+// and all other regions are fully written before they are read.  Calls that
+// overlap on the GPU race on the array.
+#include <mutex>
+
+#include "rambo_impl.cuh"
+
+using namespace rgb;
+
+namespace {
+
+// limits of one call
+constexpr uint64_t NA_MAX_QUERIES = 1ull << 19;
+constexpr uint64_t NA_MAX_BASES = 1ull << 25;
+constexpr uint64_t NA_STAGE_IDS = 1ull << 22;
+
+constexpr uint64_t align256(uint64_t x) { return (x + 255) / 256 * 256; }
+
+// layout of the array (byte offsets, 256-byte aligned)
+constexpr uint64_t NA_PACKED_WORDS = NA_MAX_BASES / 32 + 2;
+constexpr uint64_t NA_SCAN_WORDS = NA_MAX_QUERIES / 4096 + 2;
+constexpr uint64_t OFF_STATUS = 0;
+constexpr uint64_t OFF_PACKED = align256(OFF_STATUS + sizeof(DevStatus));
+constexpr uint64_t OFF_QCOUNT = align256(OFF_PACKED + NA_PACKED_WORDS * 8);
+constexpr uint64_t OFF_QSTART = align256(OFF_QCOUNT + NA_MAX_QUERIES * 4);
+constexpr uint64_t OFF_SCAN = align256(OFF_QSTART + NA_MAX_QUERIES * 8);
+constexpr uint64_t OFF_STAGE = align256(OFF_SCAN + NA_SCAN_WORDS * 8);
+constexpr uint64_t NA_SCRATCH_BYTES = align256(OFF_STAGE + NA_STAGE_IDS * 4);
+static_assert(NA_SCRATCH_BYTES < (32ull << 20), "fixed scratch stays under 32 MiB");
+
+constexpr int NA_MAX_DEVICES = 64;
+
+// host-side pointers to each device's copy of the array, found once per device
+std::mutex g_mu;
+unsigned char* g_base[NA_MAX_DEVICES] = {};
+
+int map_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return RAMBO_OK;
+    return e == cudaErrorMemoryAllocation ? RAMBO_ENOMEM : RAMBO_ECUDA;
+}
+
+}  // namespace
+
+// The fixed working memory.  In host code this name is a stand-in, not a
+// device address: host code must use the address cudaGetSymbolAddress gives.
+static __device__ __align__(256) unsigned char na_scratch[NA_SCRATCH_BYTES];
+
+namespace {
+
+// Device address of na_scratch on device dev (which must be current).
+int scratch_base(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return RAMBO_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_base[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, na_scratch);
+        if (e != cudaSuccess || !p) return map_cuda(e == cudaSuccess ? cudaErrorUnknown : e);
+        g_base[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_base[dev];
+    return RAMBO_OK;
+}
+
+int decode(unsigned long long e) {
+    if (e == NO_ERR) return RAMBO_OK;
+    switch ((unsigned)(e & 0xff)) {
+        case PRIO_ERANGE: return RAMBO_ERANGE;
+        case PRIO_EINVAL: return RAMBO_EINVAL;
+        case PRIO_EBADSEQ: return RAMBO_EBADSEQ;
+        default: return RAMBO_ECUDA;
+    }
+}
+
+#define NA_CK(x)                                       \
+    do {                                               \
+        cudaError_t e_ = (x);                          \
+        if (e_ != cudaSuccess) return map_cuda(e_);    \
+    } while (0)
+
+}  // namespace
+
+extern "C" int rambo_query_seq_batch_noalloc(rambo_t* h, const uint8_t* bases, const uint64_t* offsets,
+                                             uint64_t n_queries, uint32_t k, uint32_t* ids, uint64_t ids_cap,
+                                             uint64_t* id_offsets, uint64_t* needed, void* stream) {
+    if (!h || !offsets || !id_offsets || (!bases && n_queries) || (!ids && ids_cap)) return RAMBO_EINVAL;
+    if (k < 1 || k > 32) return RAMBO_EINVAL;
+    if (n_queries > NA_MAX_QUERIES) return RAMBO_E2BIG;
+    const uint64_t n = n_queries;
+    cudaStream_t s = (cudaStream_t)stream;
+    IndexView ix;
+    HashParams hp;
+    QueryTuning t;
+    int use_bitmap = 0, dev = 0;
+    int rc = handle_query_view(h, n ? n : 1, &ix, &hp, &t, &use_bitmap, &dev);
+    if (rc) return rc;
+    NA_CK(cudaSetDevice(dev));
+    unsigned char* base = nullptr;
+    rc = scratch_base(dev, &base);
+    if (rc) return rc;
+    if (n == 0) {
+        NA_CK(cudaMemsetAsync(id_offsets, 0, sizeof(uint64_t), s));
+        NA_CK(cudaStreamSynchronize(s));
+        if (needed) *needed = 0;
+        return RAMBO_OK;
+    }
+    uint64_t ends[2] = {0, 0};
+    NA_CK(cudaMemcpyAsync(&ends[0], offsets, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    NA_CK(cudaMemcpyAsync(&ends[1], offsets + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    NA_CK(cudaStreamSynchronize(s));
+    if (ends[1] < ends[0]) return RAMBO_EINVAL;
+    const uint64_t total = ends[1] - ends[0];
+    if (total > NA_MAX_BASES) return RAMBO_E2BIG;
+
+    DevStatus* st = reinterpret_cast<DevStatus*>(base + OFF_STATUS);
+    uint64_t* packed = reinterpret_cast<uint64_t*>(base + OFF_PACKED);
+    uint32_t* qcount = reinterpret_cast<uint32_t*>(base + OFF_QCOUNT);
+    uint64_t* qstart = reinterpret_cast<uint64_t*>(base + OFF_QSTART);
+    uint64_t* scan_tmp = reinterpret_cast<uint64_t*>(base + OFF_SCAN);
+    uint32_t* stage = reinterpret_cast<uint32_t*>(base + OFF_STAGE);
+
+    BatchView b{};
+    b.seq = 1;
+    b.offsets = offsets;
+    b.off0 = ends[0];
+    b.total = total;
+    b.n = n;
+    b.k = k;
+    b.set_ids = nullptr;
+    b.perm = nullptr;
+    NA_CK(launch_status_reset(st, s));  // clears error word, ticket, cursor, counters
+    NA_CK(launch_validate_batch(b, k, ix.K, st, s));
+    NA_CK(launch_pack(bases + ends[0], total, packed, total / 32 + 2, st, s));
+    b.packed = packed;
+    NA_CK(launch_resolve_bad_base(b, st, s));
+    QueryOut o{stage, NA_STAGE_IDS, qstart, qcount};
+    NA_CK(launch_query(ix, hp, b, o, t, use_bitmap, st, s));
+    NA_CK(launch_scan_counts(qcount, n, id_offsets, scan_tmp, NA_SCAN_WORDS, s));
+    DevStatus hst;
+    uint64_t total_ids = 0;
+    NA_CK(cudaMemcpyAsync(&hst, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    NA_CK(cudaMemcpyAsync(&total_ids, id_offsets + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    NA_CK(cudaStreamSynchronize(s));
+    rc = decode(hst.err);
+    if (rc) return rc;
+    if (hst.cursor > NA_STAGE_IDS) return RAMBO_E2BIG;
+    if (needed) *needed = total_ids;
+    if (total_ids > ids_cap) return RAMBO_ENOSPC;
+    NA_CK(launch_gather(o, id_offsets, n, ids, st, s));
+    NA_CK(cudaStreamSynchronize(s));
+    return RAMBO_OK;
+}

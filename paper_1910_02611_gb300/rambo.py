@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-OK, EINVAL, ERANGE, EBADSEQ, ENOMEM, ENOSPC, ECUDA, ETIMEOUT, EIO, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+OK, EINVAL, ERANGE, EBADSEQ, ENOMEM, ENOSPC, ECUDA, ETIMEOUT, EIO, ESTATE, E2BIG = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10
 
 _u64, _u32, _u16, _i32, _p = C.c_uint64, C.c_uint32, C.c_uint16, C.c_int, C.c_void_p
 
@@ -50,6 +50,7 @@ SIGNATURES = {
     "rambo_query_seq_batch": (_i32, [_p, _p, _p, _u64, _u32, _i32, C.POINTER(_p), C.POINTER(_p), _p]),
     "rambo_query_batch_into": (_i32, [_p, _p, _p, _u64, _i32, _p, _u64, _p, C.POINTER(_u64), _p]),
     "rambo_query_seq_batch_into": (_i32, [_p, _p, _p, _u64, _u32, _i32, _p, _u64, _p, C.POINTER(_u64), _p]),
+    "rambo_query_seq_batch_noalloc": (_i32, [_p, _p, _p, _u64, _u32, _p, _u64, _p, C.POINTER(_u64), _p]),
     "rambo_export_index": (_i32, [_p, _p, _u64]),
     "rambo_export_registered": (_i32, [_p, _p, _u64]),
     "rambo_export_partition": (_i32, [_p, _p, _u64]),
@@ -294,6 +295,17 @@ class Rambo:
         else:
             rc = L.rambo_query_seq_batch_into(self._h, *args, k, int(dev), ids_p, cap, oo, C.byref(needed), s)
         self._check(rc, "query_into")
+        return int(needed.value)
+
+    def query_seq_noalloc(self, bases, offsets, ids_out, id_offsets_out, k: int = 31, stream=None) -> int:
+        """Sequence query through the entry point that allocates nothing (all
+        arguments CUDA tensors owned by the caller; the library's fixed device
+        array holds the working memory).  Returns the number of IDs written."""
+        needed = _u64(0)
+        rc = load_library().rambo_query_seq_batch_noalloc(
+            self._h, bases.data_ptr(), offsets.data_ptr(), offsets.numel() - 1, k, ids_out.data_ptr(),
+            ids_out.numel(), id_offsets_out.data_ptr(), C.byref(needed), _stream_handle(stream))
+        self._check(rc, "query_seq_noalloc")
         return int(needed.value)
 
     def last_query_stats(self) -> dict:

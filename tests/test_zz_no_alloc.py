@@ -1,0 +1,73 @@
+"""The sequence query that allocates nothing (rambo_query_seq_batch_noalloc).
+
+It serves callers that cannot allocate device memory while they query, e.g.
+a serving thread with a fixed memory budget or code running where cudaMalloc
+is not allowed: its working memory is a fixed array the library reserves on
+each GPU.  Its answers must equal those of the allocating entry point
+(rambo_query_seq_batch_into) exactly -- set IDs are integers -- and must not
+depend on what an earlier call left in the shared array, so two calls in a
+row on different batches are compared.  This file runs last in the suite
+(its name sorts last) and also passes on its own in a fresh process."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_query_equals_allocating_query_on_two_calls_in_a_row():
+    import torch
+
+    from paper_1910_02611_gb300 import Rambo
+
+    dev = torch.device("cuda")
+    w = synth.make("genome", 0.02, m=1 << 18)
+    g = Rambo(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    g.insert(w.sets.ids, w.sets.data, w.sets.offsets, kind="seq", k=w.k)
+    # two different batches: the second call finds the first call's data in the array
+    batches = [w.queries.subset(np.arange(0, 700)), w.queries.subset(np.arange(700, 1000))]
+    for q in batches:
+        qd = torch.from_numpy(q.data).to(dev)
+        qo = torch.from_numpy(q.offsets.view(np.int64)).to(dev)
+        ref_ids = torch.empty(1 << 21, dtype=torch.int32, device=dev)
+        ref_off = torch.empty(len(q) + 1, dtype=torch.int64, device=dev)
+        n_ref = g.query_into(qd, qo, ref_ids, ref_off, kind="seq", k=w.k)
+        ids = torch.full((1 << 21,), -1, dtype=torch.int32, device=dev)
+        off = torch.full((len(q) + 1,), -1, dtype=torch.int64, device=dev)
+        n = g.query_seq_noalloc(qd, qo, ids, off, k=w.k)
+        assert n == n_ref
+        assert torch.equal(off, ref_off)
+        assert torch.equal(ids[:n], ref_ids[:n_ref])
+        assert n > 0
+    g.close()
+
+
+def test_noalloc_rejects_requests_beyond_its_fixed_scratch():
+    import torch
+
+    from paper_1910_02611_gb300 import E2BIG, ENOSPC, Rambo, RamboError
+
+    dev = torch.device("cuda")
+    w = synth.make("genome", 0.01, m=1 << 16)
+    g = Rambo(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    g.insert(w.sets.ids, w.sets.data, w.sets.offsets, kind="seq", k=w.k)
+    too_many = (1 << 19) + 1
+    qo = torch.zeros(too_many + 1, dtype=torch.int64, device=dev)
+    qd = torch.zeros(1, dtype=torch.uint8, device=dev)
+    out = torch.empty(16, dtype=torch.int32, device=dev)
+    off = torch.empty(too_many + 1, dtype=torch.int64, device=dev)
+    with pytest.raises(RamboError) as e:
+        g.query_seq_noalloc(qd, qo, out, off)
+    assert e.value.code == E2BIG
+    # a batch whose answers do not fit the caller's buffer reports the size needed
+    q = w.queries.subset(np.arange(200))
+    qd = torch.from_numpy(q.data).to(dev)
+    qo = torch.from_numpy(q.offsets.view(np.int64)).to(dev)
+    off = torch.empty(len(q) + 1, dtype=torch.int64, device=dev)
+    n_ref = g.query_into(qd, qo, torch.empty(1 << 20, dtype=torch.int32, device=dev), off, kind="seq")
+    if n_ref:
+        with pytest.raises(RamboError) as e:
+            g.query_seq_noalloc(qd, qo, torch.empty(n_ref - 1, dtype=torch.int32, device=dev), off)
+        assert e.value.code == ENOSPC
+    g.close()

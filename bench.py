@@ -338,7 +338,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, keys, probed, qk_ms, launches, n_ids = [], 0, 0, [], 0, 0
+    step_ms, keys, probed, rows_read, qk_ms, launches, n_ids = [], 0, 0, 0, [], 0, 0
     for i in range(args.steps):
         flush.zero_()
         e0.record(stream)
@@ -349,6 +349,7 @@ def run_ours(args):
         st = g.last_query_stats()
         keys += nk
         probed += st["keys_probed"]
+        rows_read += st["rows_read"]
         qk_ms.append(st["query_kernel_ms"])
         launches += st["kernel_launches"]
         n_ids += st["n_results"]
@@ -393,7 +394,7 @@ def run_ours(args):
     rows_per_key = w.R * w.eta
     row_bytes = g.row_stride * 4
     sectors_per_row = (row_bytes + SECTOR - 1) // SECTOR if row_bytes <= SECTOR else -(-row_bytes // SECTOR)
-    alg_bytes = probed * rows_per_key * sectors_per_row * SECTOR
+    alg_bytes = rows_read * sectors_per_row * SECTOR
     qk_total = sum(qk_ms)
     achieved = alg_bytes / (qk_total / 1000) / 1e9
     # random-row ceiling on a buffer the size of the index
@@ -410,8 +411,9 @@ def run_ours(args):
         blocks = torch.cuda.get_device_properties(dev).multi_processor_count * 8
         random_row_probe(buf, n_rows, g.row_stride, reads, blocks, 256)
         ms = random_row_probe(buf, n_rows, g.row_stride, reads, blocks, 256, seed=7)
-        rr_gbs = blocks * 256 * reads * SECTOR * sectors_per_row / (ms / 1000) / 1e9
-        rr = {"gbs": rr_gbs, "row_bytes": row_bytes, "buffer_bytes": n_rows * row_bytes,
+        rr_reads_s = blocks * 256 * reads / (ms / 1000)
+        rr_gbs = rr_reads_s * SECTOR * sectors_per_row / 1e9
+        rr = {"gbs": rr_gbs, "reads_per_s": rr_reads_s, "row_bytes": row_bytes, "buffer_bytes": n_rows * row_bytes,
               "frac_of_roofline": achieved / rr_gbs}
         del buf
     except Exception as ex:  # measurement helper only
@@ -462,7 +464,9 @@ def run_ours(args):
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(w.name),
             "kernel": "k_query", "peak_source": peaks["source"],
-            "bytes_model": f"{rows_per_key} rows x {sectors_per_row} sector(s) x 32 B per probed key",
+            "bytes_model": f"rows read (device counter) x {sectors_per_row} sector(s) x 32 B",
+            "rows_read_per_step": rows_read / args.steps,
+            "rows_per_submitted_key": rows_read / max(keys, 1),
             "query_kernel_ms_per_step": qk_total / args.steps,
         },
         "random_row_roofline": rr,

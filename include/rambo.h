@@ -234,6 +234,9 @@ typedef struct rambo_query_config {
     uint32_t cluster;         /* 1 = hand queries to warps grouped by their
                                * minimizer (smallest term hash), so overlapping
                                * queries run together and share cached rows */
+    uint32_t row_load;        /* cache operator of the row reads: 0 = ld.global.nc,
+                               * 1 = .cg, 2 = .cs, 3 = .lu, 4 = .cv,
+                               * 5 = .nc with L1::no_allocate */
 } rambo_query_config_t;
 
 int rambo_get_query_config(const rambo_t *h, rambo_query_config_t *out);
@@ -261,11 +264,12 @@ int rambo_load(const char *path, rambo_t **out);
 /* Measurement helper (no counterpart in the paper): every thread of
  * blocks x threads reads reads_per_thread random rows of a device buffer of
  * n_rows rows spaced row_words 32-bit words apart (the first
- * min(row_words, 4) words of each), as the query's row probes do.  *ms gets
- * the kernel time.  Gives the random-row throughput ceiling of the device. */
+ * min(row_words, 4) words of each), as the query's row probes do, with the
+ * cache operator row_load (as in rambo_query_config_t).  *ms gets the kernel
+ * time.  Gives the random-row throughput ceiling of the device. */
 int rambo_random_row_probe(const uint32_t *dev_buf, uint64_t n_rows, uint32_t row_words,
                            uint64_t reads_per_thread, uint32_t blocks, uint32_t threads,
-                           uint64_t seed, float *ms, void *stream);
+                           uint64_t seed, uint32_t row_load, float *ms, void *stream);
 
 /* The current CUDA context's L2 fetch granularity hint
  * (cudaLimitMaxL2FetchGranularity): stores the present value in *prev (if not

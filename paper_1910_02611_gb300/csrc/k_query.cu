@@ -7,10 +7,10 @@ const void* qk_kernel_ptr_e2(int V, int G);
 const void* qk_kernel_ptr_e4(int V, int G);
 cudaError_t qk_launch_e2(int V, int G, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const IndexView& ix,
                          const HashParams& hp, const BatchView& b, const QueryOut& o, int set_stage, int batch,
-                         uint32_t smem_per_warp, int use_bitmap, int order, DevStatus* st);
+                         uint32_t smem_per_warp, int use_bitmap, int order, int load_kind, DevStatus* st);
 cudaError_t qk_launch_e4(int V, int G, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const IndexView& ix,
                          const HashParams& hp, const BatchView& b, const QueryOut& o, int set_stage, int batch,
-                         uint32_t smem_per_warp, int use_bitmap, int order, DevStatus* st);
+                         uint32_t smem_per_warp, int use_bitmap, int order, int load_kind, DevStatus* st);
 
 static const void* kernel_ptr(int V, int G, uint32_t eta) {
     return eta <= 2 ? qk_kernel_ptr_e2(V, G) : qk_kernel_ptr_e4(V, G);
@@ -54,9 +54,9 @@ cudaError_t launch_query(const IndexView& ix, const HashParams& hp, const BatchV
     dim3 grid((unsigned)t.blocks), block((unsigned)(t.warps_per_block * 32));
     if (ix.eta <= 2)
         return qk_launch_e2(t.V, t.G, grid, block, smem, s, ix, hp, b, o, t.set_stage, t.batch, spw, use_bitmap,
-                            t.order, st);
+                            t.order, t.load_kind, st);
     return qk_launch_e4(t.V, t.G, grid, block, smem, s, ix, hp, b, o, t.set_stage, t.batch, spw, use_bitmap, t.order,
-                        st);
+                        t.load_kind, st);
 }
 
 }  // namespace rgb

@@ -38,15 +38,15 @@ constexpr int QK_ID_CAP = 128;  // per-warp staging of dense-stage survivors
 __host__ __device__ inline uint32_t qk_bitmap_words(uint64_t K) { return (uint32_t)((K + 31) / 32); }
 
 template <int V>
-__device__ __forceinline__ void qk_load(const uint32_t* __restrict__ p, uint32_t (&out)[V]) {
+__device__ __forceinline__ void qk_load(const uint32_t* __restrict__ p, uint32_t (&out)[V], int kind) {
     if constexpr (V == 1) {
-        out[0] = __ldg(p);
+        out[0] = ld_row1(p, kind);
     } else if constexpr (V == 2) {
-        uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+        uint2 t = ld_row2(p, kind);
         out[0] = t.x;
         out[1] = t.y;
     } else {
-        uint4 t = __ldg(reinterpret_cast<const uint4*>(p));
+        uint4 t = ld_row4(p, kind);
         out[0] = t.x;
         out[1] = t.y;
         out[2] = t.z;
@@ -85,7 +85,7 @@ __device__ __forceinline__ bool qk_set_passes(const IndexView& ix, const uint32_
 template <int V, int G, int ETA>
 __global__ void __launch_bounds__(QK_THREADS_MAX)
     k_query(IndexView ix, HashParams hp, BatchView b, QueryOut o, int set_stage, int batch,
-            uint32_t smem_per_warp, int use_bitmap, int order, DevStatus* st) {
+            uint32_t smem_per_warp, int use_bitmap, int order, int load_kind, DevStatus* st) {
     extern __shared__ uint32_t qk_smem[];
     constexpr int KPS = 32 / G;  // terms per warp step
     const unsigned lane = threadIdx.x & 31;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                         for (int j = 0; j < ETA; ++j) {
                             if (j < eta) {
                                 const uint64_t pos = (hp.s[r][j] * y) >> ix.shift;
-                                qk_load<V>(rb + pos * ix.S, val[r][j]);
+                                qk_load<V>(rb + pos * ix.S, val[r][j], load_kind);
                             }
                         }
                     }

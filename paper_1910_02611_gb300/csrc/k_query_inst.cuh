@@ -24,11 +24,11 @@ const void* QK_CAT(qk_kernel_ptr_, QK_SUFFIX)(int V, int G) {
 cudaError_t QK_CAT(qk_launch_, QK_SUFFIX)(int V, int G, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                                           const IndexView& ix, const HashParams& hp, const BatchView& b,
                                           const QueryOut& o, int set_stage, int batch, uint32_t smem_per_warp,
-                                          int use_bitmap, int order, DevStatus* st) {
+                                          int use_bitmap, int order, int load_kind, DevStatus* st) {
 #define X(v, g)                                                                                        \
     if (V == v && G == g) {                                                                            \
         k_query<v, g, QK_ETA><<<grid, block, smem, s>>>(ix, hp, b, o, set_stage, batch, smem_per_warp, \
-                                                        use_bitmap, order, st);                        \
+                                                        use_bitmap, order, load_kind, st);             \
         return cudaGetLastError();                                                                     \
     }
     QK_VG_LIST(X)

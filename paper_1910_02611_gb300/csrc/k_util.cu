@@ -105,22 +105,42 @@ __device__ __forceinline__ int base_code(unsigned ch) {
     return ok ? (int)(x ^ (x >> 1)) : -1;
 }
 
+// four ASCII bytes of a little-endian word -> four 2-bit codes; *bad gets the
+// lowest byte index (0..3) holding something other than ACGTacgt, or 4
+__device__ __forceinline__ uint32_t codes4(uint32_t w, int* bad) {
+    const uint32_t u = w | 0x20202020u;
+    const uint32_t x = (u >> 1) & 0x03030303u;
+    const uint32_t c = x ^ ((x >> 1) & 0x01010101u);  // a->0 c->1 g->2 t->3 per byte
+    *bad = 4;
+#pragma unroll
+    for (int t = 3; t >= 0; --t) {
+        const uint32_t ch = (u >> (8 * t)) & 0xffu;
+        if (!((ch == 'a') | (ch == 'c') | (ch == 'g') | (ch == 't'))) *bad = t;
+    }
+    return c;
+}
+
 __global__ void k_pack(const uint8_t* __restrict__ bases, uint64_t total, uint64_t* __restrict__ packed,
                        uint64_t n_words, DevStatus* st) {
+    const bool aligned = (reinterpret_cast<uintptr_t>(bases) & 15) == 0;
     for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < n_words;
          w += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t v = 0;
         uint64_t p0 = w * 32;
         unsigned long long bad = NO_ERR;
-        if (p0 + 32 <= total) {
+        if (aligned && p0 + 32 <= total) {
+            // two 16-byte loads, four bases per 32-bit word
+            const uint4* q = reinterpret_cast<const uint4*>(bases + p0);
+            const uint4 lo = __ldg(q), hi = __ldg(q + 1);
+            const uint32_t wd[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
-            for (int t = 0; t < 32; ++t) {
-                int c = base_code(__ldg(bases + p0 + t));
-                if (c < 0) {
-                    if (bad == NO_ERR) bad = p0 + t;
-                    c = 0;
-                }
-                v |= (uint64_t)c << (62 - 2 * t);
+            for (int i = 0; i < 8; ++i) {
+                int b4;
+                const uint32_t c = codes4(wd[i], &b4);
+                if (b4 < 4 && bad == NO_ERR) bad = p0 + 4 * i + b4;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    v |= (uint64_t)((c >> (8 * t)) & 3u) << (62 - 2 * (4 * i + t));
             }
         } else {
             for (int t = 0; t < 32; ++t) {

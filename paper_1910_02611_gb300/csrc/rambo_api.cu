@@ -203,6 +203,7 @@ void default_config(rambo* h) {
     h->cfg.visit_order = 2;
     h->cfg.l2_fetch_bytes = 0;
     h->cfg.cluster = 0;
+    h->cfg.row_load = 0;
 }
 
 int decode_err(rambo* h, unsigned long long e) {
@@ -327,6 +328,7 @@ int resolve_tuning(rambo* h, uint64_t n, int& use_bitmap, QueryTuning& t) {
     t.warps_per_block = (int)h->cfg.warps_per_block;
     t.set_stage = (int)h->cfg.set_stage;
     t.order = (int)h->cfg.visit_order;
+    t.load_kind = (int)h->cfg.row_load;
     use_bitmap = (h->mem_off && t.set_stage != 1 && (h->K + 31) / 32 <= 4096) ? 1 : 0;
     const size_t smem =
         (size_t)query_smem_words_per_warp(h->R, h->S, h->K, use_bitmap) * 4 * (size_t)t.warps_per_block;
@@ -701,7 +703,7 @@ int rambo_set_query_config(rambo_t* h, const rambo_query_config_t* cfg) {
     if (cfg->warps_per_block < 1 || cfg->warps_per_block > 8) return RAMBO_EINVAL;
     if (cfg->set_stage > 2) return RAMBO_EINVAL;
     if (cfg->set_stage == 2 && !h->mem_off) return RAMBO_EINVAL;
-    if (cfg->visit_order > 2 || cfg->cluster > 1) return RAMBO_EINVAL;
+    if (cfg->visit_order > 2 || cfg->cluster > 1 || cfg->row_load > 5) return RAMBO_EINVAL;
     if (cfg->l2_fetch_bytes && cfg->l2_fetch_bytes != 32 && cfg->l2_fetch_bytes != 64 && cfg->l2_fetch_bytes != 128)
         return RAMBO_EINVAL;
     h->cfg = *cfg;
@@ -726,6 +728,7 @@ int rambo_list_query_configs(const rambo_t* h, rambo_query_config_t* out, int ca
                 out[n].visit_order = 2;
                 out[n].l2_fetch_bytes = 0;
                 out[n].cluster = 0;
+                out[n].row_load = 0;
             }
             ++n;
         }
@@ -820,10 +823,11 @@ int rambo_load(const char* path, rambo_t** out) {
 }
 
 int rambo_random_row_probe(const uint32_t* dev_buf, uint64_t n_rows, uint32_t row_words, uint64_t reads_per_thread,
-                           uint32_t blocks, uint32_t threads, uint64_t seed, float* ms, void* stream) {
+                           uint32_t blocks, uint32_t threads, uint64_t seed, uint32_t row_load, float* ms,
+                           void* stream) {
     if (!dev_buf || !ms || !blocks || !threads || threads > 256 || !n_rows)
         return RAMBO_EINVAL;
-    if (!(row_words == 1 || row_words == 2 || row_words % 4 == 0)) return RAMBO_EINVAL;
+    if (!(row_words == 1 || row_words == 2 || row_words % 4 == 0) || row_load > 5) return RAMBO_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     uint32_t* sink = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -832,7 +836,8 @@ int rambo_random_row_probe(const uint32_t* dev_buf, uint64_t n_rows, uint32_t ro
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
     if (e == cudaSuccess)
-        e = launch_random_rows(dev_buf, n_rows, row_words, reads_per_thread, seed, sink, (int)blocks, (int)threads, s);
+        e = launch_random_rows(dev_buf, n_rows, row_words, reads_per_thread, seed, sink, (int)blocks, (int)threads,
+                               (int)row_load, s);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);

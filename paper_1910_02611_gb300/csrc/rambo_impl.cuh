@@ -81,6 +81,58 @@ __device__ __forceinline__ uint64_t kmer_at(const uint64_t* __restrict__ packed,
     return win >> (64 - 2 * k);
 }
 
+// Loads of one, two or four 32-bit words of an index row with a selectable
+// cache operator: 0 = ld.global.nc (read-only path), 1 = .cg (L2 only),
+// 2 = .cs (streaming, evict first), 3 = .lu (last use), 4 = .cv (uncached),
+// 5 = ld.global.nc.L1::no_allocate.  The row data and results never depend on
+// the choice; it only changes how the memory system fetches isolated rows.
+__device__ __forceinline__ uint32_t ld_row1(const uint32_t* p, int kind) {
+    switch (kind) {
+        case 1: return __ldcg(p);
+        case 2: return __ldcs(p);
+        case 3: return __ldlu(p);
+        case 4: return __ldcv(p);
+        case 5: {
+            uint32_t v;
+            asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+            return v;
+        }
+        default: return __ldg(p);
+    }
+}
+__device__ __forceinline__ uint2 ld_row2(const uint32_t* p, int kind) {
+    const uint2* q = reinterpret_cast<const uint2*>(p);
+    switch (kind) {
+        case 1: return __ldcg(q);
+        case 2: return __ldcs(q);
+        case 3: return __ldlu(q);
+        case 4: return __ldcv(q);
+        case 5: {
+            uint2 v;
+            asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(q));
+            return v;
+        }
+        default: return __ldg(q);
+    }
+}
+__device__ __forceinline__ uint4 ld_row4(const uint32_t* p, int kind) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+    switch (kind) {
+        case 1: return __ldcg(q);
+        case 2: return __ldcs(q);
+        case 3: return __ldlu(q);
+        case 4: return __ldcv(q);
+        case 5: {
+            uint4 v;
+            asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                         : "l"(q));
+            return v;
+        }
+        default: return __ldg(q);
+    }
+}
+
 __device__ __forceinline__ void record_error(DevStatus* st, uint64_t index, unsigned prio) {
     atomicMin(&st->err, (unsigned long long)((index << 8) | prio));
 }
@@ -128,7 +180,8 @@ struct QueryTuning {
     int blocks;            // grid size
     int set_stage;         // 1 dense, 2 sparse, 0 auto
     int batch;             // queries taken per ticket
-    int order;             // 0 input order, 1 strided
+    int order;             // 0 input order, 1 strided, 2 strided + table-0 screening
+    int load_kind;         // cache operator of the row loads (see ld_row1)
 };
 
 // ---------------------------------------------------------------------------
@@ -178,6 +231,6 @@ int handle_query_view(rambo_t* h, uint64_t n, IndexView* ix, HashParams* hp, Que
 // k_roofline.cu
 cudaError_t launch_random_rows(const uint32_t* buf, uint64_t n_rows, uint32_t row_words,
                                uint64_t reads_per_thread, uint64_t seed, uint32_t* sink,
-                               int blocks, int threads, cudaStream_t s);
+                               int blocks, int threads, int load_kind, cudaStream_t s);
 
 }  // namespace rgb

@@ -33,7 +33,7 @@ class QueryStats(C.Structure):
 class QueryConfig(C.Structure):
     _fields_ = [("lanes_per_key", _u32), ("words_per_lane", _u32), ("warps_per_block", _u32),
                 ("blocks_per_sm", _u32), ("set_stage", _u32), ("visit_order", _u32), ("l2_fetch_bytes", _u32),
-                ("cluster", _u32)]
+                ("cluster", _u32), ("row_load", _u32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -62,7 +62,7 @@ SIGNATURES = {
     "rambo_set_build_tiling": (_i32, [_p, _u64, _i32]),
     "rambo_save": (_i32, [_p, C.c_char_p]),
     "rambo_load": (_i32, [C.c_char_p, C.POINTER(_p)]),
-    "rambo_random_row_probe": (_i32, [_p, _u64, _u32, _u64, _u32, _u32, _u64, C.POINTER(C.c_float), _p]),
+    "rambo_random_row_probe": (_i32, [_p, _u64, _u32, _u64, _u32, _u32, _u64, _u32, C.POINTER(C.c_float), _p]),
     "rambo_l2_fetch_granularity": (_i32, [_u32, C.POINTER(_u32)]),
     "rambo_last_error_item": (_u64, [_p]),
     "rambo_strerror": (C.c_char_p, [_i32]),
@@ -378,11 +378,11 @@ def l2_fetch_granularity(bytes_: int = 0) -> int:
 
 
 def random_row_probe(buf, n_rows: int, row_words: int, reads_per_thread: int, blocks: int, threads: int = 256,
-                     seed: int = 1, stream=None) -> float:
+                     seed: int = 1, row_load: int = 0, stream=None) -> float:
     """Times the random-row read microbenchmark over a CUDA tensor; returns ms."""
     ms = C.c_float(0)
     rc = load_library().rambo_random_row_probe(buf.data_ptr(), n_rows, row_words, reads_per_thread, blocks, threads,
-                                               seed, C.byref(ms), _stream_handle(stream))
+                                               seed, row_load, C.byref(ms), _stream_handle(stream))
     if rc:
         raise RamboError(rc, "random_row_probe")
     return float(ms.value)

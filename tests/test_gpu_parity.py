@@ -308,3 +308,33 @@ def test_tiled_construction_matches_oracle(mods, tile_bytes):
         o2 = Oracle(10, 40, 3, 1 << 17, 2, 5)
         o2.insert_keys_batch(np.arange(10, dtype=np.uint64), keys, off)
         assert_index_equal(g2, o2)
+
+
+def test_pack_aligned_and_unaligned_inputs(mods):
+    # sequences starting at every alignment of the base array (16-byte vector
+    # path and byte path of the packer), with and without a bad byte
+    import torch
+
+    from paper_1910_02611_gb300 import EBADSEQ, RamboError
+
+    Rambo, Oracle = mods
+    rng = np.random.default_rng(21)
+    seqs = _rand_seq(rng, 3000)
+    g = Rambo(8, 16, 3, 1 << 12, 2, 4)
+    o = Oracle(8, 16, 3, 1 << 12, 2, 4)
+    off = np.array([0, 400, 900, 1500, 2100, 2500, 2800, 2900, 3000], np.uint64)
+    g.insert(np.arange(8, dtype=np.uint64), seqs, off, kind="seq")
+    o.insert_seq_batch(np.arange(8, dtype=np.uint64), seqs, off, 31)
+    dev_bases = torch.from_numpy(seqs.copy()).cuda()
+    for start in (0, 1, 3, 8, 13, 16, 31):
+        qo = np.arange(start, start + 20 * 97 + 1, 97, dtype=np.uint64)
+        ids, offs = g.query(dev_bases, torch.from_numpy(qo.view(np.int64)).cuda(), kind="seq")
+        rids, roff = o.query_batch("seq", seqs, qo, k=31)
+        assert np.array_equal(offs.cpu().numpy().view(np.uint64), roff)
+        assert np.array_equal(ids.cpu().numpy().view(np.uint32), rids)
+        for bad_at in (start + 5, start + 97 * 3 + 31, start + 97 * 7):
+            b = seqs.copy()
+            b[bad_at] = ord("x")
+            with pytest.raises(RamboError) as e:
+                g.query(torch.from_numpy(b).cuda(), torch.from_numpy(qo.view(np.int64)).cuda(), kind="seq")
+            assert e.value.code == EBADSEQ and e.value.item == (bad_at - start) // 97

@@ -63,6 +63,9 @@ def parse_args():
     ap.add_argument("--m-log2", type=int, default=None, help="override the Bloom filter size m = 2^L")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the query steps only (no e2e, random-row or CPU legs): the profiling case")
+    ap.add_argument("--per-query-baseline", type=int, default=2000,
+                    help="queries timed through the one-query-per-launch kernel (0 = skip)")
+    ap.add_argument("--autotune", action="store_true", help="pick the kernel configuration on batch 0 first")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -316,7 +319,16 @@ def run_ours(args):
         qd = torch.from_numpy(q.data.view(np.int64) if q.kind == "keys" else q.data).to(dev)
         qo = torch.from_numpy(q.offsets.view(np.int64)).to(dev)
         dev_batches.append((qd, qo, keys_in(q, w.k), len(q)))
-    out_cap = 1 << 24
+    tuned = None
+    if args.autotune:
+        qd0, qo0, _, _ = dev_batches[0]
+        tuned = g.autotune(qd0, qo0, kind=batches[0].kind, k=w.k, reps=2)
+    # size the caller-owned result buffer from one call through the allocating entry point
+    need = 0
+    for qd, qo, _, _ in dev_batches:
+        _, offs = g.query(qd, qo, kind=batches[0].kind, k=w.k)
+        need = max(need, int(offs[-1].item()))
+    out_cap = max(1 << 20, int(need * 1.05) + 1024)
     out_ids = torch.empty(out_cap, dtype=torch.int32, device=dev)
     out_off = torch.empty(max(len(q) for q in batches) + 1, dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -377,6 +389,28 @@ def run_ours(args):
         e2e_keys += nk
         h2d += hd.nbytes + ho.nbytes
         d2h += offs.nbytes + ids.nbytes
+
+    # ---- the plain one-query-per-launch kernel on the same GPU (identical results) ----
+    per_launch = None
+    if args.per_query_baseline and not args.no_extras:
+        q0 = batches[0]
+        nq = min(args.per_query_baseline, len(q0))
+        sub = q0.subset(np.arange(nq))
+        sd = torch.from_numpy(sub.data.view(np.int64) if sub.kind == "keys" else sub.data).to(dev)
+        torch.cuda.synchronize()
+        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pe0.record(stream)
+        pids, poff = g.query_one_per_launch(sd, sub.offsets, kind=sub.kind, k=w.k)
+        pe1.record(stream)
+        pe1.synchronize()
+        p_ms = pe0.elapsed_time(pe1)
+        bids, boff = g.query(sd, torch.from_numpy(sub.offsets.view(np.int64)).to(dev), kind=sub.kind, k=w.k)
+        same = bool(np.array_equal(poff, boff.cpu().numpy().view(np.uint64)) and
+                    np.array_equal(pids, bids.cpu().numpy().view(np.uint32)))
+        per_launch = {"value": keys_in(sub, w.k) / (p_ms / 1000), "unit": UNIT, "queries": nq,
+                      "launches": nq, "identical_results": same,
+                      "note": "one thread block launched per query, same GPU, first queries of batch 0 "
+                              "(includes the per-launch host loop; host offsets)"}
 
     # ---- reduce over ranks ----
     if dist:
@@ -448,10 +482,10 @@ def run_ours(args):
         "data": "synthetic",
         "config": {
             "workload": f"{w.name}: K={w.K} sets, B={w.B}, R={w.R}, m=2^{int(np.log2(w.m))}, eta={w.eta}, k={w.k}; "
-                        f"{len(batches[0])} query sequences per step (scale {args.scale})",
+                        f"{len(batches[0])} {'query sequences' if batches[0].kind == 'seq' else 'key queries'} "
+                        f"per step (scale {args.scale})",
             "parallelism": f"replicas x{world} (one index per GPU, disjoint batches)",
-            "l2": "flushed before every step (256 MiB write); index 6 GiB > L2" if w.name == "genome" else
-                  "flushed before every step (256 MiB write)",
+            "l2": f"flushed before every step (256 MiB write); index {g.info().index_bytes / 2**30:.1f} GiB",
             "batches": len(batches),
         },
         "batch_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
@@ -473,6 +507,8 @@ def run_ours(args):
         "construction": {"keys": build_keys, "ms": build_ms, "keys_per_s": build_keys / (build_ms / 1000)},
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "per_query_launch_baseline": per_launch,
+        "query_config": tuned or g.get_config(),
         "setup_s": {"workload_generation": t_gen},
     }
     print(json.dumps(line), flush=True)

@@ -177,6 +177,21 @@ int rambo_query_seq_batch_noalloc(rambo_t *h, const uint8_t *bases, const uint64
                                   uint64_t n_queries, uint32_t k, uint32_t *ids, uint64_t ids_cap,
                                   uint64_t *id_offsets, uint64_t *needed, void *stream);
 
+/* The plain one-query-per-launch kernel, kept as the measurement baseline of
+ * the batched path (no counterpart in the paper, which runs one query at a
+ * time on one CPU thread, Sec. 5.2).  For every query q one thread block is
+ * launched on `stream` that answers Algorithm 2 (with Sec. 3.2.1 for
+ * sequences) for q alone, without early exit, packing pass or work queue,
+ * and writes its ascending IDs to ids + q*K and their number to counts[q].
+ * kind 0: data = device uint64 keys; kind 1: data = device ASCII bases.
+ * host_offsets (n+1 entries) are in host memory so the launch loop needs no
+ * device reads; ids must hold n*K entries, counts n.  Returns after the last
+ * launch has finished.  Errors: RAMBO_EINVAL (empty query, k outside
+ * [1,32]), RAMBO_EBADSEQ (a byte outside ACGTacgt). */
+int rambo_query_one_per_launch(rambo_t *h, int kind, const void *data, const uint64_t *host_offsets,
+                               uint64_t n_queries, uint32_t k, uint32_t *ids, uint32_t *counts,
+                               void *stream);
+
 /* Copies the bit-sliced index to host memory: n_words must equal
  * R * m * row_stride; word (r*m + p)*row_stride + w holds bits 32w..32w+31 of
  * row (r, p), bit b of the row being bit p of the Bloom filter of cell b of
@@ -253,6 +268,14 @@ int rambo_set_build_tiling(rambo_t *h, uint64_t tile_bytes, int mode);
 /* Lists the query-kernel configurations valid for this handle (at most cap),
  * returns how many there are. */
 int rambo_list_query_configs(const rambo_t *h, rambo_query_config_t *out, int cap);
+
+/* Autotuner: times every query-kernel configuration the handle supports
+ * (lanes per key, words per lane, warps per block, visiting order) on the
+ * given sample batch (kind and pointers as in the query calls), `reps` runs
+ * each, keeps the configuration with the smallest device time, stores it in
+ * the handle and in *best.  Results never depend on the choice. */
+int rambo_autotune(rambo_t *h, int kind, const void *data, const uint64_t *offsets, uint64_t n_queries,
+                   uint32_t k, int on_device, int reps, rambo_query_config_t *best, void *stream);
 
 /* Checkpoint (no counterpart in the paper, which keeps its index in memory):
  * writes the parameters, the registered-set bitmap and the rows to a file;

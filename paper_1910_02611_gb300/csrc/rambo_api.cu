@@ -736,6 +736,75 @@ int rambo_list_query_configs(const rambo_t* h, rambo_query_config_t* out, int ca
     return n;
 }
 
+int rambo_query_one_per_launch(rambo_t* h, int kind, const void* data, const uint64_t* host_offsets,
+                               uint64_t n_queries, uint32_t k, uint32_t* ids, uint32_t* counts, void* stream) {
+    if (!h || !host_offsets || (!data && n_queries) || (n_queries && (!ids || !counts))) return RAMBO_EINVAL;
+    if (kind == 1 && (k < 1 || k > 32)) return RAMBO_EINVAL;
+    if (kind != 0 && kind != 1) return RAMBO_EINVAL;
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    for (uint64_t q = 0; q < n_queries; ++q) {
+        if (host_offsets[q + 1] < host_offsets[q]) return RAMBO_EINVAL;
+        const uint64_t len = host_offsets[q + 1] - host_offsets[q];
+        if (kind == 0 && len == 0) return RAMBO_EINVAL;
+        if (kind == 1 && len < k) return RAMBO_EBADSEQ;
+    }
+    int* d_bad = reinterpret_cast<int*>(&h->st->spare[0]);
+    CK(cudaMemsetAsync(d_bad, 0, sizeof(int), s));
+    const IndexView ix = h->view();
+    for (uint64_t q = 0; q < n_queries; ++q) {
+        const uint64_t a = host_offsets[q], len = host_offsets[q + 1] - a;
+        const uint8_t* bp = kind == 1 ? static_cast<const uint8_t*>(data) + a : nullptr;
+        const uint64_t* kp = kind == 0 ? static_cast<const uint64_t*>(data) + a : nullptr;
+        CK(launch_query_one(ix, h->hp, kind, bp, kp, len, k, ids + q * h->K, counts + q, d_bad, s));
+    }
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return bad ? RAMBO_EBADSEQ : RAMBO_OK;
+}
+
+int rambo_autotune(rambo_t* h, int kind, const void* data, const uint64_t* offsets, uint64_t n_queries, uint32_t k,
+                   int on_device, int reps, rambo_query_config_t* best, void* stream) {
+    if (!h || (kind != 0 && kind != 1) || reps < 1) return RAMBO_EINVAL;
+    const int n = rambo_list_query_configs(h, nullptr, 0);
+    std::vector<rambo_query_config_t> cands(n > 0 ? n : 1);
+    rambo_list_query_configs(h, cands.data(), n);
+    const rambo_query_config_t keep = h->cfg;
+    rambo_query_config_t win = keep;
+    float win_ms = -1.0f;
+    for (int c = 0; c < n; ++c) {
+        for (uint32_t order = 1; order <= 2; ++order) {
+            rambo_query_config_t cfg = cands[c];
+            cfg.visit_order = order;
+            cfg.set_stage = keep.set_stage;
+            cfg.row_load = keep.row_load;
+            if (rambo_set_query_config(h, &cfg) != RAMBO_OK) continue;
+            float t_min = -1.0f;
+            for (int r = 0; r < reps; ++r) {
+                const uint32_t* ids = nullptr;
+                const uint64_t* off = nullptr;
+                int rc = kind == 0 ? rambo_query_batch(h, static_cast<const uint64_t*>(data), offsets, n_queries,
+                                                       on_device, &ids, &off, stream)
+                                   : rambo_query_seq_batch(h, static_cast<const uint8_t*>(data), offsets, n_queries, k,
+                                                           on_device, &ids, &off, stream);
+                if (rc) {
+                    h->cfg = keep;
+                    return rc;
+                }
+                if (t_min < 0 || h->last.device_ms < t_min) t_min = h->last.device_ms;
+            }
+            if (win_ms < 0 || t_min < win_ms) {
+                win_ms = t_min;
+                win = cfg;
+            }
+        }
+    }
+    h->cfg = win;
+    if (best) *best = win;
+    return RAMBO_OK;
+}
+
 int rambo_set_build_tiling(rambo_t* h, uint64_t tile_bytes, int mode) {
     if (!h || mode < 0 || mode > 2) return RAMBO_EINVAL;
     if (tile_bytes) {

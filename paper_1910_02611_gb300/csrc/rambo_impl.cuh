@@ -224,6 +224,11 @@ int query_max_blocks_per_sm(int V, int G, uint32_t eta, int warps_per_block, siz
 cudaError_t launch_query(const IndexView& ix, const HashParams& hp, const BatchView& b, const QueryOut& o,
                          const QueryTuning& t, int use_bitmap, DevStatus* st, cudaStream_t s);
 
+// k_query_one.cu: the plain one-query-per-launch kernel
+cudaError_t launch_query_one(const IndexView& ix, const HashParams& hp, int seq, const uint8_t* bases,
+                             const uint64_t* keys, uint64_t len, uint32_t k, uint32_t* out_ids, uint32_t* out_count,
+                             int* bad, cudaStream_t s);
+
 // rambo_api.cu: what the fixed-scratch entry point needs from a handle
 int handle_query_view(rambo_t* h, uint64_t n, IndexView* ix, HashParams* hp, QueryTuning* t, int* use_bitmap,
                       int* device);

@@ -60,6 +60,8 @@ SIGNATURES = {
     "rambo_set_query_config": (_i32, [_p, C.POINTER(QueryConfig)]),
     "rambo_list_query_configs": (_i32, [_p, _p, _i32]),
     "rambo_set_build_tiling": (_i32, [_p, _u64, _i32]),
+    "rambo_query_one_per_launch": (_i32, [_p, _i32, _p, _p, _u64, _u32, _p, _p, _p]),
+    "rambo_autotune": (_i32, [_p, _i32, _p, _p, _u64, _u32, _i32, _i32, C.POINTER(QueryConfig), _p]),
     "rambo_save": (_i32, [_p, C.c_char_p]),
     "rambo_load": (_i32, [C.c_char_p, C.POINTER(_p)]),
     "rambo_random_row_probe": (_i32, [_p, _u64, _u32, _u64, _u32, _u32, _u64, _u32, C.POINTER(C.c_float), _p]),
@@ -307,6 +309,45 @@ class Rambo:
             ids_out.numel(), id_offsets_out.data_ptr(), C.byref(needed), _stream_handle(stream))
         self._check(rc, "query_seq_noalloc")
         return int(needed.value)
+
+    def query_one_per_launch(self, data, host_offsets, kind: str = "seq", k: int = 31, stream=None):
+        """The plain one-query-per-launch baseline (one thread block launched per
+        query).  data: CUDA tensor; host_offsets: numpy.  Returns (ids, offsets)
+        as numpy arrays in the same CSR form as query()."""
+        torch = _torch()
+        off = _host_arr(host_offsets, np.uint64)
+        n = off.size - 1
+        ids = torch.empty(max(n, 1) * self.K, dtype=torch.int32, device=data.device)
+        cnt = torch.empty(max(n, 1), dtype=torch.int32, device=data.device)
+        rc = load_library().rambo_query_one_per_launch(self._h, 0 if kind == "keys" else 1, data.data_ptr(),
+                                                       off.ctypes.data, n, k, ids.data_ptr(), cnt.data_ptr(),
+                                                       _stream_handle(stream))
+        self._check(rc, "query_one_per_launch")
+        counts = cnt[:n].cpu().numpy().astype(np.uint64)
+        out_off = np.zeros(n + 1, np.uint64)
+        np.cumsum(counts, out=out_off[1:])
+        per = ids[: n * self.K].view(n, self.K).cpu().numpy().view(np.uint32) if n else np.zeros((0, self.K), np.uint32)
+        flat = np.concatenate([per[q, : int(counts[q])] for q in range(n)]) if n else np.zeros(0, np.uint32)
+        return flat.astype(np.uint32), out_off
+
+    def autotune(self, data, offsets, kind: str = "seq", k: int = 31, reps: int = 3, stream=None) -> dict:
+        """Times every kernel configuration on a sample batch, keeps the fastest."""
+        dev = _is_cuda_tensor(data)
+        if dev:
+            dp, op, n = data.data_ptr(), offsets.data_ptr(), offsets.numel() - 1
+            keep = None
+        else:
+            d = _host_arr(data, np.uint64 if kind == "keys" else np.uint8)
+            off = _host_arr(offsets, np.uint64)
+            _check_csr(d, off, "autotune")
+            keep = (d, off)
+            dp, op, n = d.ctypes.data, off.ctypes.data, off.size - 1
+        best = QueryConfig()
+        rc = load_library().rambo_autotune(self._h, 0 if kind == "keys" else 1, dp, op, n, k, int(dev), reps,
+                                           C.byref(best), _stream_handle(stream))
+        del keep
+        self._check(rc, "autotune")
+        return best.as_dict()
 
     def last_query_stats(self) -> dict:
         st = QueryStats()

@@ -338,3 +338,28 @@ def test_pack_aligned_and_unaligned_inputs(mods):
             with pytest.raises(RamboError) as e:
                 g.query(torch.from_numpy(b).cuda(), torch.from_numpy(qo.view(np.int64)).cuda(), kind="seq")
             assert e.value.code == EBADSEQ and e.value.item == (bad_at - start) // 97
+
+
+def test_one_query_per_launch_baseline_matches_oracle(mods):
+    import torch
+
+    Rambo, Oracle = mods
+    for name, kw in (("genome", dict(m=1 << 18)), ("document", dict(m=1 << 16))):
+        w = synth.make(name, 0.01, **kw)
+        g, o = build_pair(w, Rambo, Oracle)
+        q = w.queries.subset(np.arange(min(300, len(w.queries))))
+        dd = torch.from_numpy(q.data.view(np.int64) if q.kind == "keys" else q.data).cuda()
+        ids, off = g.query_one_per_launch(dd, q.offsets, kind=q.kind, k=w.k)
+        rids, roff = o.query_batch(q.kind, q.data, q.offsets, k=w.k)
+        assert np.array_equal(off, roff) and np.array_equal(ids, rids)
+
+
+def test_autotune_picks_a_config_and_results_stay_identical(mods):
+    Rambo, Oracle = mods
+    w = synth.make("genome", 0.02, m=1 << 18)
+    g, o = build_pair(w, Rambo, Oracle)
+    q = w.queries.subset(np.arange(500))
+    best = g.autotune(q.data, q.offsets, kind="seq", reps=2)
+    assert best == g.get_config()
+    assert best["visit_order"] in (1, 2)
+    assert_query_equal(g, o, w.queries)

@@ -192,6 +192,89 @@ int rambo_query_one_per_launch(rambo_t *h, int kind, const void *data, const uin
                                uint64_t n_queries, uint32_t k, uint32_t *ids, uint32_t *counts,
                                void *stream);
 
+/* ---- Graph-captured query plans (no counterpart in the paper) ----
+ * A plan owns device and pinned host buffers for batches of up to
+ * max_queries queries, max_items input items (bases for kind 1, keys for
+ * kind 0) and max_ids result IDs, and a CUDA graph captured once at creation
+ * (descriptor upload, validation, packing, the persistent query kernel, scan,
+ * gather, status copy).  Every launch replays that graph; the batch size is
+ * read on the device, so no kernel is re-launched from the host and nothing
+ * is allocated.  Plans of one handle may run concurrently on different
+ * streams; none may run while the handle inserts.  Inputs of a plan batch
+ * start at offset 0: offsets[0] = 0 and offsets[n] = n_items. */
+typedef struct rambo_plan rambo_plan_t;
+int rambo_plan_create(rambo_t *h, int kind, uint64_t max_queries, uint64_t max_items, uint64_t max_ids,
+                      uint32_t k, rambo_plan_t **out);
+void rambo_plan_destroy(rambo_plan_t *p);
+/* The plan's input buffers: pinned host (filled by the caller, copied by a
+ * launch with from_host = 1) and device (filled by the caller, from_host = 0). */
+int rambo_plan_buffers(rambo_plan_t *p, void **host_data, uint64_t **host_offsets, void **dev_data,
+                       uint64_t **dev_offsets);
+/* Enqueues one batch of n_queries queries (n_items items) on `stream` and
+ * returns at once.  RAMBO_ESTATE if the previous launch was not waited for,
+ * RAMBO_E2BIG beyond capacity. */
+int rambo_plan_launch(rambo_plan_t *p, uint64_t n_queries, uint64_t n_items, int from_host, void *stream);
+/* 0 when the launched batch has finished, 1 while it runs, < 0 on error. */
+int rambo_plan_poll(rambo_plan_t *p);
+/* Waits for the batch; returns its ID lists (device buffers, or pinned host
+ * copies when to_host = 1, copied on `stream`) in CSR form.  RAMBO_ENOSPC
+ * (with *n_ids = IDs needed) when the results exceed max_ids, and the
+ * validation errors of the query calls. */
+int rambo_plan_wait(rambo_plan_t *p, int to_host, const uint32_t **ids, const uint64_t **id_offsets,
+                    uint64_t *n_ids, void *stream);
+/* Kernels one replay launches (inside the graph). */
+int rambo_plan_launches_per_replay(const rambo_plan_t *p);
+
+/* ---- Continuous-batching server (no counterpart in the paper; uses Sec.
+ * 3.1's streaming updates) ----
+ * A worker thread owns the GPU side: up to `slots` graph-captured plans per
+ * query kind in flight on their own streams.  Whenever a slot frees up it
+ * takes every queued query of its kind that fits its buffers (admission by
+ * device memory), so requests that arrive while others run are batched and
+ * overlap on the device.  Inserts are ordering barriers: queries submitted
+ * before an insert see the index without it, queries after it see it.  While
+ * a server exists, no other call may use its handle. */
+typedef struct rambo_server rambo_server_t;
+typedef struct rambo_server_config {
+    uint32_t slots;              /* plans in flight per query kind (1..16) */
+    uint64_t max_batch_queries;  /* queries per batch */
+    uint64_t max_batch_bases;    /* DNA bases per batch (0 = no sequence queries) */
+    uint64_t max_batch_keys;     /* keys per batch (0 = no key queries) */
+    uint64_t max_batch_ids;      /* result IDs per batch */
+    uint32_t k;                  /* k-mer length of sequence queries and inserts */
+    uint32_t idle_wait_us;       /* worker sleep when idle (0 = 20 us) */
+} rambo_server_config_t;
+typedef struct rambo_server_stats {
+    uint64_t queries, batches, inserts, keys;
+    double seconds;              /* first launch to last completion */
+    uint64_t p50_ns, p99_ns, max_ns;  /* submit-to-result latency of queries */
+} rambo_server_stats_t;
+int rambo_server_create(rambo_t *h, const rambo_server_config_t *cfg, rambo_server_t **out);
+/* Queues one query (kind 0: n_items uint64 keys; kind 1: n_items ASCII
+ * bases); copies the input.  RAMBO_E2BIG if larger than a whole slot. */
+int rambo_server_submit(rambo_server_t *s, int kind, const void *data, uint64_t n_items, uint64_t *ticket);
+/* Queues an insert batch (as rambo_insert_batch / rambo_insert_seq_batch). */
+int rambo_server_submit_insert(rambo_server_t *s, int kind, const uint64_t *set_ids, const void *data,
+                               const uint64_t *offsets, uint64_t n_sets, uint64_t *ticket);
+/* Result of a ticket: RAMBO_OK with the ascending IDs (up to cap; with
+ * RAMBO_ENOSPC and *n_ids set, call again with a larger buffer), 1 if still
+ * pending and wait = 0, or the request's error.  A delivered result is
+ * forgotten. */
+int rambo_server_result(rambo_server_t *s, uint64_t ticket, int wait, uint32_t *ids, uint64_t cap,
+                        uint64_t *n_ids, uint64_t *latency_ns);
+/* Waits until every submitted request has completed. */
+int rambo_server_drain(rambo_server_t *s);
+int rambo_server_stats(rambo_server_t *s, rambo_server_stats_t *out);
+int rambo_server_reset_stats(rambo_server_t *s);
+/* Load generator: submits request i (kind kinds[i], bytes
+ * bytes[byte_offsets[i] .. byte_offsets[i+1])) at arrival_ns[i] after the
+ * call starts, from the calling thread; tickets[i] receives its ticket. */
+int rambo_server_replay(rambo_server_t *s, const uint8_t *kinds, const uint8_t *bytes,
+                        const uint64_t *byte_offsets, const uint64_t *arrival_ns, uint64_t n,
+                        uint64_t *tickets);
+/* Finishes all queued work, stops the worker and frees the server. */
+void rambo_server_destroy(rambo_server_t *s);
+
 /* Copies the bit-sliced index to host memory: n_words must equal
  * R * m * row_stride; word (r*m + p)*row_stride + w holds bits 32w..32w+31 of
  * row (r, p), bit b of the row being bit p of the Bloom filter of cell b of
@@ -230,6 +313,8 @@ int rambo_last_query_stats(const rambo_t *h, rambo_query_stats_t *out);
  *   warps_per_block, blocks_per_sm (0 = as many as fit),
  *   set_stage: 0 = auto, 1 = dense scan of the partition table,
  *              2 = sparse enumeration of the hit cells' members,
+ *              3 = union of the hit cells' member bitmaps (complemented for
+ *                  tables with most cells hit), per table, intersected,
  *   visit_order and l2_fetch_bytes as described in the struct. */
 typedef struct rambo_query_config {
     uint32_t lanes_per_key;

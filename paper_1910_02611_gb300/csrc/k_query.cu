@@ -42,7 +42,7 @@ int query_max_blocks_per_sm(int V, int G, uint32_t eta, int warps_per_block, siz
 
 cudaError_t launch_query(const IndexView& ix, const HashParams& hp, const BatchView& b, const QueryOut& o,
                          const QueryTuning& t, int use_bitmap, DevStatus* st, cudaStream_t s) {
-    if (b.n == 0) return cudaSuccess;
+    if (b.n == 0 && !b.desc) return cudaSuccess;
     const uint32_t spw = query_smem_words_per_warp(ix.R, ix.S, ix.K, use_bitmap);
     const size_t smem = (size_t)spw * 4 * t.warps_per_block;
     const void* f = kernel_ptr(t.V, t.G, ix.eta);

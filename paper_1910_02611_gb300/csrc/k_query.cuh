@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
     const uint32_t* __restrict__ rows = ix.rows;
 
     if (*(volatile unsigned long long*)&st->err != NO_ERR) return;
+    bv_resolve(b);
     if (use_bitmap)
         for (uint32_t w = lane; w < bw; w += 32) sBits[w] = 0;
     __syncwarp();
@@ -208,75 +209,101 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                             for (int v = 0; v < V; ++v) sM[r * ix.S + w0 + v] = M[r][v];
                 }
                 __syncwarp();
-                // table with the fewest hit cells (its cells' members are the candidates)
+                // per-table hit-cell counts; the table with the fewest hit cells
+                // gives the sparse stage its candidates
+                uint32_t pc[RMAX];
                 int rstar = 0;
                 uint32_t pmin = 0xffffffffu;
-                {
-                    uint32_t pc[RMAX];
 #pragma unroll
-                    for (int r = 0; r < RMAX; ++r) {
-                        uint32_t c = 0;
-                        if (r < R && grp == 0 && has_words)
+                for (int r = 0; r < RMAX; ++r) {
+                    uint32_t c = 0;
+                    if (r < R && grp == 0 && has_words)
 #pragma unroll
-                            for (int v = 0; v < V; ++v) c += __popc(M[r][v]);
-                        pc[r] = (r < R) ? __reduce_add_sync(FULL, c) : 0xffffffffu;
+                        for (int v = 0; v < V; ++v) c += __popc(M[r][v]);
+                    pc[r] = (r < R) ? __reduce_add_sync(FULL, c) : 0u;
+                    if (r < R && pc[r] < pmin) {
+                        pmin = pc[r];
+                        rstar = r;
                     }
-#pragma unroll
-                    for (int r = 0; r < RMAX; ++r)
-                        if (pc[r] < pmin) {
-                            pmin = pc[r];
-                            rstar = r;
-                        }
                 }
-                bool sparse = use_bitmap && (set_stage == 2 ||
-                                             (set_stage == 0 && (uint64_t)pmin * (ix.K / ix.B + 1) * (uint64_t)R +
-                                                                        2ull * ix.K <
-                                                                    ix.K * (uint64_t)R));
-                if (!sparse) {
-                    // dense: every ID in order; ballot keeps the order
-                    for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
-                        const uint64_t i = i0 + lane;
-                        const bool ok = (i < ix.K) && qk_set_passes(ix, sM, i, -1);
-                        const unsigned bal = __ballot_sync(FULL, ok);
-                        if (bal) {
-                            const unsigned pre = __popc(bal & ((1u << lane) - 1u));
-                            if (ok && count + pre < (uint32_t)QK_ID_CAP) sIds[count + pre] = (uint32_t)i;
-                            count += __popc(bal);
+                // A5 strategy (all give the same set): 1 dense scan of every ID,
+                // 2 sparse enumeration of rstar's hit cells, 3 union of the
+                // precomputed member bitmaps of the hit cells (or of the missed
+                // cells, complemented, when a table is mostly hit).  Auto picks
+                // the fewest warp-wide operations (Lemma 4.4's candidate term).
+                int stage = set_stage;
+                if (!use_bitmap) stage = 1;
+                if (stage == 3 && !ix.mem_bits) stage = 1;
+                if (stage == 0) {
+                    const uint64_t kw = (ix.K + 31) / 32;
+                    const uint64_t dense = kw * (uint64_t)(R + 2);
+                    const uint64_t sparse = ((uint64_t)pmin * (ix.K / ix.B + 1) / 32 + pmin) * (uint64_t)(R + 3) + kw / 16;
+                    uint64_t uni = ~0ull;
+                    if (ix.mem_bits) {
+                        uni = kw / 32 + 1;
+#pragma unroll
+                        for (int r = 0; r < RMAX; ++r) {
+                            if (r >= R) continue;
+                            const uint32_t cr = pc[r] < ix.B - pc[r] ? pc[r] : ix.B - pc[r];
+                            uni += (uint64_t)cr * (kw / 32 + 1);
                         }
                     }
-                    if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
-                    start = __shfl_sync(FULL, start, 0);
-                    if (count && start + count <= o.stage_cap) {
-                        if (count <= (uint32_t)QK_ID_CAP) {
-                            for (uint32_t t = lane; t < count; t += 32) o.stage[start + t] = sIds[t];
-                        } else {
-                            uint32_t at = 0;
-                            for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
-                                const uint64_t i = i0 + lane;
-                                const bool ok = (i < ix.K) && qk_set_passes(ix, sM, i, -1);
-                                const unsigned bal = __ballot_sync(FULL, ok);
-                                if (ok) o.stage[start + at + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
-                                at += __popc(bal);
+                    stage = (dense <= sparse && dense <= uni) ? 1 : (sparse <= uni ? 2 : 3);
+                }
+                if (use_bitmap) {
+                    if (stage == 1) {
+                        // dense: one ballot per 32 IDs becomes one bitmap word
+                        for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
+                            const uint64_t i = i0 + lane;
+                            const bool ok = (i < ix.K) && qk_set_passes(ix, sM, i, -1);
+                            const unsigned bal = __ballot_sync(FULL, ok);
+                            if (lane == 0) sBits[i0 >> 5] = bal;
+                        }
+                    } else if (stage == 2) {
+                        // sparse: members of the hit cells of table rstar, tested on the other tables
+                        const uint32_t* cellmask = sM + rstar * ix.S;
+                        for (uint32_t w = 0; w < ix.W; ++w) {
+                            uint32_t bits = cellmask[w];
+                            while (bits) {
+                                const uint32_t cb = w * 32 + (__ffs(bits) - 1);
+                                bits &= bits - 1;
+                                const uint64_t cell = (uint64_t)rstar * ix.B + cb;
+                                const uint64_t m0 = __ldg(ix.mem_off + cell), m1 = __ldg(ix.mem_off + cell + 1);
+                                for (uint64_t u = m0 + lane; u < m1; u += 32) {
+                                    const uint32_t i = __ldg(ix.mem_ids + u);
+                                    if (qk_set_passes(ix, sM, i, rstar)) atomicOr(sBits + (i >> 5), 1u << (i & 31));
+                                }
                             }
                         }
-                    }
-                } else {
-                    // sparse: members of the hit cells of table rstar, tested on the other tables
-                    const uint32_t* cellmask = sM + rstar * ix.S;
-                    for (uint32_t w = 0; w < ix.W; ++w) {
-                        uint32_t bits = cellmask[w];
-                        while (bits) {
-                            const uint32_t cb = w * 32 + (__ffs(bits) - 1);
-                            bits &= bits - 1;
-                            const uint64_t cell = (uint64_t)rstar * ix.B + cb;
-                            const uint64_t m0 = __ldg(ix.mem_off + cell), m1 = __ldg(ix.mem_off + cell + 1);
-                            for (uint64_t u = m0 + lane; u < m1; u += 32) {
-                                const uint32_t i = __ldg(ix.mem_ids + u);
-                                if (qk_set_passes(ix, sM, i, rstar)) atomicOr(sBits + (i >> 5), 1u << (i & 31));
+                    } else {
+                        // union of member bitmaps: G_r = OR of the hit cells' bitmaps
+                        // (or NOT of the missed cells' when over half are hit); the
+                        // answer is registered AND every G_r
+                        for (uint32_t w = lane; w < bw; w += 32) {
+                            uint32_t g = __ldg(ix.reg + w);
+#pragma unroll
+                            for (int r = 0; r < RMAX; ++r) {
+                                if (r >= R || !g) continue;
+                                const bool comp = pc[r] * 2 > ix.B;
+                                const uint32_t* cm = sM + r * ix.S;
+                                const uint32_t* mb = ix.mem_bits + (uint64_t)r * ix.B * bw + w;
+                                uint32_t acc = 0;
+                                for (uint32_t cw = 0; cw < ix.W; ++cw) {
+                                    uint32_t bits = comp ? ~cm[cw] : cm[cw];
+                                    if (cw == ix.W - 1 && (ix.B & 31)) bits &= (1u << (ix.B & 31)) - 1u;
+                                    while (bits) {
+                                        const uint32_t cb = cw * 32 + (__ffs(bits) - 1);
+                                        bits &= bits - 1;
+                                        acc |= __ldg(mb + (uint64_t)cb * bw);
+                                    }
+                                }
+                                g &= comp ? ~acc : acc;
                             }
+                            sBits[w] = g;
                         }
                     }
                     __syncwarp();
+                    // compaction: ascending IDs from the bitmap, bitmap cleared
                     for (uint32_t w = lane; w < bw; w += 32) count += __popc(sBits[w]);
                     count = __reduce_add_sync(FULL, count);
                     if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
@@ -305,6 +332,35 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                         at += __shfl_sync(FULL, incl, 31);
                     }
                     __syncwarp();
+                } else {
+                    // ID space too large for a shared-memory bitmap: dense scan,
+                    // survivors staged in shared memory, recounted if they overflow
+                    for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
+                        const uint64_t i = i0 + lane;
+                        const bool ok = (i < ix.K) && qk_set_passes(ix, sM, i, -1);
+                        const unsigned bal = __ballot_sync(FULL, ok);
+                        if (bal) {
+                            const unsigned pre = __popc(bal & ((1u << lane) - 1u));
+                            if (ok && count + pre < (uint32_t)QK_ID_CAP) sIds[count + pre] = (uint32_t)i;
+                            count += __popc(bal);
+                        }
+                    }
+                    if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
+                    start = __shfl_sync(FULL, start, 0);
+                    if (count && start + count <= o.stage_cap) {
+                        if (count <= (uint32_t)QK_ID_CAP) {
+                            for (uint32_t t = lane; t < count; t += 32) o.stage[start + t] = sIds[t];
+                        } else {
+                            uint32_t at = 0;
+                            for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
+                                const uint64_t i = i0 + lane;
+                                const bool ok = (i < ix.K) && qk_set_passes(ix, sM, i, -1);
+                                const unsigned bal = __ballot_sync(FULL, ok);
+                                if (ok) o.stage[start + at + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
+                                at += __popc(bal);
+                            }
+                        }
+                    }
                 }
             }
             if (lane == 0) {

@@ -69,6 +69,10 @@ cudaError_t launch_phi_init(uint16_t* phi, uint64_t K, uint32_t R, uint32_t B, c
 
 __global__ void k_validate(BatchView b, uint64_t min_len, unsigned short_prio, uint64_t K,
                            DevStatus* st) {
+    bv_resolve(b);
+    // a descriptor-driven batch must start at 0 and end exactly at the staged data's end
+    if (b.desc && blockIdx.x == 0 && threadIdx.x == 0 && (b.offsets[0] != 0 || b.offsets[b.n] != b.total))
+        record_error(st, 0, PRIO_EINVAL);
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < b.n;
          t += (uint64_t)gridDim.x * blockDim.x) {
         if (b.set_ids && b.set_ids[t] >= K) {
@@ -86,7 +90,7 @@ __global__ void k_validate(BatchView b, uint64_t min_len, unsigned short_prio, u
 
 cudaError_t launch_validate_batch(const BatchView& b, uint64_t min_len, uint64_t K, DevStatus* st,
                                   cudaStream_t s) {
-    if (b.n == 0) return cudaSuccess;
+    if (b.n == 0 && !b.desc) return cudaSuccess;
     // a sequence query shorter than k is a bad sequence; an empty key query is invalid
     unsigned prio = b.seq ? PRIO_EBADSEQ : PRIO_EINVAL;
     k_validate<<<grid_for(b.n, 256, 8192), 256, 0, s>>>(b, min_len, prio, K, st);
@@ -121,7 +125,11 @@ __device__ __forceinline__ uint32_t codes4(uint32_t w, int* bad) {
 }
 
 __global__ void k_pack(const uint8_t* __restrict__ bases, uint64_t total, uint64_t* __restrict__ packed,
-                       uint64_t n_words, DevStatus* st) {
+                       uint64_t n_words, DevStatus* st, const uint64_t* __restrict__ desc) {
+    if (desc) {
+        total = desc[1];
+        n_words = total / 32 + 2;
+    }
     const bool aligned = (reinterpret_cast<uintptr_t>(bases) & 15) == 0;
     for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < n_words;
          w += (uint64_t)gridDim.x * blockDim.x) {
@@ -160,14 +168,16 @@ __global__ void k_pack(const uint8_t* __restrict__ bases, uint64_t total, uint64
 }
 
 cudaError_t launch_pack(const uint8_t* bases, uint64_t total, uint64_t* packed, uint64_t n_words,
-                        DevStatus* st, cudaStream_t s) {
+                        DevStatus* st, cudaStream_t s, const uint64_t* desc) {
     if (n_words == 0) return cudaSuccess;
-    k_pack<<<grid_for(n_words, 256, 1 << 16), 256, 0, s>>>(bases, total, packed, n_words, st);
+    // with a descriptor, n_words is the capacity the grid is sized for
+    k_pack<<<grid_for(n_words, 256, 1 << 16), 256, 0, s>>>(bases, total, packed, n_words, st, desc);
     return cudaGetLastError();
 }
 
 // The item holding the lowest bad byte gets an EBADSEQ error.
 __global__ void k_resolve_bad_base(BatchView b, DevStatus* st) {
+    bv_resolve(b);
     unsigned long long p = st->bad_pos;
     if (p == NO_ERR || b.n == 0) return;
     uint64_t abs_p = p + b.off0;
@@ -242,9 +252,10 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* w
 }
 
 __global__ void k_scan_tiles(const uint32_t* __restrict__ counts, uint64_t n, uint64_t* __restrict__ out,
-                             uint64_t* __restrict__ tile_sums) {
+                             uint64_t* __restrict__ tile_sums, const uint64_t* __restrict__ n_dev) {
     __shared__ uint64_t warp_tot[32];
     __shared__ uint64_t tot;
+    if (n_dev) n = *n_dev;
     uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
     uint64_t v[SCAN_ITEMS];
     uint64_t sum = 0;
@@ -262,9 +273,14 @@ __global__ void k_scan_tiles(const uint32_t* __restrict__ counts, uint64_t n, ui
     if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_sums(uint64_t* tile_sums, uint64_t n_tiles) {
+__global__ void k_scan_sums(uint64_t* tile_sums, uint64_t n_tiles, const uint64_t* __restrict__ n_dev) {
     __shared__ uint64_t warp_tot[32];
     __shared__ uint64_t tot;
+    if (n_dev) {
+        const uint64_t n = *n_dev;
+        n_tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+        if (n_tiles == 0) n_tiles = 1;
+    }
     uint64_t carry = 0;
     for (uint64_t b0 = 0; b0 < n_tiles; b0 += blockDim.x) {
         uint64_t i = b0 + threadIdx.x;
@@ -278,7 +294,13 @@ __global__ void k_scan_sums(uint64_t* tile_sums, uint64_t n_tiles) {
 }
 
 __global__ void k_scan_add(uint64_t* __restrict__ out, uint64_t n, const uint64_t* __restrict__ tile_sums,
-                           uint64_t n_tiles) {
+                           uint64_t n_tiles, const uint64_t* __restrict__ n_dev) {
+    if (n_dev) {
+        n = *n_dev;
+        n_tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+        if (n_tiles == 0) n_tiles = 1;
+    }
+    if ((uint64_t)blockIdx.x >= n_tiles) return;
     uint64_t add = tile_sums[blockIdx.x];
     uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
     for (int t = threadIdx.x; t < SCAN_TILE; t += blockDim.x)
@@ -287,13 +309,14 @@ __global__ void k_scan_add(uint64_t* __restrict__ out, uint64_t n, const uint64_
 }
 
 cudaError_t launch_scan_counts(const uint32_t* counts, uint64_t n, uint64_t* offsets, uint64_t* tmp,
-                               uint64_t tmp_words, cudaStream_t s) {
+                               uint64_t tmp_words, cudaStream_t s, const uint64_t* n_dev) {
+    // with n_dev, n is the capacity the grids are sized for and the true count is read on the device
     uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles == 0) tiles = 1;
     if (tmp_words < tiles + 1) return cudaErrorInvalidValue;
-    k_scan_tiles<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(counts, n, offsets, tmp);
-    k_scan_sums<<<1, SCAN_THREADS, 0, s>>>(tmp, tiles);
-    k_scan_add<<<(unsigned)tiles, 256, 0, s>>>(offsets, n, tmp, tiles);
+    k_scan_tiles<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(counts, n, offsets, tmp, n_dev);
+    k_scan_sums<<<1, SCAN_THREADS, 0, s>>>(tmp, tiles, n_dev);
+    k_scan_add<<<(unsigned)tiles, 256, 0, s>>>(offsets, n, tmp, tiles, n_dev);
     return cudaGetLastError();
 }
 
@@ -359,8 +382,11 @@ cudaError_t launch_cluster_order(const BatchView& b, uint64_t* keys, uint32_t* h
 // gather staged result IDs into CSR order: one warp per query
 
 __global__ void k_gather(QueryOut o, const uint64_t* __restrict__ id_offsets, uint64_t n,
-                         uint32_t* __restrict__ ids, const DevStatus* st) {
+                         uint32_t* __restrict__ ids, const DevStatus* st, const uint64_t* __restrict__ n_dev,
+                         uint64_t ids_cap) {
     if (st->err != NO_ERR || st->cursor > o.stage_cap) return;
+    if (n_dev) n = *n_dev;
+    if (id_offsets[n] > ids_cap) return;  // the caller sees the total and reports the shortfall
     const int lane = threadIdx.x & 31;
     uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -374,10 +400,10 @@ __global__ void k_gather(QueryOut o, const uint64_t* __restrict__ id_offsets, ui
 }
 
 cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_t n, uint32_t* ids,
-                          const DevStatus* st, cudaStream_t s) {
+                          const DevStatus* st, cudaStream_t s, const uint64_t* n_dev, uint64_t ids_cap) {
     if (n == 0) return cudaSuccess;
     int blocks = grid_for(n * 32, 256, 152 * 16);
-    k_gather<<<blocks, 256, 0, s>>>(o, id_offsets, n, ids, st);
+    k_gather<<<blocks, 256, 0, s>>>(o, id_offsets, n, ids, st, n_dev, ids_cap);
     return cudaGetLastError();
 }
 
@@ -434,6 +460,25 @@ __global__ void k_member_place(const uint16_t* __restrict__ phi, uint64_t K, uin
             uint32_t at = atomicAdd(fill + cell, 1u);
             ids[off[cell] + at] = (uint32_t)i;
         }
+}
+
+__global__ void k_member_bits(const uint16_t* __restrict__ phi, uint64_t K, uint32_t R, uint32_t B,
+                              uint32_t* __restrict__ bits) {
+    const uint64_t bw = (K + 31) / 32;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < K;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        for (uint32_t r = 0; r < R; ++r) {
+            const uint64_t cell = (uint64_t)r * B + phi[i * PHI_STRIDE + r];
+            atomicOr(bits + cell * bw + (i >> 5), 1u << (i & 31));
+        }
+}
+
+cudaError_t launch_member_bits(const IndexView& ix, uint32_t* mem_bits, cudaStream_t s) {
+    const uint64_t words = (uint64_t)ix.R * ix.B * ((ix.K + 31) / 32);
+    cudaError_t e = cudaMemsetAsync(mem_bits, 0, words * 4, s);
+    if (e != cudaSuccess) return e;
+    k_member_bits<<<grid_for(ix.K, 256, 4096), 256, 0, s>>>(ix.phi, ix.K, ix.R, ix.B, mem_bits);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_members(const IndexView& ix, uint64_t* mem_off, uint32_t* mem_ids, uint32_t* fill,

@@ -114,6 +114,7 @@ struct rambo {
     uint32_t* reg = nullptr;
     uint64_t* mem_off = nullptr;
     uint32_t* mem_ids = nullptr;
+    uint32_t* mem_bits = nullptr;
     DevStatus* st = nullptr;
     DevStatus* h_st = nullptr;  // pinned
     uint64_t* h_small = nullptr;  // pinned, 8 words
@@ -147,6 +148,7 @@ struct rambo {
         v.reg = reg;
         v.mem_off = mem_off;
         v.mem_ids = mem_ids;
+        v.mem_bits = mem_bits;
         return v;
     }
     uint64_t index_words() const { return (uint64_t)R * m * S; }
@@ -164,6 +166,7 @@ void free_handle(rambo* h) {
     if (h->reg) cudaFree(h->reg);
     if (h->mem_off) cudaFree(h->mem_off);
     if (h->mem_ids) cudaFree(h->mem_ids);
+    if (h->mem_bits) cudaFree(h->mem_bits);
     if (h->st) cudaFree(h->st);
     if (h->h_st) cudaFreeHost(h->h_st);
     if (h->h_small) cudaFreeHost(h->h_small);
@@ -576,6 +579,12 @@ int rambo_create(uint64_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
         if (rc) return fail(rc);
         if (launch_members(h->view(), h->mem_off, h->mem_ids, h->fill.p, s) != cudaSuccess)
             return fail(RAMBO_ECUDA);
+        // member bitmaps of every cell for the union set stage (bounded size)
+        const uint64_t mb_bytes = cells * ((K + 31) / 32) * 4;
+        if ((K + 31) / 32 <= 4096 && mb_bytes <= (256ull << 20)) {
+            if (cudaMalloc(&h->mem_bits, mb_bytes) != cudaSuccess) return fail(RAMBO_ENOMEM);
+            if (launch_member_bits(h->view(), h->mem_bits, s) != cudaSuccess) return fail(RAMBO_ECUDA);
+        }
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(RAMBO_ECUDA);
     default_config(h);
@@ -701,8 +710,9 @@ int rambo_set_query_config(rambo_t* h, const rambo_query_config_t* cfg) {
     if (!h || !cfg) return RAMBO_EINVAL;
     if (!query_config_supported((int)cfg->words_per_lane, (int)cfg->lanes_per_key, h->S)) return RAMBO_EINVAL;
     if (cfg->warps_per_block < 1 || cfg->warps_per_block > 8) return RAMBO_EINVAL;
-    if (cfg->set_stage > 2) return RAMBO_EINVAL;
+    if (cfg->set_stage > 3) return RAMBO_EINVAL;
     if (cfg->set_stage == 2 && !h->mem_off) return RAMBO_EINVAL;
+    if (cfg->set_stage == 3 && !h->mem_bits) return RAMBO_EINVAL;
     if (cfg->visit_order > 2 || cfg->cluster > 1 || cfg->row_load > 5) return RAMBO_EINVAL;
     if (cfg->l2_fetch_bytes && cfg->l2_fetch_bytes != 32 && cfg->l2_fetch_bytes != 64 && cfg->l2_fetch_bytes != 128)
         return RAMBO_EINVAL;

@@ -152,6 +152,7 @@ struct IndexView {
     uint32_t* reg;         // ceil(K/32) words
     const uint64_t* mem_off;  // [R*B + 1] offsets of each cell's members (sparse stage)
     const uint32_t* mem_ids;  // members of each cell (unordered)
+    const uint32_t* mem_bits; // [R][B][ceil(K/32)] member bitmap of every cell (union set stage)
 };
 
 struct BatchView {
@@ -165,7 +166,19 @@ struct BatchView {
     uint32_t k;
     const uint64_t* set_ids;       // insert batches only
     const uint32_t* perm;          // queries only: processing order (NULL = 0..n-1)
+    const uint64_t* desc;          // device descriptor {n, total} (offsets[0] = 0) read at
+                                   // kernel start instead of n/total/off0; lets one captured
+                                   // CUDA graph serve batches of any size up to its capacity
 };
+
+// Takes n, total and off0 from the device descriptor when there is one.
+__device__ __forceinline__ void bv_resolve(BatchView& b) {
+    if (b.desc) {
+        b.n = b.desc[0];
+        b.total = b.desc[1];
+        b.off0 = 0;
+    }
+}
 
 struct QueryOut {
     uint32_t* stage;       // staged IDs (arena)
@@ -195,17 +208,19 @@ cudaError_t launch_phi_init(uint16_t* phi, uint64_t K, uint32_t R, uint32_t B, c
 cudaError_t launch_validate_batch(const BatchView& b, uint64_t min_len, uint64_t K, DevStatus* st,
                                   cudaStream_t s);
 cudaError_t launch_pack(const uint8_t* bases, uint64_t total, uint64_t* packed, uint64_t n_words,
-                        DevStatus* st, cudaStream_t s);
+                        DevStatus* st, cudaStream_t s, const uint64_t* desc = nullptr);
 cudaError_t launch_resolve_bad_base(const BatchView& b, DevStatus* st, cudaStream_t s);
 cudaError_t launch_register(const BatchView& b, uint32_t* reg, DevStatus* st, cudaStream_t s);
 cudaError_t launch_scan_counts(const uint32_t* counts, uint64_t n, uint64_t* offsets,
-                               uint64_t* tmp, uint64_t tmp_words, cudaStream_t s);
+                               uint64_t* tmp, uint64_t tmp_words, cudaStream_t s, const uint64_t* n_dev = nullptr);
 uint64_t scan_tmp_words(uint64_t n);
 cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_t n, uint32_t* ids,
-                          const DevStatus* st, cudaStream_t s);
+                          const DevStatus* st, cudaStream_t s, const uint64_t* n_dev = nullptr,
+                          uint64_t ids_cap = ~0ull);
 cudaError_t launch_cell_popcount(const IndexView& ix, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_members(const IndexView& ix, uint64_t* mem_off, uint32_t* mem_ids,
                            uint32_t* fill, cudaStream_t s);
+cudaError_t launch_member_bits(const IndexView& ix, uint32_t* mem_bits, cudaStream_t s);
 
 cudaError_t launch_cluster_order(const BatchView& b, uint64_t* keys, uint32_t* hist, uint64_t* bucket_off,
                                  uint64_t* scan_tmp, uint64_t scan_tmp_words, uint32_t* perm, const DevStatus* st,

@@ -1,0 +1,295 @@
+// rambo_plan.cu -- graph-captured query plans.
+//
+// A plan owns device buffers sized for a maximum batch (queries, bases or
+// keys, result IDs) and a CUDA graph captured once at creation: descriptor
+// upload, status reset, validation, 2-bit packing, the persistent query
+// kernel, the count scan, the gather, and the copy of the status word back to
+// pinned host memory.  Kernels read the batch size from the uploaded
+// descriptor, so one captured graph replays for any batch up to capacity.
+// A launch is asynchronous; the host learns the result size from the status
+// copy and then copies exactly the IDs it needs.  Each plan has its own
+// status block and buffers, so several plans run concurrently on different
+// streams against the same (read-only) index.
+#include <cstring>
+#include <new>
+
+#include "k_query.cuh"
+#include "rambo_impl.cuh"
+
+using namespace rgb;
+
+namespace {
+
+int map_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return RAMBO_OK;
+    return e == cudaErrorMemoryAllocation ? RAMBO_ENOMEM : RAMBO_ECUDA;
+}
+
+#define PK(x)                                      \
+    do {                                           \
+        cudaError_t e_ = (x);                      \
+        if (e_ != cudaSuccess) return map_cuda(e_); \
+    } while (0)
+
+// total number of staged result IDs, read where the descriptor says the batch ends
+__global__ void k_store_total(const uint64_t* __restrict__ id_off, const uint64_t* __restrict__ desc,
+                              DevStatus* st) {
+    st->spare[1] = id_off[desc[0]];
+}
+
+}  // namespace
+
+struct rambo_plan {
+    rambo_t* h = nullptr;
+    int kind = 1;
+    uint32_t k = 31;
+    uint64_t max_q = 0, max_items = 0, max_ids = 0;
+    int device = 0;
+    size_t elem = 1;
+    // device
+    uint8_t* d_data = nullptr;
+    uint64_t* d_off = nullptr;
+    uint64_t* d_packed = nullptr;
+    uint32_t* qcount = nullptr;
+    uint64_t* qstart = nullptr;
+    uint64_t* scan_tmp = nullptr;
+    uint32_t* stage = nullptr;
+    uint32_t* ids = nullptr;
+    uint64_t* id_off = nullptr;
+    DevStatus* st = nullptr;
+    uint64_t* d_desc = nullptr;
+    // pinned host
+    uint8_t* h_data = nullptr;
+    uint64_t* h_off = nullptr;
+    uint64_t* h_desc = nullptr;
+    DevStatus* h_st = nullptr;
+    uint32_t* h_ids = nullptr;
+    uint64_t* h_id_off = nullptr;
+    // graph
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev_done = nullptr;
+    uint64_t launched_n = 0;
+    bool busy = false;
+    int launches_per_replay = 0;
+};
+
+namespace {
+
+void plan_free(rambo_plan* p) {
+    if (!p) return;
+    cudaSetDevice(p->device);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->ev_done) cudaEventDestroy(p->ev_done);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    void* dev[] = {p->d_data, p->d_off, p->d_packed, p->qcount, p->qstart, p->scan_tmp,
+                   p->stage, p->ids, p->id_off, p->st, p->d_desc};
+    for (void* d : dev)
+        if (d) cudaFree(d);
+    void* host[] = {p->h_data, p->h_off, p->h_desc, p->h_st, p->h_ids, p->h_id_off};
+    for (void* x : host)
+        if (x) cudaFreeHost(x);
+    delete p;
+}
+
+int plan_capture(rambo_plan* p) {
+    IndexView ix;
+    HashParams hp;
+    QueryTuning t;
+    int use_bitmap = 0, dev = 0;
+    int rc = handle_query_view(p->h, p->max_q, &ix, &hp, &t, &use_bitmap, &dev);
+    if (rc) return rc;
+    BatchView b{};
+    b.seq = p->kind;
+    b.offsets = p->d_off;
+    b.keys = p->kind == 0 ? reinterpret_cast<const uint64_t*>(p->d_data) : nullptr;
+    b.packed = p->kind == 1 ? p->d_packed : nullptr;
+    b.n = p->max_q;
+    b.total = p->max_items;
+    b.off0 = 0;
+    b.k = p->k;
+    b.desc = p->d_desc;
+    const uint64_t scan_words = scan_tmp_words(p->max_q);
+    cudaStream_t s = p->cap;
+    PK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemcpyAsync(p->d_desc, p->h_desc, 2 * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+    int n_launch = 0;
+    if (e == cudaSuccess) e = launch_status_reset(p->st, s), ++n_launch;
+    if (e == cudaSuccess) e = launch_validate_batch(b, p->kind ? p->k : 1, ix.K, p->st, s), ++n_launch;
+    if (e == cudaSuccess && p->kind == 1) {
+        e = launch_pack(p->d_data, p->max_items, p->d_packed, p->max_items / 32 + 2, p->st, s, p->d_desc);
+        if (e == cudaSuccess) e = launch_resolve_bad_base(b, p->st, s);
+        n_launch += 2;
+    }
+    QueryOut o{p->stage, p->max_ids, p->qstart, p->qcount};
+    if (e == cudaSuccess) e = launch_query(ix, hp, b, o, t, use_bitmap, p->st, s), ++n_launch;
+    if (e == cudaSuccess) e = launch_scan_counts(p->qcount, p->max_q, p->id_off, p->scan_tmp, scan_words, s, p->d_desc);
+    n_launch += 3;
+    if (e == cudaSuccess) e = launch_gather(o, p->id_off, p->max_q, p->ids, p->st, s, p->d_desc, p->max_ids);
+    ++n_launch;
+    if (e == cudaSuccess) {
+        k_store_total<<<1, 1, 0, s>>>(p->id_off, p->d_desc, p->st);
+        e = cudaGetLastError();
+        ++n_launch;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->h_st, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return map_cuda(e != cudaSuccess ? e : e2);
+    }
+    p->graph = g;
+    PK(cudaGraphInstantiate(&p->exec, g, 0));
+    p->launches_per_replay = n_launch;
+    return RAMBO_OK;
+}
+
+int decode(unsigned long long e) {
+    if (e == NO_ERR) return RAMBO_OK;
+    switch ((unsigned)(e & 0xff)) {
+        case PRIO_ERANGE: return RAMBO_ERANGE;
+        case PRIO_EINVAL: return RAMBO_EINVAL;
+        case PRIO_EBADSEQ: return RAMBO_EBADSEQ;
+        default: return RAMBO_ECUDA;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int rambo_plan_create(rambo_t* h, int kind, uint64_t max_queries, uint64_t max_items, uint64_t max_ids, uint32_t k,
+                      rambo_plan_t** out) {
+    if (!h || !out || (kind != 0 && kind != 1) || !max_queries || !max_items || !max_ids) return RAMBO_EINVAL;
+    if (kind == 1 && (k < 1 || k > 32)) return RAMBO_EINVAL;
+    if (max_queries > 0xffffffffull) return RAMBO_EINVAL;
+    *out = nullptr;
+    rambo_plan* p = new (std::nothrow) rambo_plan();
+    if (!p) return RAMBO_ENOMEM;
+    IndexView ix;
+    HashParams hp;
+    QueryTuning t;
+    int ub = 0;
+    int rc = handle_query_view(h, max_queries, &ix, &hp, &t, &ub, &p->device);
+    if (rc) {
+        delete p;
+        return rc;
+    }
+    p->h = h;
+    p->kind = kind;
+    p->k = kind == 1 ? k : 0;
+    p->max_q = max_queries;
+    p->max_items = max_items;
+    p->max_ids = max_ids;
+    p->elem = kind == 0 ? 8 : 1;
+    auto fail = [&](int code) {
+        plan_free(p);
+        return code;
+    };
+    if (cudaSetDevice(p->device) != cudaSuccess) return fail(RAMBO_ECUDA);
+    bool ok = cudaMalloc(&p->d_data, max_items * p->elem + 16) == cudaSuccess &&
+              cudaMalloc(&p->d_off, (max_queries + 1) * 8) == cudaSuccess &&
+              (kind == 0 || cudaMalloc(&p->d_packed, (max_items / 32 + 2) * 8) == cudaSuccess) &&
+              cudaMalloc(&p->qcount, max_queries * 4) == cudaSuccess &&
+              cudaMalloc(&p->qstart, max_queries * 8) == cudaSuccess &&
+              cudaMalloc(&p->scan_tmp, scan_tmp_words(max_queries) * 8) == cudaSuccess &&
+              cudaMalloc(&p->stage, max_ids * 4) == cudaSuccess && cudaMalloc(&p->ids, max_ids * 4) == cudaSuccess &&
+              cudaMalloc(&p->id_off, (max_queries + 1) * 8) == cudaSuccess &&
+              cudaMalloc(&p->st, sizeof(DevStatus)) == cudaSuccess && cudaMalloc(&p->d_desc, 16) == cudaSuccess &&
+              cudaMallocHost(&p->h_data, max_items * p->elem + 16) == cudaSuccess &&
+              cudaMallocHost(&p->h_off, (max_queries + 1) * 8) == cudaSuccess &&
+              cudaMallocHost(&p->h_desc, 16) == cudaSuccess && cudaMallocHost(&p->h_st, sizeof(DevStatus)) == cudaSuccess &&
+              cudaMallocHost(&p->h_ids, max_ids * 4) == cudaSuccess &&
+              cudaMallocHost(&p->h_id_off, (max_queries + 1) * 8) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return fail(RAMBO_ENOMEM);
+    }
+    if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming) != cudaSuccess)
+        return fail(RAMBO_ECUDA);
+    p->h_desc[0] = 0;
+    p->h_desc[1] = 0;
+    rc = plan_capture(p);
+    if (rc) return fail(rc);
+    *out = p;
+    return RAMBO_OK;
+}
+
+void rambo_plan_destroy(rambo_plan_t* p) {
+    if (p && p->busy) cudaEventSynchronize(p->ev_done);
+    plan_free(p);
+}
+
+int rambo_plan_buffers(rambo_plan_t* p, void** host_data, uint64_t** host_offsets, void** dev_data,
+                       uint64_t** dev_offsets) {
+    if (!p) return RAMBO_EINVAL;
+    if (host_data) *host_data = p->h_data;
+    if (host_offsets) *host_offsets = p->h_off;
+    if (dev_data) *dev_data = p->d_data;
+    if (dev_offsets) *dev_offsets = p->d_off;
+    return RAMBO_OK;
+}
+
+int rambo_plan_launch(rambo_plan_t* p, uint64_t n_queries, uint64_t n_items, int from_host, void* stream) {
+    if (!p || n_queries == 0) return RAMBO_EINVAL;
+    if (p->busy) return RAMBO_ESTATE;
+    if (n_queries > p->max_q || n_items > p->max_items) return RAMBO_E2BIG;
+    cudaStream_t s = (cudaStream_t)stream;
+    PK(cudaSetDevice(p->device));
+    p->h_desc[0] = n_queries;
+    p->h_desc[1] = n_items;
+    if (from_host) {
+        PK(cudaMemcpyAsync(p->d_off, p->h_off, (n_queries + 1) * 8, cudaMemcpyHostToDevice, s));
+        if (n_items) PK(cudaMemcpyAsync(p->d_data, p->h_data, n_items * p->elem, cudaMemcpyHostToDevice, s));
+    }
+    PK(cudaGraphLaunch(p->exec, s));
+    PK(cudaEventRecord(p->ev_done, s));
+    p->launched_n = n_queries;
+    p->busy = true;
+    return RAMBO_OK;
+}
+
+int rambo_plan_poll(rambo_plan_t* p) {
+    if (!p) return RAMBO_EINVAL;
+    if (!p->busy) return RAMBO_ESTATE;
+    cudaError_t e = cudaEventQuery(p->ev_done);
+    if (e == cudaErrorNotReady) return 1;
+    return map_cuda(e);
+}
+
+int rambo_plan_wait(rambo_plan_t* p, int to_host, const uint32_t** ids, const uint64_t** id_offsets, uint64_t* n_ids,
+                    void* stream) {
+    if (!p) return RAMBO_EINVAL;
+    if (!p->busy) return RAMBO_ESTATE;
+    PK(cudaSetDevice(p->device));
+    PK(cudaEventSynchronize(p->ev_done));
+    p->busy = false;
+    const DevStatus st = *p->h_st;
+    int rc = decode(st.err);
+    if (rc) return rc;
+    const uint64_t total = st.spare[1];
+    if (n_ids) *n_ids = total;
+    if (st.cursor > p->max_ids || total > p->max_ids) return RAMBO_ENOSPC;
+    const uint64_t n = p->launched_n;
+    if (to_host) {
+        cudaStream_t s = (cudaStream_t)stream;
+        PK(cudaMemcpyAsync(p->h_id_off, p->id_off, (n + 1) * 8, cudaMemcpyDeviceToHost, s));
+        if (total) PK(cudaMemcpyAsync(p->h_ids, p->ids, total * 4, cudaMemcpyDeviceToHost, s));
+        PK(cudaStreamSynchronize(s));
+        if (ids) *ids = p->h_ids;
+        if (id_offsets) *id_offsets = p->h_id_off;
+    } else {
+        if (ids) *ids = p->ids;
+        if (id_offsets) *id_offsets = p->id_off;
+    }
+    return RAMBO_OK;
+}
+
+int rambo_plan_launches_per_replay(const rambo_plan_t* p) { return p ? p->launches_per_replay : 0; }
+
+}  // extern "C"

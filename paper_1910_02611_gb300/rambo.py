@@ -30,6 +30,16 @@ class QueryStats(C.Structure):
                 ("device_ms", C.c_float)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("slots", _u32), ("max_batch_queries", _u64), ("max_batch_bases", _u64), ("max_batch_keys", _u64),
+                ("max_batch_ids", _u64), ("k", _u32), ("idle_wait_us", _u32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("queries", _u64), ("batches", _u64), ("inserts", _u64), ("keys", _u64), ("seconds", C.c_double),
+                ("p50_ns", _u64), ("p99_ns", _u64), ("max_ns", _u64)]
+
+
 class QueryConfig(C.Structure):
     _fields_ = [("lanes_per_key", _u32), ("words_per_lane", _u32), ("warps_per_block", _u32),
                 ("blocks_per_sm", _u32), ("set_stage", _u32), ("visit_order", _u32), ("l2_fetch_bytes", _u32),
@@ -61,6 +71,22 @@ SIGNATURES = {
     "rambo_list_query_configs": (_i32, [_p, _p, _i32]),
     "rambo_set_build_tiling": (_i32, [_p, _u64, _i32]),
     "rambo_query_one_per_launch": (_i32, [_p, _i32, _p, _p, _u64, _u32, _p, _p, _p]),
+    "rambo_plan_create": (_i32, [_p, _i32, _u64, _u64, _u64, _u32, C.POINTER(_p)]),
+    "rambo_plan_destroy": (None, [_p]),
+    "rambo_plan_buffers": (_i32, [_p, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), C.POINTER(_p)]),
+    "rambo_plan_launch": (_i32, [_p, _u64, _u64, _i32, _p]),
+    "rambo_plan_poll": (_i32, [_p]),
+    "rambo_plan_wait": (_i32, [_p, _i32, C.POINTER(_p), C.POINTER(_p), C.POINTER(_u64), _p]),
+    "rambo_plan_launches_per_replay": (_i32, [_p]),
+    "rambo_server_create": (_i32, [_p, C.POINTER(ServerConfig), C.POINTER(_p)]),
+    "rambo_server_submit": (_i32, [_p, _i32, _p, _u64, C.POINTER(_u64)]),
+    "rambo_server_submit_insert": (_i32, [_p, _i32, _p, _p, _p, _u64, C.POINTER(_u64)]),
+    "rambo_server_result": (_i32, [_p, _u64, _i32, _p, _u64, C.POINTER(_u64), C.POINTER(_u64)]),
+    "rambo_server_drain": (_i32, [_p]),
+    "rambo_server_stats": (_i32, [_p, C.POINTER(ServerStats)]),
+    "rambo_server_reset_stats": (_i32, [_p]),
+    "rambo_server_replay": (_i32, [_p, _p, _p, _p, _p, _u64, _p]),
+    "rambo_server_destroy": (None, [_p]),
     "rambo_autotune": (_i32, [_p, _i32, _p, _p, _u64, _u32, _i32, _i32, C.POINTER(QueryConfig), _p]),
     "rambo_save": (_i32, [_p, C.c_char_p]),
     "rambo_load": (_i32, [C.c_char_p, C.POINTER(_p)]),
@@ -242,9 +268,11 @@ class Rambo:
         self._check(rc, "insert")
 
     # -- Algorithm 2 ----------------------------------------------------------------
-    def query(self, data, offsets, kind: str = "keys", k: int = 31, stream=None):
+    def query(self, data, offsets, kind: str = "keys", k: int = 31, stream=None, copy: bool = True):
         """Returns (ids, id_offsets): numpy arrays for host inputs, torch CUDA
-        tensors for device inputs.  Query q's answer is ids[id_offsets[q]:id_offsets[q+1]]."""
+        tensors for device inputs.  Query q's answer is ids[id_offsets[q]:id_offsets[q+1]].
+        With copy=False and host inputs the arrays are views of the handle's
+        pinned result arena, valid until the next query call."""
         L = load_library()
         dev = _is_cuda_tensor(data)
         if dev:
@@ -268,12 +296,13 @@ class Rambo:
             off_t = _device_copy(offo_p.value, n + 1, "<u8")
             total = int(off_t[-1].item())
             return _device_copy(ids_p.value or 0, total, "<u4"), off_t
-        offs = np.ctypeslib.as_array(C.cast(offo_p, C.POINTER(_u64)), shape=(n + 1,)).copy()
+        offs = np.ctypeslib.as_array(C.cast(offo_p, C.POINTER(_u64)), shape=(n + 1,))
+        offs = offs.copy() if copy else offs
         total = int(offs[-1])
         if total == 0:
             return np.zeros(0, np.uint32), offs
-        ids = np.ctypeslib.as_array(C.cast(ids_p, C.POINTER(_u32)), shape=(total,)).copy()
-        return ids, offs
+        ids = np.ctypeslib.as_array(C.cast(ids_p, C.POINTER(_u32)), shape=(total,))
+        return (ids.copy() if copy else ids), offs
 
     def query_into(self, data, offsets, ids_out, id_offsets_out, kind: str = "keys", k: int = 31, stream=None) -> int:
         """Writes results into caller buffers (numpy or CUDA tensors).  Returns
@@ -296,6 +325,8 @@ class Rambo:
             rc = L.rambo_query_batch_into(self._h, *args, int(dev), ids_p, cap, oo, C.byref(needed), s)
         else:
             rc = L.rambo_query_seq_batch_into(self._h, *args, k, int(dev), ids_p, cap, oo, C.byref(needed), s)
+        if rc == ENOSPC:
+            raise RamboError(rc, "query_into (item = IDs needed)", int(needed.value))
         self._check(rc, "query_into")
         return int(needed.value)
 
@@ -406,6 +437,173 @@ class Rambo:
 
     def save(self, path: str) -> None:
         self._check(load_library().rambo_save(self._h, path.encode()), "save")
+
+
+class Plan:
+    """A graph-captured query plan (see rambo_plan_create): fixed buffers and a
+    CUDA graph replayed for every batch up to the plan's capacity."""
+
+    def __init__(self, index: "Rambo", kind: str, max_queries: int, max_items: int, max_ids: int, k: int = 31):
+        L = load_library()
+        self._index = index  # keeps the index alive while the plan exists
+        self.kind = kind
+        self.max_queries, self.max_items, self.max_ids = max_queries, max_items, max_ids
+        h = _p()
+        rc = L.rambo_plan_create(index._h, 0 if kind == "keys" else 1, max_queries, max_items, max_ids, k, C.byref(h))
+        if rc:
+            raise RamboError(rc, "rambo_plan_create")
+        self._p = h
+        hd, ho, dd, do = _p(), _p(), _p(), _p()
+        L.rambo_plan_buffers(h, C.byref(hd), C.byref(ho), C.byref(dd), C.byref(do))
+        self._elem = 8 if kind == "keys" else 1
+        dt = np.uint64 if kind == "keys" else np.uint8
+        self.host_data = np.ctypeslib.as_array(C.cast(hd, C.POINTER(C.c_uint64 if kind == "keys" else C.c_uint8)),
+                                               shape=(max_items,)).view(dt)
+        self.host_offsets = np.ctypeslib.as_array(C.cast(ho, C.POINTER(_u64)), shape=(max_queries + 1,))
+        self.dev_data_ptr, self.dev_offsets_ptr = dd.value, do.value
+        self.launches_per_replay = int(L.rambo_plan_launches_per_replay(h))
+        self._n = 0
+
+    def close(self):
+        if getattr(self, "_p", None) is not None and self._p.value:
+            load_library().rambo_plan_destroy(self._p)
+        self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_host(self, data, offsets, stream=None) -> None:
+        """Copies a batch into the plan's pinned buffers and launches it (async)."""
+        d = _host_arr(data, np.uint64 if self.kind == "keys" else np.uint8)
+        off = _host_arr(offsets, np.uint64)
+        n = off.size - 1
+        base = int(off[0])
+        items = int(off[-1]) - base
+        self.host_data[:items] = d[base: base + items]
+        self.host_offsets[: n + 1] = off - np.uint64(base)
+        self._n = n
+        rc = load_library().rambo_plan_launch(self._p, n, items, 1, _stream_handle(stream))
+        if rc:
+            raise RamboError(rc, "rambo_plan_launch")
+
+    def launch_device(self, n_queries: int, n_items: int, stream=None) -> None:
+        """Launches a batch already written to the plan's device buffers."""
+        self._n = n_queries
+        rc = load_library().rambo_plan_launch(self._p, n_queries, n_items, 0, _stream_handle(stream))
+        if rc:
+            raise RamboError(rc, "rambo_plan_launch")
+
+    def poll(self) -> bool:
+        rc = load_library().rambo_plan_poll(self._p)
+        if rc < 0:
+            raise RamboError(rc, "rambo_plan_poll")
+        return rc == 0
+
+    def wait(self, to_host: bool = True, stream=None):
+        ids_p, off_p, n_ids = _p(), _p(), _u64(0)
+        rc = load_library().rambo_plan_wait(self._p, int(to_host), C.byref(ids_p), C.byref(off_p), C.byref(n_ids),
+                                            _stream_handle(stream))
+        if rc:
+            raise RamboError(rc, "rambo_plan_wait", int(n_ids.value) if rc == ENOSPC else None)
+        n = self._n
+        total = int(n_ids.value)
+        if to_host:
+            offs = np.ctypeslib.as_array(C.cast(off_p, C.POINTER(_u64)), shape=(n + 1,)).copy()
+            ids = (np.ctypeslib.as_array(C.cast(ids_p, C.POINTER(_u32)), shape=(total,)).copy() if total
+                   else np.zeros(0, np.uint32))
+            return ids, offs
+        return _device_copy(ids_p.value or 0, total, "<u4"), _device_copy(off_p.value, n + 1, "<u8")
+
+
+class Server:
+    """Continuous-batching query server over an index (rambo_server_*)."""
+
+    def __init__(self, index: "Rambo", slots: int = 3, max_batch_queries: int = 4096, max_batch_bases: int = 1 << 22,
+                 max_batch_keys: int = 1 << 16, max_batch_ids: int = 1 << 22, k: int = 31, idle_wait_us: int = 20):
+        cfg = ServerConfig(slots, max_batch_queries, max_batch_bases, max_batch_keys, max_batch_ids, k, idle_wait_us)
+        h = _p()
+        rc = load_library().rambo_server_create(index._h, C.byref(cfg), C.byref(h))
+        if rc:
+            raise RamboError(rc, "rambo_server_create")
+        self._s = h
+        self._index = index
+        self.max_batch_ids = max_batch_ids
+
+    def submit(self, data, kind: str = "seq") -> int:
+        d = _host_arr(data, np.uint64 if kind == "keys" else np.uint8)
+        t = _u64(0)
+        rc = load_library().rambo_server_submit(self._s, 0 if kind == "keys" else 1, d.ctypes.data, d.size, C.byref(t))
+        if rc:
+            raise RamboError(rc, "rambo_server_submit")
+        return int(t.value)
+
+    def submit_insert(self, set_ids, data, offsets, kind: str = "keys") -> int:
+        ids = _host_arr(set_ids, np.uint64)
+        d = _host_arr(data, np.uint64 if kind == "keys" else np.uint8)
+        off = _host_arr(offsets, np.uint64)
+        _check_csr(d, off, "submit_insert")
+        t = _u64(0)
+        rc = load_library().rambo_server_submit_insert(self._s, 0 if kind == "keys" else 1, ids.ctypes.data,
+                                                       d.ctypes.data, off.ctypes.data, ids.size, C.byref(t))
+        if rc:
+            raise RamboError(rc, "rambo_server_submit_insert")
+        return int(t.value)
+
+    def result(self, ticket: int, wait: bool = True):
+        """(ids, latency_ns) once done; None if pending and wait is False."""
+        L = load_library()
+        cap = 1 << 16
+        while True:
+            buf = np.empty(cap, np.uint32)
+            n, lat = _u64(0), _u64(0)
+            rc = L.rambo_server_result(self._s, ticket, int(wait), buf.ctypes.data, cap, C.byref(n), C.byref(lat))
+            if rc == 1:
+                return None
+            if rc == ENOSPC:
+                cap = int(n.value)
+                continue
+            if rc:
+                raise RamboError(rc, "rambo_server_result")
+            return buf[: n.value].copy(), int(lat.value)
+
+    def drain(self) -> None:
+        load_library().rambo_server_drain(self._s)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        load_library().rambo_server_stats(self._s, C.byref(st))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def reset_stats(self) -> None:
+        load_library().rambo_server_reset_stats(self._s)
+
+    def replay(self, kinds: np.ndarray, payload: np.ndarray, byte_offsets: np.ndarray, arrival_ns: np.ndarray):
+        """Submits requests at the given arrival times (native load generator);
+        returns their tickets."""
+        k = _host_arr(kinds, np.uint8)
+        b = _host_arr(payload, np.uint8)
+        o = _host_arr(byte_offsets, np.uint64)
+        a = _host_arr(arrival_ns, np.uint64)
+        t = np.zeros(k.size, np.uint64)
+        rc = load_library().rambo_server_replay(self._s, k.ctypes.data, b.ctypes.data, o.ctypes.data, a.ctypes.data,
+                                                k.size, t.ctypes.data)
+        if rc:
+            raise RamboError(rc, "rambo_server_replay")
+        return t
+
+    def close(self) -> None:
+        if getattr(self, "_s", None) is not None and self._s.value:
+            load_library().rambo_server_destroy(self._s)
+        self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def l2_fetch_granularity(bytes_: int = 0) -> int:

@@ -66,7 +66,7 @@ def test_queries_identical_every_kernel_config(pair):
     q = w.queries.subset(np.arange(min(len(w.queries), 800)))
     try:
         for cfg in g.list_configs():
-            for stage in (1, 2):
+            for stage in (1, 2, 3):
                 for order in (0, 1, 2):
                     g.set_config(**{**cfg, "set_stage": stage, "visit_order": order})
                     assert_query_equal(g, o, q, k=w.k)

@@ -54,7 +54,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", default="genome", choices=["genome", "uneven", "document", "tiny"])
+    ap.add_argument("--config", default="genome", choices=["genome", "uneven", "document", "tiny", "serving"])
+    ap.add_argument("--rates", default="1000,10000,100000,1000000",
+                    help="serving: Poisson arrival rates (requests/s) to sweep")
+    ap.add_argument("--requests-per-rate", type=int, default=20000)
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = the full configuration)")
     ap.add_argument("--batches", type=int, default=6, help="distinct query batches rotated over the steps")
     ap.add_argument("--e2e-steps", type=int, default=30)
@@ -250,7 +253,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     nthreads = os.cpu_count() or 1
-    w = make_workload(args.config, args.scale, args.m_log2)
+    w = make_workload("document" if args.config == "serving" else args.config, args.scale, args.m_log2)
     o, build_s = oracle_index(w, nthreads)
     q = w.queries
     # size one step to a bounded sample so the whole run stays within minutes
@@ -544,10 +547,151 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# serving (continuous batching with streaming inserts)
+# ---------------------------------------------------------------------------
+
+def serving_workload(scale: float, rng):
+    """Document index (K docs over a Zipf(1.0) vocabulary, B=320, R=8, m=2^25,
+    eta=3) plus genome-like sets for the DNA queries, and new documents to
+    stream in, 100 per insert batch."""
+    docs = synth.make("document", scale)
+    gen = synth.make("genome", 0.1 * max(scale, 0.05))
+    vocab = docs.meta["vocab_keys"]
+    df = docs.meta["df"]
+    p = df / df.sum()
+    mu = np.log(500.0) - 0.5
+    new_docs = []
+    for _ in range(400):
+        L = int(np.clip(np.round(rng.lognormal(mu, 1.0)), 1, vocab.size))
+        new_docs.append(np.unique(vocab[rng.choice(vocab.size, L, p=p)]))
+    return docs, gen, new_docs, p
+
+
+def serving_requests(rng, docs, gen, p, n):
+    """A third each: 1-term and 5-term key queries by corpus term frequency,
+    and DNA substrings of U{31..2000} bases of the genome-like sets."""
+    vocab = docs.meta["vocab_keys"]
+    kinds = np.zeros(n, np.uint8)
+    payload = []
+    r = rng.random(n)
+    for i in range(n):
+        if r[i] < 1 / 3:
+            payload.append(vocab[rng.choice(vocab.size, 1, p=p)].astype(np.uint64).view(np.uint8))
+        elif r[i] < 2 / 3:
+            payload.append(vocab[rng.choice(vocab.size, 5, replace=False, p=p)].astype(np.uint64).view(np.uint8))
+        else:
+            kinds[i] = 1
+            gi = int(rng.integers(0, len(gen.sets)))
+            s = gen.sets.item(gi)
+            L = int(min(s.size, rng.integers(31, 2001)))
+            a = int(rng.integers(0, s.size - L + 1))
+            payload.append(s[a: a + L])
+    boff = np.zeros(n + 1, np.uint64)
+    np.cumsum([x.size for x in payload], out=boff[1:])
+    return kinds, np.concatenate(payload), boff, payload
+
+
+def run_serving(args):
+    import torch
+
+    from paper_1910_02611_gb300 import Rambo, Server
+
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rng = np.random.default_rng(1005)
+    t_gen = time.perf_counter()
+    docs, gen, new_docs, p = serving_workload(args.scale, rng)
+    rates = [float(x) for x in args.rates.split(",")]
+    n_req = args.requests_per_rate
+    phases = [serving_requests(rng, docs, gen, p, n_req) for _ in rates]
+    t_gen = time.perf_counter() - t_gen
+    n_docs, n_gen = len(docs.sets), len(gen.sets)
+    K = n_docs + n_gen + len(new_docs)
+    g = Rambo(K, docs.B, docs.R, docs.m, docs.eta, 42)
+    g.insert(docs.sets.ids, docs.sets.data, docs.sets.offsets, kind="keys")
+    g.insert(gen.sets.ids + np.uint64(n_docs), gen.sets.data, gen.sets.offsets, kind="seq")
+    srv = Server(g, slots=4, max_batch_queries=1024, max_batch_bases=1024 * 2000, max_batch_keys=1024 * 5,
+                 max_batch_ids=1 << 25)
+    sweep = []
+    next_doc = 0
+    check_sample = []
+    clocks = None
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    time.sleep(0.3)
+    for (kinds, payload, boff, items), rate in zip(phases, rates):
+        # a streamed insert batch of 100 new documents before every phase
+        batch = new_docs[next_doc: next_doc + 100]
+        ids = np.arange(n_docs + n_gen + next_doc, n_docs + n_gen + next_doc + len(batch), dtype=np.uint64)
+        off = np.zeros(len(batch) + 1, np.uint64)
+        np.cumsum([b.size for b in batch], out=off[1:])
+        t_ins = srv.submit_insert(ids, np.concatenate(batch), off, kind="keys")
+        next_doc += len(batch)
+        srv.drain()
+        srv.result(t_ins)
+        srv.reset_stats()
+        arrivals = np.cumsum(rng.exponential(1e9 / rate, len(kinds))).astype(np.uint64)
+        t0 = time.perf_counter()
+        tickets = srv.replay(kinds, payload, boff, arrivals)
+        srv.drain()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        results = [srv.result(int(t))[0] for t in tickets]
+        keys = st["keys"]
+        sweep.append({"rate_per_s": rate, "offered_s": float(arrivals[-1]) / 1e9, "wall_s": wall,
+                      "queries": st["queries"], "batches": st["batches"],
+                      "mean_batch": st["queries"] / max(st["batches"], 1),
+                      "keys_per_s": keys / wall, "queries_per_s": st["queries"] / wall,
+                      "p50_ms": st["p50_ns"] / 1e6, "p99_ms": st["p99_ns"] / 1e6, "max_ms": st["max_ns"] / 1e6})
+        sel = rng.choice(len(kinds), 64, replace=False)
+        check_sample.append((sel, kinds, items, results))
+    clocks = sampler.stop()
+    srv.close()
+    # served answers equal the plain query call at the same (final) index state
+    # for the last phase (no insert happened after it)
+    sel, kinds, items, results = check_sample[-1]
+    same = True
+    for i in sel:
+        kind = "keys" if kinds[i] == 0 else "seq"
+        data = items[i].view(np.uint64) if kind == "keys" else items[i]
+        ids_plain, _ = g.query(data, np.array([0, data.size], np.uint64), kind=kind)
+        same &= bool(np.array_equal(ids_plain, results[i]))
+    best = max(sweep, key=lambda x: x["keys_per_s"])
+    line = {
+        "metric": METRIC, "value": best["keys_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(rates),
+        "warmup": 0, "ms_per_step": 1000 * sum(x["wall_s"] for x in sweep) / len(sweep),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"serving: document index K={n_docs} (+{n_gen} genome sets, +{len(new_docs)} "
+                               f"streamed docs capacity), B={docs.B}, R={docs.R}, m=2^{int(np.log2(docs.m))}, "
+                               f"eta={docs.eta}; Poisson arrivals, 1/3 1-term, 1/3 5-term, 1/3 DNA 31-2000 bases; "
+                               f"100-document insert batch before every rate phase",
+                   "step": f"one rate phase of {n_req} requests", "slots": 4},
+        "latency": {"p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"]},
+        "sweep": sweep,
+        "served_equals_plain_call": same,
+        "e2e": {"value": best["keys_per_s"], "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(x.size for x in phases[-1][3])),
+                "d2h_bytes_per_step": None, "note": "requests enter from host memory and results return to host "
+                                                    "memory inside the measured latency"},
+        "clocks": clocks,
+        "setup_s": {"workload_generation": t_gen},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                json.dump(line, f, indent=1)
+    g.close()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

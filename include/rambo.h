@@ -286,6 +286,14 @@ int rambo_export_index(const rambo_t *h, uint32_t *host_words, uint64_t n_words)
 int rambo_export_registered(const rambo_t *h, uint32_t *host_words, uint64_t n_words);
 int rambo_export_partition(const rambo_t *h, uint16_t *host_phi, uint64_t n);
 
+/* Folding over (appendix, Sec. 5.2): ORs cell b + B/2 onto cell b of every
+ * table, halving B (and the index) while R, m, eta and the hashes stay.  The
+ * result is exactly the index that rambo_create with B/2 and the same seed
+ * would have built from the same inserts, because the partition hash mod B
+ * then mod B/2 equals the hash mod B/2.  Resets the query configuration.
+ * Errors: RAMBO_EINVAL when B is odd or 1, RAMBO_ENOMEM. */
+int rambo_fold(rambo_t *h, void *stream);
+
 /* Number of set bits of every Bloom filter, out[r*B + b] (host memory, R*B
  * entries); fill/m is the quantity Sec. 2's false-positive formula predicts. */
 int rambo_cell_popcount(const rambo_t *h, uint64_t *host_out, void *stream);

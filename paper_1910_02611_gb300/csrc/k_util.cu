@@ -408,6 +408,44 @@ cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_
 }
 
 // ---------------------------------------------------------------------------
+// folding over (appendix): cell b of the folded index is the OR of cells b and
+// b + B/2.  Each thread rewrites whole rows from the old layout (W words,
+// stride S) into the new one (W2 words, stride S2).
+
+__device__ __forceinline__ uint32_t row_window(const uint32_t* row, uint32_t W, uint32_t x) {
+    // the 32 bits starting at bit x of a row of W words (bits past the row are zero)
+    const uint32_t wi = x >> 5, sh = x & 31;
+    const uint32_t lo = wi < W ? row[wi] : 0u;
+    if (!sh) return lo;
+    const uint32_t hi = wi + 1 < W ? row[wi + 1] : 0u;
+    return (lo >> sh) | (hi << (32 - sh));
+}
+
+__global__ void k_fold(const uint32_t* __restrict__ old_rows, uint64_t n_rows, uint32_t W, uint32_t S, uint32_t B2,
+                       uint32_t W2, uint32_t S2, uint32_t* __restrict__ new_rows) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n_rows;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t* row = old_rows + p * S;
+        uint32_t* out = new_rows + p * S2;
+        for (uint32_t w = 0; w < S2; ++w) {
+            uint32_t v = 0;
+            if (w < W2) {
+                v = row_window(row, W, 32 * w) | row_window(row, W, B2 + 32 * w);
+                const uint32_t bits_here = B2 - 32 * w;  // cells of the folded row in this word
+                if (bits_here < 32) v &= (1u << bits_here) - 1u;
+            }
+            out[w] = v;
+        }
+    }
+}
+
+cudaError_t launch_fold(const uint32_t* old_rows, uint64_t n_rows, uint32_t W, uint32_t S, uint32_t B2, uint32_t W2,
+                        uint32_t S2, uint32_t* new_rows, cudaStream_t s) {
+    k_fold<<<grid_for(n_rows, 256, 152 * 64), 256, 0, s>>>(old_rows, n_rows, W, S, B2, W2, S2, new_rows);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // statistics: set bits of every Bloom filter (bit b of the rows of table r)
 
 __global__ void k_cell_popcount(IndexView ix, unsigned long long* out) {

@@ -193,6 +193,30 @@ void free_handle(rambo* h) {
     delete h;
 }
 
+// Member lists and member bitmaps of every cell (sparse and union set stages),
+// rebuilt from the partition table; skipped when they would be too large.
+int build_cell_members(rambo* h, cudaStream_t s) {
+    if (h->mem_off) cudaFree(h->mem_off);
+    if (h->mem_ids) cudaFree(h->mem_ids);
+    if (h->mem_bits) cudaFree(h->mem_bits);
+    h->mem_off = nullptr;
+    h->mem_ids = nullptr;
+    h->mem_bits = nullptr;
+    const uint64_t cells = (uint64_t)h->R * h->B, K = h->K;
+    if ((uint64_t)h->R * K * 4 > (1ull << 30)) return RAMBO_OK;
+    if (cudaMalloc(&h->mem_off, (cells + 1 + scan_tmp_words(cells)) * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&h->mem_ids, (uint64_t)h->R * K * sizeof(uint32_t)) != cudaSuccess)
+        return RAMBO_ENOMEM;
+    RK(h->fill.ensure(cells));
+    CK(launch_members(h->view(), h->mem_off, h->mem_ids, h->fill.p, s));
+    const uint64_t mb_bytes = cells * ((K + 31) / 32) * 4;
+    if ((K + 31) / 32 <= 4096 && mb_bytes <= (256ull << 20)) {
+        if (cudaMalloc(&h->mem_bits, mb_bytes) != cudaSuccess) return RAMBO_ENOMEM;
+        CK(launch_member_bits(h->view(), h->mem_bits, s));
+    }
+    return RAMBO_OK;
+}
+
 void default_config(rambo* h) {
     // one vector read per probe where the row allows it
     int V = h->S % 4 == 0 ? 4 : (h->S % 2 == 0 ? 2 : 1);
@@ -569,23 +593,8 @@ int rambo_create(uint64_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     if (cudaMemsetAsync(h->reg, 0, ((K + 31) / 32) * 4, s) != cudaSuccess) return fail(RAMBO_ECUDA);
     if (launch_phi_init(h->phi, K, R, B, h->a, h->c, s) != cudaSuccess) return fail(RAMBO_ECUDA);
     if (launch_status_reset(h->st, s) != cudaSuccess) return fail(RAMBO_ECUDA);
-    // members of every cell, for the sparse set stage (skipped for huge K)
-    const uint64_t cells = (uint64_t)R * B;
-    if ((uint64_t)R * K * 4 <= (1ull << 30)) {
-        if (cudaMalloc(&h->mem_off, (cells + 1 + scan_tmp_words(cells)) * sizeof(uint64_t)) != cudaSuccess ||
-            cudaMalloc(&h->mem_ids, (uint64_t)R * K * sizeof(uint32_t)) != cudaSuccess)
-            return fail(RAMBO_ENOMEM);
-        rc = h->fill.ensure(cells);
-        if (rc) return fail(rc);
-        if (launch_members(h->view(), h->mem_off, h->mem_ids, h->fill.p, s) != cudaSuccess)
-            return fail(RAMBO_ECUDA);
-        // member bitmaps of every cell for the union set stage (bounded size)
-        const uint64_t mb_bytes = cells * ((K + 31) / 32) * 4;
-        if ((K + 31) / 32 <= 4096 && mb_bytes <= (256ull << 20)) {
-            if (cudaMalloc(&h->mem_bits, mb_bytes) != cudaSuccess) return fail(RAMBO_ENOMEM);
-            if (launch_member_bits(h->view(), h->mem_bits, s) != cudaSuccess) return fail(RAMBO_ECUDA);
-        }
-    }
+    rc = build_cell_members(h, s);
+    if (rc) return fail(rc);
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(RAMBO_ECUDA);
     default_config(h);
     *out = h;
@@ -812,6 +821,37 @@ int rambo_autotune(rambo_t* h, int kind, const void* data, const uint64_t* offse
     }
     h->cfg = win;
     if (best) *best = win;
+    return RAMBO_OK;
+}
+
+int rambo_fold(rambo_t* h, void* stream) {
+    if (!h || h->B < 2 || (h->B & 1)) return RAMBO_EINVAL;
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t B2 = h->B / 2, W2 = (B2 + 31) / 32, S2 = stride_for(W2);
+    const uint64_t n_rows = (uint64_t)h->R * h->m;
+    uint32_t* rows2 = nullptr;
+    if (cudaMalloc(&rows2, n_rows * S2 * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return RAMBO_ENOMEM;
+    }
+    cudaError_t e = launch_fold(h->rows, n_rows, h->W, h->S, B2, W2, S2, rows2, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(rows2);
+        return map_cuda(e);
+    }
+    cudaFree(h->rows);
+    h->rows = rows2;
+    h->B = B2;
+    h->W = W2;
+    h->S = S2;
+    // (a*i + c mod P) mod B mod B/2 = (a*i + c mod P) mod B/2: the folded
+    // partition is the same hash with range B/2
+    CK(launch_phi_init(h->phi, h->K, h->R, h->B, h->a, h->c, s));
+    RK(build_cell_members(h, s));
+    CK(cudaStreamSynchronize(s));
+    default_config(h);
     return RAMBO_OK;
 }
 

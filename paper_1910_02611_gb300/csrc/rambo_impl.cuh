@@ -221,6 +221,8 @@ cudaError_t launch_cell_popcount(const IndexView& ix, unsigned long long* out, c
 cudaError_t launch_members(const IndexView& ix, uint64_t* mem_off, uint32_t* mem_ids,
                            uint32_t* fill, cudaStream_t s);
 cudaError_t launch_member_bits(const IndexView& ix, uint32_t* mem_bits, cudaStream_t s);
+cudaError_t launch_fold(const uint32_t* old_rows, uint64_t n_rows, uint32_t W, uint32_t S, uint32_t B2, uint32_t W2,
+                        uint32_t S2, uint32_t* new_rows, cudaStream_t s);
 
 cudaError_t launch_cluster_order(const BatchView& b, uint64_t* keys, uint32_t* hist, uint64_t* bucket_off,
                                  uint64_t* scan_tmp, uint64_t scan_tmp_words, uint32_t* perm, const DevStatus* st,

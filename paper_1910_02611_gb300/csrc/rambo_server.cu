@@ -40,6 +40,7 @@ struct Op {
     uint64_t items = 0;  // keys or bases
     std::vector<uint64_t> set_ids, offsets;
     uint32_t k = 31;
+    bool solo = false;  // results overflowed a shared batch: run alone
     Clock::time_point t_submit;
 };
 
@@ -93,6 +94,20 @@ void finish_slot(rambo_server* S, Slot& sl) {
     uint64_t n_ids = 0;
     const int rc = rambo_plan_wait(sl.plan, 1, &ids, &off, &n_ids, sl.stream);
     const auto now = Clock::now();
+    if (rc == RAMBO_ENOSPC && sl.members.size() > 1) {
+        // the batch's answers did not fit the slot: requeue its queries at the
+        // front, each to run alone (their order among queries does not matter)
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto& qq = S->q[sl.kind];
+        for (auto it = sl.members.rbegin(); it != sl.members.rend(); ++it) {
+            it->solo = true;
+            qq.push_front(std::move(*it));
+        }
+        sl.members.clear();
+        sl.busy = false;
+        S->cv_work.notify_one();
+        return;
+    }
     {
         std::lock_guard<std::mutex> lk(S->mu);
         for (size_t i = 0; i < sl.members.size(); ++i) {
@@ -124,10 +139,13 @@ bool admit(rambo_server* S, Slot& sl) {
     const uint64_t max_items = sl.kind == 0 ? S->cfg.max_batch_keys : S->cfg.max_batch_bases;
     uint64_t n = 0, items = 0;
     while (!qq.empty() && qq.front().seq < barrier && n < max_q && items + qq.front().items <= max_items) {
+        if (qq.front().solo && n > 0) break;  // a requeued query rides alone
+        const bool solo = qq.front().solo;
         items += qq.front().items;
         sl.members.push_back(std::move(qq.front()));
         qq.pop_front();
         ++n;
+        if (solo) break;
     }
     if (!n) return false;
     void* hd = nullptr;

@@ -65,6 +65,7 @@ SIGNATURES = {
     "rambo_export_registered": (_i32, [_p, _p, _u64]),
     "rambo_export_partition": (_i32, [_p, _p, _u64]),
     "rambo_cell_popcount": (_i32, [_p, _p, _p]),
+    "rambo_fold": (_i32, [_p, _p]),
     "rambo_last_query_stats": (_i32, [_p, C.POINTER(QueryStats)]),
     "rambo_get_query_config": (_i32, [_p, C.POINTER(QueryConfig)]),
     "rambo_set_query_config": (_i32, [_p, C.POINTER(QueryConfig)]),
@@ -434,6 +435,12 @@ class Rambo:
         self._check(load_library().rambo_cell_popcount(self._h, out.ctypes.data, _stream_handle(stream)),
                     "cell_popcount")
         return out.reshape(self.R, self.B)
+
+    def fold(self, stream=None) -> None:
+        """Folding over: B -> B/2 by OR-ing cell b + B/2 onto cell b."""
+        self._check(load_library().rambo_fold(self._h, _stream_handle(stream)), "fold")
+        info = self.info()
+        self.B, self.row_stride, self.row_words = info.B, info.row_stride, info.row_words
 
     def save(self, path: str) -> None:
         self._check(load_library().rambo_save(self._h, path.encode()), "save")

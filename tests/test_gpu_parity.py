@@ -363,3 +363,26 @@ def test_autotune_picks_a_config_and_results_stay_identical(mods):
     assert best == g.get_config()
     assert best["visit_order"] in (1, 2)
     assert_query_equal(g, o, w.queries)
+
+
+@pytest.mark.parametrize("B,folds", [(64, 1), (640, 3), (320, 2), (10, 1)])
+def test_folding_over_equals_an_index_built_with_half_the_cells(mods, B, folds):
+    # appendix "folding over": OR of cell b + B/2 onto cell b.  With the same
+    # seed the folded index equals the oracle (and a GPU index) built with
+    # B / 2^folds cells from the same sets.
+    Rambo, Oracle = mods
+    w = synth.make("genome", 0.01, m=1 << 15, B=B, R=4)
+    g = Rambo(w.K, B, w.R, w.m, w.eta, w.seed)
+    g.insert(w.sets.ids, w.sets.data, w.sets.offsets, kind="seq")
+    for _ in range(folds):
+        g.fold()
+    B2 = B >> folds
+    o = Oracle(w.K, B2, w.R, w.m, w.eta, w.seed)
+    o.insert_seq_batch(w.sets.ids, w.sets.data, w.sets.offsets, 31)
+    assert g.B == B2
+    assert_index_equal(g, o)
+    assert_partition_equal(g, o)
+    assert_query_equal(g, o, w.queries)
+    direct = Rambo(w.K, B2, w.R, w.m, w.eta, w.seed)
+    direct.insert(w.sets.ids, w.sets.data, w.sets.offsets, kind="seq")
+    assert np.array_equal(direct.export_index(), g.export_index())

@@ -315,3 +315,19 @@ def test_rambo_false_positive_rate_lemma_4_1(fp_setup, V):
     delta = K * (1 - (1 - p) * q) ** R
     any_fp = (obs > 0).mean()
     assert any_fp <= min(1.0, delta) + 4 * np.sqrt(max(any_fp, 1 / n_keys) / n_keys)
+
+
+def test_folding_over_equals_half_the_cells(oracle_mod):
+    # appendix, folding over: OR-ing cell b + B/2 onto cell b gives the Bloom
+    # filter of the union of both cells' sets, i.e. the structure built with
+    # B/2 cells; the partition hash mod B then mod B/2 is the hash mod B/2.
+    rng = np.random.default_rng(30)
+    K, B, R, m = 40, 12, 3, 1 << 12
+    sets, _ = _random_sets(rng, K, 30, 80)
+    full = _build(oracle_mod, sets, K, B, R, m, 2, 99)
+    half = _build(oracle_mod, sets, K, B // 2, R, m, 2, 99)
+    for r in range(R):
+        for b in range(B // 2):
+            assert np.array_equal(full.export_bf(r, b) | full.export_bf(r, b + B // 2), half.export_bf(r, b))
+        for i in range(K):
+            assert full.phi(r, i) % (B // 2) == half.phi(r, i)

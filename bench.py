@@ -192,10 +192,17 @@ def load_peaks() -> dict:
 
 
 def kernel_source_hash() -> str:
+    """Hash of the query kernel's device code: k_query.cuh, its instantiation
+    header, and the device helpers of rambo_impl.cuh (up to the launcher
+    declarations)."""
     h = hashlib.sha256()
-    for name in ("k_query.cuh", "k_query_inst.cuh", "rambo_impl.cuh"):
-        with open(os.path.join(ROOT, "paper_1910_02611_gb300", "csrc", name), "rb") as f:
+    csrc = os.path.join(ROOT, "paper_1910_02611_gb300", "csrc")
+    for name in ("k_query.cuh", "k_query_inst.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
+    with open(os.path.join(csrc, "rambo_impl.cuh"), "rb") as f:
+        text = f.read()
+    h.update(text.split(b"// launchers (defined in the .cu files)")[0])
     return h.hexdigest()[:16]
 
 

@@ -489,6 +489,10 @@ class Plan:
         n = off.size - 1
         base = int(off[0])
         items = int(off[-1]) - base
+        if n > self.max_queries or items > self.max_items:
+            # the library rejects a batch beyond capacity before touching any buffer
+            rc = load_library().rambo_plan_launch(self._p, n, items, 1, _stream_handle(stream))
+            raise RamboError(rc if rc else EINVAL, "rambo_plan_launch")
         self.host_data[:items] = d[base: base + items]
         self.host_offsets[: n + 1] = off - np.uint64(base)
         self._n = n

@@ -33,7 +33,7 @@
 namespace rgb {
 
 constexpr int QK_THREADS_MAX = 256;
-constexpr int QK_ID_CAP = 128;  // per-warp staging of dense-stage survivors
+constexpr int QK_ID_CAP = 512;  // per-warp staging words: dense survivors, or the union stage's cell lists
 
 __host__ __device__ inline uint32_t qk_bitmap_words(uint64_t K) { return (uint32_t)((K + 31) / 32); }
 
@@ -233,13 +233,18 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                 // the fewest warp-wide operations (Lemma 4.4's candidate term).
                 int stage = set_stage;
                 if (!use_bitmap) stage = 1;
-                if (stage == 3 && !ix.mem_bits) stage = 1;
+                uint32_t list_total = 0;
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r)
+                    if (r < R) list_total += pc[r] * 2 > ix.B ? ix.B - pc[r] : pc[r];
+                const bool union_ok = ix.mem_bits && list_total <= 2u * QK_ID_CAP;
+                if (stage == 3 && !union_ok) stage = 1;
                 if (stage == 0) {
                     const uint64_t kw = (ix.K + 31) / 32;
                     const uint64_t dense = kw * (uint64_t)(R + 2);
                     const uint64_t sparse = ((uint64_t)pmin * (ix.K / ix.B + 1) / 32 + pmin) * (uint64_t)(R + 3) + kw / 16;
                     uint64_t uni = ~0ull;
-                    if (ix.mem_bits) {
+                    if (union_ok) {
                         uni = kw / 32 + 1;
 #pragma unroll
                         for (int r = 0; r < RMAX; ++r) {
@@ -252,12 +257,31 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                 }
                 if (use_bitmap) {
                     if (stage == 1) {
-                        // dense: one ballot per 32 IDs becomes one bitmap word
-                        for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
-                            const uint64_t i = i0 + lane;
-                            const bool ok = (i < ix.K) && qk_set_passes(ix, sM, i, -1);
-                            const unsigned bal = __ballot_sync(FULL, ok);
-                            if (lane == 0) sBits[i0 >> 5] = bal;
+                        // dense: one ballot per 32 IDs becomes one bitmap word; four
+                        // chunks per iteration so their table loads are in flight together
+                        constexpr int DU = 4;
+                        for (uint64_t i0 = 0; i0 < ix.K; i0 += 32 * DU) {
+                            uint32_t regw[DU];
+                            uint4 ph[DU];
+#pragma unroll
+                            for (int u = 0; u < DU; ++u) {
+                                const uint64_t i = i0 + 32 * u + lane;
+                                regw[u] = i < ix.K ? __ldg(ix.reg + (i >> 5)) : 0u;
+                                ph[u] = i < ix.K ? __ldg(reinterpret_cast<const uint4*>(ix.phi) + i) : make_uint4(0, 0, 0, 0);
+                            }
+#pragma unroll
+                            for (int u = 0; u < DU; ++u) {
+                                const uint64_t i = i0 + 32 * u + lane;
+                                bool ok = i < ix.K && ((regw[u] >> (i & 31)) & 1u);
+                                const uint32_t cell[8] = {ph[u].x & 0xffffu, ph[u].x >> 16, ph[u].y & 0xffffu,
+                                                          ph[u].y >> 16,     ph[u].z & 0xffffu, ph[u].z >> 16,
+                                                          ph[u].w & 0xffffu, ph[u].w >> 16};
+#pragma unroll
+                                for (int r = 0; r < RMAX; ++r)
+                                    if (r < R) ok &= (sM[r * ix.S + (cell[r] >> 5)] >> (cell[r] & 31)) & 1u;
+                                const unsigned bal = __ballot_sync(FULL, ok);
+                                if (lane == 0 && i0 + 32 * u < ix.K) sBits[(i0 >> 5) + u] = bal;
+                            }
                         }
                     } else if (stage == 2) {
                         // sparse: members of the hit cells of table rstar, tested on the other tables
@@ -278,28 +302,81 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                     } else {
                         // union of member bitmaps: G_r = OR of the hit cells' bitmaps
                         // (or NOT of the missed cells' when over half are hit); the
-                        // answer is registered AND every G_r
-                        for (uint32_t w = lane; w < bw; w += 32) {
-                            uint32_t g = __ldg(ix.reg + w);
+                        // answer is registered AND every G_r.  The cell lists go to
+                        // shared memory first (warp prefix sums), then each lane ORs
+                        // UW words per cell for UC cells at a time.
+                        uint16_t* list = reinterpret_cast<uint16_t*>(sIds);
+                        uint32_t list_off[RMAX + 1];
+                        list_off[0] = 0;
+#pragma unroll
+                        for (int r = 0; r < RMAX; ++r) {
+                            uint32_t n_r = 0;
+                            if (r < R) {
+                                const bool comp = pc[r] * 2 > ix.B;
+                                for (uint32_t c0 = 0; c0 < ix.W; c0 += 32) {
+                                    const uint32_t cw = c0 + lane;
+                                    uint32_t bits = 0;
+                                    if (cw < ix.W) {
+                                        bits = comp ? ~sM[r * ix.S + cw] : sM[r * ix.S + cw];
+                                        if (cw == ix.W - 1 && (ix.B & 31)) bits &= (1u << (ix.B & 31)) - 1u;
+                                    }
+                                    const uint32_t c = __popc(bits);
+                                    uint32_t incl = c;
+#pragma unroll
+                                    for (int off = 1; off < 32; off <<= 1) {
+                                        const uint32_t y = __shfl_up_sync(FULL, incl, off);
+                                        if (lane >= (unsigned)off) incl += y;
+                                    }
+                                    uint32_t pos = list_off[r] + n_r + incl - c;
+                                    while (bits) {
+                                        list[pos++] = (uint16_t)(cw * 32 + (__ffs(bits) - 1));
+                                        bits &= bits - 1;
+                                    }
+                                    n_r += __shfl_sync(FULL, incl, 31);
+                                }
+                            }
+                            list_off[r + 1] = list_off[r] + n_r;
+                        }
+                        __syncwarp();
+                        constexpr int UW = 4, UC = 4;
+                        for (uint32_t wb = 0; wb < bw; wb += 32 * UW) {
+                            uint32_t g[UW];
+#pragma unroll
+                            for (int u = 0; u < UW; ++u) {
+                                const uint32_t w = wb + 32 * u + lane;
+                                g[u] = w < bw ? __ldg(ix.reg + w) : 0u;
+                            }
 #pragma unroll
                             for (int r = 0; r < RMAX; ++r) {
-                                if (r >= R || !g) continue;
+                                if (r >= R) continue;
                                 const bool comp = pc[r] * 2 > ix.B;
-                                const uint32_t* cm = sM + r * ix.S;
-                                const uint32_t* mb = ix.mem_bits + (uint64_t)r * ix.B * bw + w;
-                                uint32_t acc = 0;
-                                for (uint32_t cw = 0; cw < ix.W; ++cw) {
-                                    uint32_t bits = comp ? ~cm[cw] : cm[cw];
-                                    if (cw == ix.W - 1 && (ix.B & 31)) bits &= (1u << (ix.B & 31)) - 1u;
-                                    while (bits) {
-                                        const uint32_t cb = cw * 32 + (__ffs(bits) - 1);
-                                        bits &= bits - 1;
-                                        acc |= __ldg(mb + (uint64_t)cb * bw);
+                                const uint32_t* mb = ix.mem_bits + (uint64_t)r * ix.B * bw;
+                                uint32_t acc[UW] = {0, 0, 0, 0};
+                                for (uint32_t t = list_off[r]; t < list_off[r + 1]; t += UC) {
+                                    uint32_t v[UC][UW];
+#pragma unroll
+                                    for (int c = 0; c < UC; ++c) {
+                                        const bool have = t + c < list_off[r + 1];
+                                        const uint32_t* col = mb + (uint64_t)(have ? list[t + c] : 0) * bw;
+#pragma unroll
+                                        for (int u = 0; u < UW; ++u) {
+                                            const uint32_t w = wb + 32 * u + lane;
+                                            v[c][u] = (have && w < bw) ? __ldg(col + w) : 0u;
+                                        }
                                     }
+#pragma unroll
+                                    for (int c = 0; c < UC; ++c)
+#pragma unroll
+                                        for (int u = 0; u < UW; ++u) acc[u] |= v[c][u];
                                 }
-                                g &= comp ? ~acc : acc;
+#pragma unroll
+                                for (int u = 0; u < UW; ++u) g[u] &= comp ? ~acc[u] : acc[u];
                             }
-                            sBits[w] = g;
+#pragma unroll
+                            for (int u = 0; u < UW; ++u) {
+                                const uint32_t w = wb + 32 * u + lane;
+                                if (w < bw) sBits[w] = g[u];
+                            }
                         }
                     }
                     __syncwarp();

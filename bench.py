@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--per-query-baseline", type=int, default=2000,
                     help="queries timed through the one-query-per-launch kernel (0 = skip)")
     ap.add_argument("--autotune", action="store_true", help="pick the kernel configuration on batch 0 first")
+    ap.add_argument("--api", choices=["call", "plan"], default="call",
+                    help="timed step through rambo_query_*_into (call) or a replayed CUDA-graph plan (plan)")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -373,6 +375,30 @@ def run_ours(args):
         g.query_into(qd, qo, out_ids, out_off[: nq + 1], kind=batches[0].kind, k=w.k)
         return nk
 
+    plans = []
+    if args.api == "plan":
+        from paper_1910_02611_gb300 import Plan
+        from paper_1910_02611_gb300.rambo import _CudaArray
+
+        # one graph-captured plan per batch, its inputs copied into the plan's
+        # device buffers before the timed region
+        for (qd, qo, nk, nq), q in zip(dev_batches, batches):
+            items = int(q.offsets[-1] - q.offsets[0])
+            plan = Plan(g, q.kind, max_queries=nq, max_items=max(items, 1), max_ids=out_cap, k=w.k)
+            nbytes = items * (8 if q.kind == "keys" else 1)
+            dst = torch.as_tensor(_CudaArray(plan.dev_data_ptr, nbytes, "|u1"), device=dev)
+            dst.copy_(qd.view(torch.uint8)[:nbytes])
+            dst_off = torch.as_tensor(_CudaArray(plan.dev_offsets_ptr, nq + 1, "<i8"), device=dev)
+            dst_off.copy_(qo - qo[0])
+            plans.append((plan, nq, items, nk))
+        torch.cuda.synchronize()
+
+        def plan_step(i):
+            plan, nq, items, nk = plans[i % len(plans)]
+            plan.launch_device(nq, items, stream=stream)
+            plan.wait(to_host=False, copy=False, stream=stream)
+            return nk
+
     for i in range(args.warmup):
         flush.zero_()
         one_step(i)
@@ -389,18 +415,33 @@ def run_ours(args):
     for i in range(args.steps):
         flush.zero_()
         e0.record(stream)
-        nk = one_step(i)
+        nk = plan_step(i) if plans else one_step(i)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        st = g.last_query_stats()
         keys += nk
+        if plans:
+            launches += plans[i % len(plans)][0].launches_per_replay
+            continue
+        st = g.last_query_stats()
         probed += st["keys_probed"]
         rows_read += st["rows_read"]
         qk_ms.append(st["query_kernel_ms"])
         launches += st["kernel_launches"]
         n_ids += st["n_results"]
     torch.cuda.synchronize()
+    if plans:
+        # the kernel time and rows read of the roofline come from direct calls of
+        # the same kernel on the same batches (the graph hides per-kernel events)
+        n_roof = min(args.steps, 20)
+        for i in range(n_roof):
+            flush.zero_()
+            one_step(i)
+            st = g.last_query_stats()
+            probed += st["keys_probed"] * args.steps / n_roof
+            rows_read += st["rows_read"] * args.steps / n_roof
+            qk_ms.append(st["query_kernel_ms"] * args.steps / n_roof)
+            n_ids += st["n_results"] * args.steps / n_roof
     if dist:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
@@ -517,6 +558,7 @@ def run_ours(args):
                         f"{len(batches[0])} {'query sequences' if batches[0].kind == 'seq' else 'key queries'} "
                         f"per step (scale {args.scale})",
             "parallelism": f"replicas x{world} (one index per GPU, disjoint batches)",
+            "api": "CUDA-graph plan replay" if plans else "rambo_query_*_into call",
             "l2": f"flushed before every step (256 MiB write); index {g.info().index_bytes / 2**30:.1f} GiB",
             "batches": len(batches),
         },

@@ -18,7 +18,9 @@
  *     h_{r,j}(x) = (s_{r,j} * mix64(x) mod 2^64) >> (64 - L)
  *   mix64 being SplitMix64's output finalizer.  DNA k-mers (1 <= k <= 32) are
  *   keys of 2 bits per base, A/a=0 C/c=1 G/g=2 T/t=3, first base most
- *   significant; every length-k window of a sequence is one key.
+ *   significant; every length-k window of a sequence is one key (with
+ *   RAMBO_KMER_CANONICAL in k: the smaller of the window's key and its
+ *   reverse complement's, the complement of code c being 3 - c).
  *
  * Conventions for every entry point:
  *   - Return RAMBO_OK (0) or a negative RAMBO_E* code; rambo_strerror names it.
@@ -66,6 +68,10 @@ enum {
                             rambo_query_seq_batch_noalloc */
 };
 
+/* OR-ed into a k-mer length argument: every window's key is the smaller of
+ * the window and its reverse complement (both DNA strands give one key). */
+#define RAMBO_KMER_CANONICAL 0x100u
+
 /* Limits of this implementation. */
 #define RAMBO_MAX_R 8        /* repetitions (tables) */
 #define RAMBO_MAX_ETA 4      /* hashes per Bloom filter */
@@ -108,6 +114,11 @@ int rambo_get_info(const rambo_t *h, rambo_info_t *out);
 int rambo_insert_batch(rambo_t *h, const uint64_t *set_ids, const uint64_t *keys,
                        const uint64_t *offsets, uint64_t n_sets, int on_device,
                        void *stream);
+
+/* Algorithm 1 for one set: inserts keys[0 .. n) into set set_id (same as
+ * rambo_insert_batch with one item). */
+int rambo_insert(rambo_t *h, uint64_t set_id, const uint64_t *keys, uint64_t n, int on_device,
+                 void *stream);
 
 /* Algorithm 1 for sets given as DNA: set t's keys are the k-mers of
  * bases[offsets[t] .. offsets[t+1]) (Sec. 5.2: overlapping windows, k = 31).
@@ -285,6 +296,19 @@ int rambo_export_index(const rambo_t *h, uint32_t *host_words, uint64_t n_words)
  * the partition table (K*R values, phi_r(i) at [i*R + r]) to host memory. */
 int rambo_export_registered(const rambo_t *h, uint32_t *host_words, uint64_t n_words);
 int rambo_export_partition(const rambo_t *h, uint16_t *host_phi, uint64_t n);
+
+/* Parameter chooser (Sec. 4 analysis, Sec. 5.1 parameter selection; no GPU
+ * involved).  Given K sets of mean size n_mean keys, a key multiplicity V
+ * (sets per key), a target per-BFU false-positive rate p and a target
+ * failure probability delta (probability of any wrong ID for a query), fills
+ * *B with the query-time optimum sqrt(K V / eta) of Lemma 4.4 (at least 2,
+ * at most RAMBO_MAX_B), *R with the smallest R meeting Lemma 4.2's bound
+ * K (1 - (1-p)(1-1/B)^V)^R <= delta (at most RAMBO_MAX_R; RAMBO_ERANGE if
+ * that is not enough), *m with the power of two at or above the Bloom-filter
+ * size n ln(1/p) / (ln 2)^2 for the expected n = n_mean K / B keys per cell,
+ * and *eta with round(ln 2 * m / n) clamped to [1, RAMBO_MAX_ETA]. */
+int rambo_suggest_params(uint64_t K, double n_mean, double V, double p, double delta, uint32_t *B,
+                         uint32_t *R, uint64_t *m, uint32_t *eta);
 
 /* Folding over (appendix, Sec. 5.2): ORs cell b + B/2 onto cell b of every
  * table, halving B (and the index) while R, m, eta and the hashes stay.  The

@@ -113,23 +113,33 @@ int orc_base_code(uint8_t ch) {
     }
 }
 
+/* k may carry ORC_CANONICAL: each window's key is then the smaller of the
+ * window and its reverse complement (the same DNA read on the other strand:
+ * bases in reverse order, A<->T and C<->G, i.e. code c -> 3 - c). */
+#define ORC_CANONICAL 0x100u
+
+/* Key of the window seq[p .. p+k): forward, or canonical. */
+static uint64_t window_key(const uint8_t *seq, uint64_t p, uint32_t k, int canon) {
+    uint64_t fwd = 0, rc = 0;
+    for (uint32_t t = 0; t < k; ++t) fwd = fwd * 4 + (uint64_t)orc_base_code(seq[p + t]);
+    if (!canon) return fwd;
+    for (uint32_t t = 0; t < k; ++t) rc = rc * 4 + (uint64_t)(3 - orc_base_code(seq[p + k - 1 - t]));
+    return rc < fwd ? rc : fwd;
+}
+
 /* Writes the n-k+1 window keys of seq into out (if out != NULL).  Returns the
  * number of windows (0 when n < k) or ORC_EBADSEQ on a byte outside ACGTacgt,
- * or ORC_EINVAL for k outside [1,32]. */
-int64_t orc_kmers(const uint8_t *seq, uint64_t n, uint32_t k, uint64_t *out) {
-    if (k < 1 || k > 32) return ORC_EINVAL;
+ * or ORC_EINVAL for k outside [1,32] (or unknown flag bits). */
+int64_t orc_kmers(const uint8_t *seq, uint64_t n, uint32_t kflags, uint64_t *out) {
+    const uint32_t k = kflags & 0xffu;
+    const int canon = (kflags & ORC_CANONICAL) != 0;
+    if (k < 1 || k > 32 || (kflags & ~(0xffu | ORC_CANONICAL))) return ORC_EINVAL;
     for (uint64_t p = 0; p < n; ++p)
         if (orc_base_code(seq[p]) < 0) return ORC_EBADSEQ;
     if (n < k) return 0;
     uint64_t nw = n - k + 1;
-    if (out) {
-        for (uint64_t p = 0; p < nw; ++p) {
-            uint64_t v = 0;
-            for (uint32_t t = 0; t < k; ++t)
-                v = v * 4 + (uint64_t)orc_base_code(seq[p + t]);
-            out[p] = v;
-        }
-    }
+    if (out)
+        for (uint64_t p = 0; p < nw; ++p) out[p] = window_key(seq, p, k, canon);
     return (int64_t)nw;
 }
 
@@ -242,7 +252,7 @@ int orc_insert_keys(orc_t *o, uint64_t set_id, const uint64_t *keys, uint64_t n)
 }
 
 /* Insert the k-mers of one sequence into set S_i. */
-int orc_insert_seq(orc_t *o, uint64_t set_id, const uint8_t *seq, uint64_t n, uint32_t k) {
+int orc_insert_seq(orc_t *o, uint64_t set_id, const uint8_t *seq, uint64_t n, uint32_t k /* may carry ORC_CANONICAL */) {
     if (set_id >= o->K) return ORC_ERANGE;
     int64_t nw = orc_kmers(seq, n, k, NULL);
     if (nw < 0) return (int)nw;
@@ -261,13 +271,15 @@ int orc_insert_seq(orc_t *o, uint64_t set_id, const uint8_t *seq, uint64_t n, ui
  * final bits do not depend on the order (Sec. 3.1, "conducive to updates").
  * All inputs are validated before anything is inserted. */
 int orc_insert_seq_batch(orc_t *o, const uint64_t *set_ids, const uint8_t *seq,
-                         const uint64_t *offsets, uint64_t n_sets, uint32_t k,
+                         const uint64_t *offsets, uint64_t n_sets, uint32_t kflags,
                          int nthreads) {
-    if (k < 1 || k > 32) return ORC_EINVAL;
+    const uint32_t k = kflags & 0xffu;
+    const int canon = (kflags & ORC_CANONICAL) != 0;
+    if (k < 1 || k > 32 || (kflags & ~(0xffu | ORC_CANONICAL))) return ORC_EINVAL;
     for (uint64_t t = 0; t < n_sets; ++t) {
         if (set_ids[t] >= o->K) return ORC_ERANGE;
         if (offsets[t + 1] < offsets[t]) return ORC_EINVAL;
-        int64_t nw = orc_kmers(seq + offsets[t], offsets[t + 1] - offsets[t], k, NULL);
+        int64_t nw = orc_kmers(seq + offsets[t], offsets[t + 1] - offsets[t], kflags, NULL);
         if (nw < 0) return (int)nw;
     }
     for (uint64_t t = 0; t < n_sets; ++t) reg_set(o, set_ids[t]);
@@ -291,7 +303,7 @@ int orc_insert_seq_batch(orc_t *o, const uint64_t *set_ids, const uint8_t *seq,
                 uint64_t v = 0;
                 for (uint64_t p = 0; p < n; ++p) {
                     v = ((v << 2) | (uint64_t)orc_base_code(s[p])) & mask;
-                    if (p + 1 >= k) bf_insert(o, d, b, v);
+                    if (p + 1 >= k) bf_insert(o, d, b, canon ? window_key(s, p + 1 - k, k, 1) : v);
                 }
             }
         }
@@ -438,7 +450,7 @@ int orc_query_batch(const orc_t *o, int kind, const void *data, const uint64_t *
                 nt = offsets[q + 1] - offsets[q];
             } else {
                 uint64_t n = offsets[q + 1] - offsets[q];
-                nt = n - k + 1;
+                nt = n - (k & 0xffu) + 1;
                 if (nt > qcap) {
                     free(Q);
                     qcap = nt;

@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(256) k_insert(IndexView ix, HashParams hp, Bat
             if (b.seq) {
                 if (p + b.k > t_end) continue;  // window runs past the end of this set's sequence
                 key = kmer_at(b.packed, p, b.k);
+                if (b.canon) key = canonical_kmer(key, b.k);
             } else {
                 key = __ldg(b.keys + p);
             }

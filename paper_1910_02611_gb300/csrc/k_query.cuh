@@ -144,7 +144,14 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                 const uint64_t idx = order ? (uint64_t)grp * nsteps + s : s * KPS + grp;
                 const bool act = idx < nkeys;
                 uint64_t key = 0;
-                if (act) key = b.seq ? kmer_at(b.packed, a + idx, b.k) : __ldg(b.keys + a + idx);
+                if (act) {
+                    if (b.seq) {
+                        key = kmer_at(b.packed, a + idx, b.k);
+                        if (b.canon) key = canonical_kmer(key, b.k);
+                    } else {
+                        key = __ldg(b.keys + a + idx);
+                    }
+                }
                 const uint64_t y = mix64(key);
                 // A3: issue every row read of this step, then combine
                 uint32_t val[RMAX][ETA][V];

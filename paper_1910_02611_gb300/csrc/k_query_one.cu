@@ -21,7 +21,7 @@ __device__ __forceinline__ int q1_code(unsigned ch) {
 
 __global__ void __launch_bounds__(Q1_THREADS)
     k_query_one(IndexView ix, HashParams hp, int seq, const uint8_t* __restrict__ bases,
-                const uint64_t* __restrict__ keys, uint64_t len, uint32_t k, uint32_t* __restrict__ out_ids,
+                const uint64_t* __restrict__ keys, uint64_t len, uint32_t k, int canon, uint32_t* __restrict__ out_ids,
                 uint32_t* __restrict__ out_count, int* __restrict__ bad) {
     extern __shared__ uint32_t sM[];  // [R][W] masks, then [32] warp counts
     uint32_t* warp_cnt = sM + ix.R * ix.W;
@@ -39,6 +39,14 @@ __global__ void __launch_bounds__(Q1_THREADS)
                     v = 0;
                 }
                 key = key * 4 + (uint64_t)v;
+            }
+            if (canon) {
+                uint64_t rc = 0;  // reverse complement, from the bytes again
+                for (uint32_t c = 0; c < k; ++c) {
+                    int v = q1_code(bases[t + k - 1 - c]);
+                    rc = rc * 4 + (uint64_t)(3 - (v < 0 ? 0 : v));
+                }
+                if (rc < key) key = rc;
             }
         } else {
             key = keys[t];
@@ -81,10 +89,10 @@ __global__ void __launch_bounds__(Q1_THREADS)
 }
 
 cudaError_t launch_query_one(const IndexView& ix, const HashParams& hp, int seq, const uint8_t* bases,
-                             const uint64_t* keys, uint64_t len, uint32_t k, uint32_t* out_ids, uint32_t* out_count,
-                             int* bad, cudaStream_t s) {
+                             const uint64_t* keys, uint64_t len, uint32_t k, int canon, uint32_t* out_ids,
+                             uint32_t* out_count, int* bad, cudaStream_t s) {
     const size_t smem = (size_t)(ix.R * ix.W + 32) * 4;
-    k_query_one<<<1, Q1_THREADS, smem, s>>>(ix, hp, seq, bases, keys, len, k, out_ids, out_count, bad);
+    k_query_one<<<1, Q1_THREADS, smem, s>>>(ix, hp, seq, bases, keys, len, k, canon, out_ids, out_count, bad);
     return cudaGetLastError();
 }
 

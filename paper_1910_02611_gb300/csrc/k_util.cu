@@ -339,7 +339,8 @@ __global__ void k_minimizer(BatchView b, uint64_t* __restrict__ keys, uint32_t* 
         const uint64_t nkeys = b.seq ? (e - a - b.k + 1) : (e - a);
         uint64_t mn = ~0ull;
         for (uint64_t t = lane; t < nkeys; t += 32) {
-            const uint64_t key = b.seq ? kmer_at(b.packed, a + t, b.k) : __ldg(b.keys + a + t);
+            uint64_t key = b.seq ? kmer_at(b.packed, a + t, b.k) : __ldg(b.keys + a + t);
+            if (b.seq && b.canon) key = canonical_kmer(key, b.k);
             const uint64_t h = mix64(key ^ 0x5851F42D4C957F2Dull);
             mn = h < mn ? h : mn;
         }

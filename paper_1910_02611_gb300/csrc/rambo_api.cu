@@ -2,6 +2,7 @@
 // life cycle, parameter derivation, input staging, kernel sequencing, status
 // decoding and result hand-out.  Every step of insertion and query runs in the
 // kernels of this library; the host only moves buffers and orders launches.
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -302,12 +303,15 @@ int pack_bases(rambo* h, BatchView& b, const void* d_bases, cudaStream_t s) {
 int run_insert(rambo* h, int seq, const uint64_t* set_ids, const void* data, const uint64_t* offsets,
                uint64_t n, uint32_t k, int on_device, cudaStream_t s) {
     if (!h || !offsets || !set_ids || (!data && n)) return RAMBO_EINVAL;
-    if (seq && (k < 1 || k > 32)) return RAMBO_EINVAL;
+    uint32_t kk = 0;
+    int canon = 0;
+    if (seq && !split_k(k, &kk, &canon)) return RAMBO_EINVAL;
     if (n == 0) return RAMBO_OK;
     CK(cudaSetDevice(h->device));
     BatchView b{};
     b.seq = seq;
-    b.k = k;
+    b.k = kk;
+    b.canon = canon;
     const void* d_data = nullptr;
     RK(stage_batch(h, data, seq ? 1 : 8, offsets, set_ids, n, on_device, s, b, &d_data));
     CK(launch_status_reset(h->st, s));
@@ -378,7 +382,10 @@ int resolve_tuning(rambo* h, uint64_t n, int& use_bitmap, QueryTuning& t) {
 int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint64_t n, uint32_t k,
               int on_device, cudaStream_t s, QueryDest& d) {
     if (!h || !offsets || (!data && n)) return RAMBO_EINVAL;
-    if (seq && (k < 1 || k > 32)) return RAMBO_EINVAL;
+    uint32_t kk = 0;
+    int canon = 0;
+    if (seq && !split_k(k, &kk, &canon)) return RAMBO_EINVAL;
+    k = kk;
     CK(cudaSetDevice(h->device));
     h->last = rambo_query_stats_t{};
     h->launches = 0;
@@ -408,6 +415,7 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
     BatchView b{};
     b.seq = seq;
     b.k = k;
+    b.canon = canon;
     const void* d_data = nullptr;
     RK(stage_batch(h, data, seq ? 1 : 8, offsets, nullptr, n, on_device, s, b, &d_data));
     int use_bitmap = 0;
@@ -629,6 +637,64 @@ int rambo_insert_batch(rambo_t* h, const uint64_t* set_ids, const uint64_t* keys
     return run_insert(h, 0, set_ids, keys, offsets, n_sets, 0, on_device, (cudaStream_t)stream);
 }
 
+int rambo_insert(rambo_t* h, uint64_t set_id, const uint64_t* keys, uint64_t n, int on_device, void* stream) {
+    if (!h) return RAMBO_EINVAL;
+    if (!on_device) {
+        const uint64_t off[2] = {0, n};
+        return run_insert(h, 0, &set_id, keys, off, 1, 0, 0, (cudaStream_t)stream);
+    }
+    // device keys: the set ID and offsets travel from the host, the keys stay on the device
+    const uint64_t off[2] = {0, n};
+    uint64_t* d = nullptr;
+    CK(cudaSetDevice(h->device));
+    if (cudaMalloc(&d, 3 * sizeof(uint64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return RAMBO_ENOMEM;
+    }
+    const uint64_t host3[3] = {set_id, off[0], off[1]};
+    cudaError_t e = cudaMemcpy(d, host3, sizeof(host3), cudaMemcpyHostToDevice);
+    int rc = e == cudaSuccess ? run_insert(h, 0, d, keys, d + 1, 1, 0, 1, (cudaStream_t)stream) : map_cuda(e);
+    cudaFree(d);
+    return rc;
+}
+
+int rambo_suggest_params(uint64_t K, double n_mean, double V, double p, double delta, uint32_t* B, uint32_t* R,
+                         uint64_t* m, uint32_t* eta) {
+    if (!K || !(n_mean > 0) || !(V >= 1) || !(p > 0 && p < 1) || !(delta > 0 && delta < 1) || !B || !R || !m || !eta)
+        return RAMBO_EINVAL;
+    const double ln2 = 0.6931471805599453;
+    // Lemma 4.4: E[q_t] = B R eta + (K/B)(V + Bp) R is smallest at B* = sqrt(K V / eta);
+    // eta is not known yet, so take the optimal eta of a Bloom filter at rate p first
+    double eta0 = std::log(1.0 / p) / ln2;
+    if (eta0 < 1) eta0 = 1;
+    if (eta0 > RAMBO_MAX_ETA) eta0 = RAMBO_MAX_ETA;
+    double b = std::sqrt((double)K * V / eta0);
+    uint32_t Bv = (uint32_t)std::llround(b);
+    if (Bv < 2) Bv = 2;
+    if (Bv > RAMBO_MAX_B) Bv = RAMBO_MAX_B;
+    // Lemma 4.2: delta <= K (1 - (1-p)(1-1/B)^V)^R
+    const double f = 1.0 - (1.0 - p) * std::pow(1.0 - 1.0 / Bv, V);
+    uint32_t Rv = 0;
+    for (uint32_t r = 1; r <= RAMBO_MAX_R; ++r)
+        if ((double)K * std::pow(f, (double)r) <= delta) {
+            Rv = r;
+            break;
+        }
+    *B = Bv;
+    // Bloom-filter size for n keys per cell at rate p: n ln(1/p) / (ln 2)^2
+    const double n = n_mean * (double)K / Bv;
+    const double mm = n * std::log(1.0 / p) / (ln2 * ln2);
+    uint64_t mv = 2;
+    while ((double)mv < mm && mv < (1ull << 32)) mv <<= 1;
+    *m = mv;
+    long e = std::lround(ln2 * (double)mv / n);
+    if (e < 1) e = 1;
+    if (e > RAMBO_MAX_ETA) e = RAMBO_MAX_ETA;
+    *eta = (uint32_t)e;
+    *R = Rv ? Rv : RAMBO_MAX_R;
+    return Rv ? RAMBO_OK : RAMBO_ERANGE;
+}
+
 int rambo_insert_seq_batch(rambo_t* h, const uint64_t* set_ids, const uint8_t* bases, const uint64_t* offsets,
                            uint64_t n_sets, uint32_t k, int on_device, void* stream) {
     return run_insert(h, 1, set_ids, bases, offsets, n_sets, k, on_device, (cudaStream_t)stream);
@@ -758,7 +824,10 @@ int rambo_list_query_configs(const rambo_t* h, rambo_query_config_t* out, int ca
 int rambo_query_one_per_launch(rambo_t* h, int kind, const void* data, const uint64_t* host_offsets,
                                uint64_t n_queries, uint32_t k, uint32_t* ids, uint32_t* counts, void* stream) {
     if (!h || !host_offsets || (!data && n_queries) || (n_queries && (!ids || !counts))) return RAMBO_EINVAL;
-    if (kind == 1 && (k < 1 || k > 32)) return RAMBO_EINVAL;
+    uint32_t kk = 0;
+    int canon = 0;
+    if (kind == 1 && !split_k(k, &kk, &canon)) return RAMBO_EINVAL;
+    k = kk;
     if (kind != 0 && kind != 1) return RAMBO_EINVAL;
     CK(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
@@ -775,7 +844,7 @@ int rambo_query_one_per_launch(rambo_t* h, int kind, const void* data, const uin
         const uint64_t a = host_offsets[q], len = host_offsets[q + 1] - a;
         const uint8_t* bp = kind == 1 ? static_cast<const uint8_t*>(data) + a : nullptr;
         const uint64_t* kp = kind == 0 ? static_cast<const uint64_t*>(data) + a : nullptr;
-        CK(launch_query_one(ix, h->hp, kind, bp, kp, len, k, ids + q * h->K, counts + q, d_bad, s));
+        CK(launch_query_one(ix, h->hp, kind, bp, kp, len, k, canon, ids + q * h->K, counts + q, d_bad, s));
     }
     int bad = 0;
     CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));

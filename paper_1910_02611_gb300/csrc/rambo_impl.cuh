@@ -133,6 +133,26 @@ __device__ __forceinline__ uint4 ld_row4(const uint32_t* p, int kind) {
     }
 }
 
+// Reverse complement of a k-mer key (complement of code c is 3 - c): NOT,
+// reverse the 2-bit groups of the word, keep the top 2k bits.
+__device__ __forceinline__ uint64_t revcomp_kmer(uint64_t fwd, uint32_t k) {
+    uint64_t x = __brevll(~fwd);  // reverses bits, so each 2-bit group comes out bit-swapped
+    x = ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
+    return x >> (64 - 2 * k);
+}
+
+__device__ __forceinline__ uint64_t canonical_kmer(uint64_t fwd, uint32_t k) {
+    const uint64_t rc = revcomp_kmer(fwd, k);
+    return rc < fwd ? rc : fwd;
+}
+
+// k and the canonical flag from a k-mer length argument; false when invalid
+__host__ __device__ inline bool split_k(uint32_t kflags, uint32_t* k, int* canon) {
+    *k = kflags & 0xffu;
+    *canon = (kflags & RAMBO_KMER_CANONICAL) ? 1 : 0;
+    return *k >= 1 && *k <= 32 && !(kflags & ~(0xffu | RAMBO_KMER_CANONICAL));
+}
+
 __device__ __forceinline__ void record_error(DevStatus* st, uint64_t index, unsigned prio) {
     atomicMin(&st->err, (unsigned long long)((index << 8) | prio));
 }
@@ -164,6 +184,7 @@ struct BatchView {
     uint64_t total;                // offsets[n] - offsets[0]
     uint64_t n;                    // items
     uint32_t k;
+    int canon;                     // keys are canonical k-mers (min of both strands)
     const uint64_t* set_ids;       // insert batches only
     const uint32_t* perm;          // queries only: processing order (NULL = 0..n-1)
     const uint64_t* desc;          // device descriptor {n, total} (offsets[0] = 0) read at
@@ -243,8 +264,8 @@ cudaError_t launch_query(const IndexView& ix, const HashParams& hp, const BatchV
 
 // k_query_one.cu: the plain one-query-per-launch kernel
 cudaError_t launch_query_one(const IndexView& ix, const HashParams& hp, int seq, const uint8_t* bases,
-                             const uint64_t* keys, uint64_t len, uint32_t k, uint32_t* out_ids, uint32_t* out_count,
-                             int* bad, cudaStream_t s);
+                             const uint64_t* keys, uint64_t len, uint32_t k, int canon, uint32_t* out_ids,
+                             uint32_t* out_count, int* bad, cudaStream_t s);
 
 // rambo_api.cu: what the fixed-scratch entry point needs from a handle
 int handle_query_view(rambo_t* h, uint64_t n, IndexView* ix, HashParams* hp, QueryTuning* t, int* use_bitmap,

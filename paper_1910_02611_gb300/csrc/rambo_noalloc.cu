@@ -94,7 +94,10 @@ extern "C" int rambo_query_seq_batch_noalloc(rambo_t* h, const uint8_t* bases, c
                                              uint64_t n_queries, uint32_t k, uint32_t* ids, uint64_t ids_cap,
                                              uint64_t* id_offsets, uint64_t* needed, void* stream) {
     if (!h || !offsets || !id_offsets || (!bases && n_queries) || (!ids && ids_cap)) return RAMBO_EINVAL;
-    if (k < 1 || k > 32) return RAMBO_EINVAL;
+    uint32_t kk = 0;
+    int canon = 0;
+    if (!split_k(k, &kk, &canon)) return RAMBO_EINVAL;
+    k = kk;
     if (n_queries > NA_MAX_QUERIES) return RAMBO_E2BIG;
     const uint64_t n = n_queries;
     cudaStream_t s = (cudaStream_t)stream;
@@ -136,6 +139,7 @@ extern "C" int rambo_query_seq_batch_noalloc(rambo_t* h, const uint8_t* bases, c
     b.total = total;
     b.n = n;
     b.k = k;
+    b.canon = canon;
     b.set_ids = nullptr;
     b.perm = nullptr;
     NA_CK(launch_status_reset(st, s));  // clears error word, ticket, cursor, counters

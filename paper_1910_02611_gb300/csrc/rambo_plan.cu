@@ -43,6 +43,7 @@ struct rambo_plan {
     rambo_t* h = nullptr;
     int kind = 1;
     uint32_t k = 31;
+    int canon = 0;
     uint64_t max_q = 0, max_items = 0, max_ids = 0;
     int device = 0;
     size_t elem = 1;
@@ -110,6 +111,7 @@ int plan_capture(rambo_plan* p) {
     b.total = p->max_items;
     b.off0 = 0;
     b.k = p->k;
+    b.canon = p->canon;
     b.desc = p->d_desc;
     const uint64_t scan_words = scan_tmp_words(p->max_q);
     cudaStream_t s = p->cap;
@@ -165,7 +167,9 @@ extern "C" {
 int rambo_plan_create(rambo_t* h, int kind, uint64_t max_queries, uint64_t max_items, uint64_t max_ids, uint32_t k,
                       rambo_plan_t** out) {
     if (!h || !out || (kind != 0 && kind != 1) || !max_queries || !max_items || !max_ids) return RAMBO_EINVAL;
-    if (kind == 1 && (k < 1 || k > 32)) return RAMBO_EINVAL;
+    uint32_t kk = 0;
+    int canon = 0;
+    if (kind == 1 && !split_k(k, &kk, &canon)) return RAMBO_EINVAL;
     if (max_queries > 0xffffffffull) return RAMBO_EINVAL;
     *out = nullptr;
     rambo_plan* p = new (std::nothrow) rambo_plan();
@@ -181,7 +185,8 @@ int rambo_plan_create(rambo_t* h, int kind, uint64_t max_queries, uint64_t max_i
     }
     p->h = h;
     p->kind = kind;
-    p->k = kind == 1 ? k : 0;
+    p->k = kind == 1 ? kk : 0;
+    p->canon = kind == 1 ? canon : 0;
     p->max_q = max_queries;
     p->max_items = max_items;
     p->max_ids = max_ids;

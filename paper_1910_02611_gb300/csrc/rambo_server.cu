@@ -85,7 +85,8 @@ namespace {
 
 uint64_t op_keys(const Op& op) {
     if (op.kind == 0) return op.items;
-    return op.items >= op.k ? op.items - op.k + 1 : 0;
+    const uint32_t k = op.k & 0xffu;
+    return op.items >= k ? op.items - k + 1 : 0;
 }
 
 void finish_slot(rambo_server* S, Slot& sl) {
@@ -253,8 +254,13 @@ extern "C" {
 
 int rambo_server_create(rambo_t* h, const rambo_server_config_t* cfg, rambo_server_t** out) {
     if (!h || !cfg || !out || cfg->slots < 1 || cfg->slots > 16 || !cfg->max_batch_queries || !cfg->max_batch_ids ||
-        (!cfg->max_batch_bases && !cfg->max_batch_keys) || cfg->k < 1 || cfg->k > 32)
+        (!cfg->max_batch_bases && !cfg->max_batch_keys))
         return RAMBO_EINVAL;
+    {
+        uint32_t kk = 0;
+        int canon = 0;
+        if (!rgb::split_k(cfg->k, &kk, &canon)) return RAMBO_EINVAL;
+    }
     *out = nullptr;
     rambo_server* S = new (std::nothrow) rambo_server();
     if (!S) return RAMBO_ENOMEM;

@@ -55,6 +55,9 @@ SIGNATURES = {
     "rambo_destroy": (None, [_p]),
     "rambo_get_info": (_i32, [_p, C.POINTER(RamboInfo)]),
     "rambo_insert_batch": (_i32, [_p, _p, _p, _p, _u64, _i32, _p]),
+    "rambo_insert": (_i32, [_p, _u64, _p, _u64, _i32, _p]),
+    "rambo_suggest_params": (_i32, [_u64, C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(_u32),
+                                    C.POINTER(_u32), C.POINTER(_u64), C.POINTER(_u32)]),
     "rambo_insert_seq_batch": (_i32, [_p, _p, _p, _p, _u64, _u32, _i32, _p]),
     "rambo_query_batch": (_i32, [_p, _p, _p, _u64, _i32, C.POINTER(_p), C.POINTER(_p), _p]),
     "rambo_query_seq_batch": (_i32, [_p, _p, _p, _u64, _u32, _i32, C.POINTER(_p), C.POINTER(_p), _p]),
@@ -267,6 +270,16 @@ class Rambo:
             rc = L.rambo_insert_seq_batch(self._h, ids_p, data_p, off_p, n, k, int(dev), s)
         del keep
         self._check(rc, "insert")
+
+    def insert_set(self, set_id: int, keys, stream=None) -> None:
+        """Algorithm 1 for one set of keys (rambo_insert)."""
+        dev = _is_cuda_tensor(keys)
+        if dev:
+            rc = load_library().rambo_insert(self._h, set_id, keys.data_ptr(), keys.numel(), 1, _stream_handle(stream))
+        else:
+            k = _host_arr(keys, np.uint64)
+            rc = load_library().rambo_insert(self._h, set_id, k.ctypes.data, k.size, 0, _stream_handle(stream))
+        self._check(rc, "insert_set")
 
     # -- Algorithm 2 ----------------------------------------------------------------
     def query(self, data, offsets, kind: str = "keys", k: int = 31, stream=None, copy: bool = True):
@@ -513,7 +526,9 @@ class Plan:
             raise RamboError(rc, "rambo_plan_poll")
         return rc == 0
 
-    def wait(self, to_host: bool = True, stream=None):
+    def wait(self, to_host: bool = True, stream=None, copy: bool = True):
+        """Results of the launched batch.  copy=False with to_host=False returns
+        (ids device pointer, offsets device pointer, number of IDs) only."""
         ids_p, off_p, n_ids = _p(), _p(), _u64(0)
         rc = load_library().rambo_plan_wait(self._p, int(to_host), C.byref(ids_p), C.byref(off_p), C.byref(n_ids),
                                             _stream_handle(stream))
@@ -521,6 +536,8 @@ class Plan:
             raise RamboError(rc, "rambo_plan_wait", int(n_ids.value) if rc == ENOSPC else None)
         n = self._n
         total = int(n_ids.value)
+        if not copy and not to_host:
+            return ids_p.value, off_p.value, total
         if to_host:
             offs = np.ctypeslib.as_array(C.cast(off_p, C.POINTER(_u64)), shape=(n + 1,)).copy()
             ids = (np.ctypeslib.as_array(C.cast(ids_p, C.POINTER(_u32)), shape=(total,)).copy() if total
@@ -615,6 +632,20 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def suggest_params(K: int, n_mean: float, V: float = 1.0, p: float = 0.01, delta: float = 0.01) -> dict:
+    """Parameter chooser (Lemma 4.4 for B, Lemma 4.2 for R, Bloom-filter sizing
+    for m and eta); host-only.  Raises RamboError(ERANGE) if R <= RAMBO_MAX_R
+    cannot reach delta (the dict is still attached as .params)."""
+    B, R, m, eta = _u32(), _u32(), _u64(), _u32()
+    rc = load_library().rambo_suggest_params(K, n_mean, V, p, delta, C.byref(B), C.byref(R), C.byref(m), C.byref(eta))
+    out = dict(B=B.value, R=R.value, m=m.value, eta=eta.value)
+    if rc:
+        err = RamboError(rc, "suggest_params")
+        err.params = out
+        raise err
+    return out
 
 
 def l2_fetch_granularity(bytes_: int = 0) -> int:

@@ -162,3 +162,30 @@ def test_kmer_sliding_invariant(oracle_mod):
             assert ks[p + 1] == (ks[p] * 4 + code[seq[p + k]]) % mod
         # the first window read as a base-4 numeral, most significant first
         assert ks[0] == int("".join(str(code[c]) for c in seq[:k]), 4)
+
+
+CANON = 0x100
+
+
+def _revcomp(seq: bytes) -> bytes:
+    return bytes(seq[::-1]).translate(bytes.maketrans(b"ACGTacgt", b"TGCAtgca"))
+
+
+def test_canonical_kmers_are_strand_independent(oracle_mod):
+    # canonical key = min(window, reverse complement): a sequence and its
+    # reverse complement give the same keys, in reverse order
+    rng = np.random.default_rng(9)
+    seq = bytes(np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, 400)])
+    for k in (1, 2, 15, 31, 32):
+        a = [int(v) for v in oracle_mod.kmers(seq, k | CANON)]
+        b = [int(v) for v in oracle_mod.kmers(_revcomp(seq), k | CANON)]
+        assert a == b[::-1]
+        fwd = [int(v) for v in oracle_mod.kmers(seq, k)]
+        rc = [int(v) for v in oracle_mod.kmers(_revcomp(seq), k)][::-1]
+        assert a == [min(x, y) for x, y in zip(fwd, rc)]
+    # closed forms (A=0 C=1 G=2 T=3): ACG -> min(ACG=6, CGT=27); TTT -> AAA = 0
+    assert list(oracle_mod.kmers(b"ACG", 3 | CANON)) == [6]
+    assert list(oracle_mod.kmers(b"TTT", 3 | CANON)) == [0]
+    assert list(oracle_mod.kmers(b"GGG", 3 | CANON)) == [int("111", 4)]  # CCC
+    with pytest.raises(ValueError):
+        oracle_mod.kmers(b"ACGT", 3 | 0x200)

@@ -336,6 +336,9 @@ typedef struct rambo_query_stats {
     uint64_t kernel_launches;  /* kernels this library launched for the call */
     float query_kernel_ms;
     float device_ms;
+    uint64_t stage_queries[4];  /* queries that reached the set stage, by stage used:
+                                 * [0] staged dense (large ID space), [1] dense,
+                                 * [2] sparse, [3] union */
 } rambo_query_stats_t;
 
 int rambo_last_query_stats(const rambo_t *h, rambo_query_stats_t *out);

@@ -262,6 +262,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                     }
                     stage = (dense <= sparse && dense <= uni) ? 1 : (sparse <= uni ? 2 : 3);
                 }
+                if (lane == 0) atomicAdd(&st->stage_count[use_bitmap ? stage : 0], 1ull);
                 if (use_bitmap) {
                     if (stage == 1) {
                         // dense: one ballot per 32 IDs becomes one bitmap word; four

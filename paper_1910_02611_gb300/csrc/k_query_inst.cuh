@@ -6,7 +6,7 @@
 
 // (words per lane V, lanes per key G) pairs the dispatcher knows
 #define QK_VG_LIST(X) \
-    X(1, 1) X(2, 1) X(1, 2) X(4, 1) X(2, 2) X(4, 2) X(2, 4) X(4, 4) X(2, 8) X(4, 8) X(4, 16) X(4, 32)
+    X(1, 1) X(2, 1) X(1, 2) X(4, 1) X(2, 2) X(4, 2) X(2, 4) X(4, 4) X(2, 8) X(1, 16) X(4, 8) X(4, 16) X(4, 32)
 
 #define QK_CAT2(a, b) a##b
 #define QK_CAT(a, b) QK_CAT2(a, b)

@@ -23,6 +23,7 @@ __global__ void k_status_reset(DevStatus* st) {
     st->keys_probed = 0;
     st->rows_read = 0;
     st->spare[0] = st->spare[1] = 0;
+    st->stage_count[0] = st->stage_count[1] = st->stage_count[2] = st->stage_count[3] = 0;
 }
 
 cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s) {

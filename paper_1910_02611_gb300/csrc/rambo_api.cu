@@ -482,6 +482,7 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
     h->last.keys_probed = h->h_st->keys_probed;
     h->last.rows_read = h->h_st->rows_read;
     h->last.n_results = total_ids;
+    for (int i = 0; i < 4; ++i) h->last.stage_queries[i] = h->h_st->stage_count[i];
     CK(cudaEventElapsedTime(&h->last.query_kernel_ms, h->ev[1], h->ev[2]));
     if (d.needed) *d.needed = total_ids;
     if (!d.arena && total_ids > d.ids_cap) return RAMBO_ENOSPC;
@@ -797,8 +798,8 @@ int rambo_set_query_config(rambo_t* h, const rambo_query_config_t* cfg) {
 
 int rambo_list_query_configs(const rambo_t* h, rambo_query_config_t* out, int cap) {
     if (!h) return RAMBO_EINVAL;
-    static const int vg[][2] = {{1, 1}, {2, 1}, {1, 2}, {4, 1}, {2, 2}, {4, 2},
-                                {2, 4}, {4, 4}, {2, 8}, {4, 8}, {4, 16}, {4, 32}};
+    static const int vg[][2] = {{1, 1}, {2, 1}, {1, 2}, {4, 1}, {2, 2}, {4, 2}, {2, 4},
+                                {4, 4}, {2, 8}, {1, 16}, {4, 8}, {4, 16}, {4, 32}};
     static const int wpb[] = {2, 4, 8};
     int n = 0;
     for (auto& p : vg) {

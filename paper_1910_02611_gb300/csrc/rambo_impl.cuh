@@ -33,6 +33,7 @@ struct DevStatus {
     unsigned long long keys_probed;  // keys whose rows were read
     unsigned long long rows_read;    // row reads issued
     unsigned long long spare[2];
+    unsigned long long stage_count[4];   // surviving queries per set stage (1 dense, 2 sparse, 3 union)
 };
 
 // Position multipliers s_{r,j}, passed by value so every warp reads them from

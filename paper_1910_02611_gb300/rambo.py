@@ -27,7 +27,7 @@ class RamboInfo(C.Structure):
 class QueryStats(C.Structure):
     _fields_ = [("n_queries", _u64), ("keys_submitted", _u64), ("keys_probed", _u64), ("rows_read", _u64),
                 ("n_results", _u64), ("kernel_launches", _u64), ("query_kernel_ms", C.c_float),
-                ("device_ms", C.c_float)]
+                ("device_ms", C.c_float), ("stage_queries", _u64 * 4)]
 
 
 class ServerConfig(C.Structure):
@@ -397,7 +397,11 @@ class Rambo:
     def last_query_stats(self) -> dict:
         st = QueryStats()
         self._check(load_library().rambo_last_query_stats(self._h, C.byref(st)), "last_query_stats")
-        return {f: (float(getattr(st, f)) if f.endswith("_ms") else int(getattr(st, f))) for f, _ in st._fields_}
+        out = {}
+        for f, _ in st._fields_:
+            v = getattr(st, f)
+            out[f] = float(v) if f.endswith("_ms") else (list(v) if f == "stage_queries" else int(v))
+        return out
 
     # -- configuration ------------------------------------------------------------
     def get_config(self) -> dict:

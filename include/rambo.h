@@ -87,6 +87,9 @@ typedef struct rambo_info {
     uint32_t row_stride;   /* S >= W: words between consecutive rows in memory */
     uint64_t index_bytes;  /* R * m * S * 4 */
     uint64_t n_registered; /* sets inserted so far (ID registered) */
+    uint32_t nodes;        /* two-level hash: nodes (1 = plain partition) */
+    uint32_t cells_per_node;
+    uint64_t tau_seed;
 } rambo_info_t;
 
 /* Creates an empty index (Sec. 3: R tables x B cells of m-bit Bloom filters,
@@ -98,6 +101,23 @@ typedef struct rambo_info {
  * released with rambo_destroy). */
 int rambo_create(uint64_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta,
                  uint64_t seed, rambo_t **out);
+
+/* The two-level hash of the paper's node-parallel construction (Sec. 5.2,
+ * appendix): n_nodes node-local structures of cells_per_node cells stacked
+ * into one of B = cells_per_node * n_nodes cells.  A set i is routed to node
+ * tau(i) = ((a_tau i + c_tau) mod P) mod n_nodes (a_tau, c_tau drawn from
+ * SplitMix64 at tau_seed as a_r, c_r are from seed) and lives in cell
+ * cells_per_node * tau(i) + phi_r(i) of table r, phi_r having range
+ * cells_per_node.  Handles created with the same arguments on different GPUs
+ * or at different times, each inserting only the sets routed to "its" node,
+ * OR together (rambo_merge) into exactly the index built at once. */
+int rambo_create_stacked(uint64_t K, uint32_t cells_per_node, uint32_t n_nodes, uint32_t R, uint64_t m,
+                         uint32_t eta, uint64_t seed, uint64_t tau_seed, rambo_t **out);
+/* tau(set_id) of a stacked handle (0 for a plain one). */
+uint32_t rambo_node_of(const rambo_t *h, uint64_t set_id);
+/* ORs src's rows and registered sets into dst (identical parameters and
+ * device required; RAMBO_EINVAL otherwise). */
+int rambo_merge(rambo_t *dst, const rambo_t *src, void *stream);
 
 /* Releases all device and host memory of the handle (NULL is ignored). */
 void rambo_destroy(rambo_t *h);
@@ -314,7 +334,8 @@ int rambo_suggest_params(uint64_t K, double n_mean, double V, double p, double d
  * table, halving B (and the index) while R, m, eta and the hashes stay.  The
  * result is exactly the index that rambo_create with B/2 and the same seed
  * would have built from the same inserts, because the partition hash mod B
- * then mod B/2 equals the hash mod B/2.  Resets the query configuration.
+ * then mod B/2 equals the hash mod B/2 (for a stacked handle every set's
+ * cell becomes its cell mod B/2).  Resets the query configuration.
  * Errors: RAMBO_EINVAL when B is odd or 1, RAMBO_ENOMEM. */
 int rambo_fold(rambo_t *h, void *stream);
 

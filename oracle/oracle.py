@@ -83,6 +83,14 @@ def lib():
         L.orc_get_row.argtypes = [p, u32, u64, p]
         L.orc_cell_popcount.argtypes = [p, p]
         L.orc_export_reg.argtypes = [p, p]
+        L.orc_create_stacked.restype = p
+        L.orc_create_stacked.argtypes = [u64, u32, u32, u32, u64, u32, u64, u64]
+        L.orc_node.restype = u32
+        L.orc_node.argtypes = [p, u64]
+        L.orc_fold.restype = C.c_int
+        L.orc_fold.argtypes = [p]
+        L.orc_merge.restype = C.c_int
+        L.orc_merge.argtypes = [p, p]
         _lib = L
     return _lib
 
@@ -124,12 +132,32 @@ class OracleError(RuntimeError):
 class Oracle:
     """A plain RAMBO: B*R separate m-bit Bloom filters (Secs. 2-3)."""
 
-    def __init__(self, K: int, B: int, R: int, m: int, eta: int, seed: int):
-        self.K, self.B, self.R, self.m, self.eta, self.seed = K, B, R, m, eta, seed
-        h = lib().orc_create(K, B, R, m, eta, seed)
+    def __init__(self, K: int, B: int, R: int, m: int, eta: int, seed: int, *, nodes: int = 1, tau_seed: int = 0):
+        """nodes > 1: the two-level hash of Sec. 5.2 with B cells per node
+        (B * nodes cells in the stacked structure)."""
+        self.K, self.R, self.m, self.eta, self.seed = K, R, m, eta, seed
+        self.B = B * nodes
+        if nodes > 1:
+            h = lib().orc_create_stacked(K, B, nodes, R, m, eta, seed, tau_seed)
+        else:
+            h = lib().orc_create(K, B, R, m, eta, seed)
         if not h:
             raise OracleError(EINVAL, "orc_create rejected parameters")
         self._h = C.c_void_p(h)
+
+    def node(self, set_id: int) -> int:
+        return int(lib().orc_node(self._h, set_id))
+
+    def fold(self) -> None:
+        rc = lib().orc_fold(self._h)
+        if rc:
+            raise OracleError(rc, "fold")
+        self.B //= 2
+
+    def merge(self, other: "Oracle") -> None:
+        rc = lib().orc_merge(self._h, other._h)
+        if rc:
+            raise OracleError(rc, "merge")
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -72,6 +72,9 @@ typedef struct orc {
     uint64_t m;          /* bits per Bloom filter, 2^L */
     uint64_t seed;
     uint64_t *a, *c;     /* phi parameters, R each */
+    uint32_t B_local;    /* cells per node (two-level hash); B_local = B with one node */
+    uint32_t n_nodes;    /* nodes of the two-level hash (1 = plain partition) */
+    uint64_t a_tau, c_tau; /* node hash tau(i) = ((a_tau i + c_tau) mod P) mod n_nodes */
     uint64_t *s;         /* position multipliers, R*eta */
     uint64_t wpb;        /* 64-bit words per Bloom filter */
     uint64_t *bits;      /* BF of (table r, cell b) at bits + (r*B + b)*wpb */
@@ -93,9 +96,19 @@ uint64_t orc_splitmix64_next(uint64_t *state) {
     return orc_mix64(*state);
 }
 
+/* Cell of set i in table r.  Plain: phi_r(i) = ((a_r i + c_r) mod P) mod B.
+ * Two-level (Sec. 5.2, appendix): B_local * tau(i) + phi_r(i) with phi_r over
+ * B_local cells and tau over the nodes.  After folding over (B halved f
+ * times) the cell is the original cell mod the current B. */
 uint32_t orc_phi(const orc_t *o, uint32_t r, uint64_t set_id) {
     unsigned __int128 v = (unsigned __int128)o->a[r] * set_id + o->c[r];
-    return (uint32_t)((uint64_t)(v % ORC_P) % o->B);
+    uint64_t local = (uint64_t)(v % ORC_P) % o->B_local;
+    uint64_t node = 0;
+    if (o->n_nodes > 1) {
+        unsigned __int128 t = (unsigned __int128)o->a_tau * set_id + o->c_tau;
+        node = (uint64_t)(t % ORC_P) % o->n_nodes;
+    }
+    return (uint32_t)((o->B_local * node + local) % o->B);
 }
 
 uint64_t orc_pos(const orc_t *o, uint32_t r, uint32_t j, uint64_t key) {
@@ -155,14 +168,24 @@ void orc_destroy(orc_t *o) {
 /* Parameters as in the specification above.  Returns NULL on bad parameters
  * (B=0, R=0, eta=0, K=0, K > 2^32, m not a power of two in [2, 2^32]) or when
  * memory runs out. */
-orc_t *orc_create(uint64_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta,
-                  uint64_t seed) {
-    if (K == 0 || K > (1ULL << 32) || B == 0 || B > 65535 || R == 0 || R > 64 ||
+static int build_members(orc_t *o);
+
+static orc_t *create_impl(uint64_t K, uint32_t B_local, uint32_t n_nodes, uint32_t R, uint64_t m,
+                          uint32_t eta, uint64_t seed, uint64_t tau_seed) {
+    uint64_t Bfull = (uint64_t)B_local * n_nodes;
+    if (K == 0 || K > (1ULL << 32) || B_local == 0 || n_nodes == 0 || Bfull > 65535 || R == 0 || R > 64 ||
         eta == 0 || eta > 64 || m < 2 || m > (1ULL << 32) || (m & (m - 1)))
         return NULL;
+    uint32_t B = (uint32_t)Bfull;
     orc_t *o = (orc_t *)calloc(1, sizeof(orc_t));
     if (!o) return NULL;
     o->K = K; o->B = B; o->R = R; o->eta = eta; o->m = m; o->seed = seed;
+    o->B_local = B_local; o->n_nodes = n_nodes;
+    if (n_nodes > 1) {
+        uint64_t ts = tau_seed;
+        o->a_tau = 1 + orc_splitmix64_next(&ts) % (ORC_P - 1);
+        o->c_tau = orc_splitmix64_next(&ts) % ORC_P;
+    }
     uint32_t L = 0;
     while ((1ULL << L) < m) ++L;
     o->L = L;
@@ -186,20 +209,47 @@ orc_t *orc_create(uint64_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta,
     for (uint32_t r = 0; r < R; ++r)
         for (uint32_t j = 0; j < eta; ++j)
             o->s[(uint64_t)r * eta + j] = orc_splitmix64_next(&st) | 1ULL;
-    /* SetIDs(M[b,r]) over the whole ID range, ascending: counting sort by cell. */
+    if (build_members(o)) { orc_destroy(o); return NULL; }
+    return o;
+}
+
+/* SetIDs(M[b,r]) over the whole ID range, ascending: counting sort by cell. */
+static int build_members(orc_t *o) {
+    const uint32_t R = o->R, B = o->B;
+    const uint64_t K = o->K;
+    memset(o->mem_off, 0, sizeof(uint64_t) * ((size_t)R * B + 1));
     for (uint32_t r = 0; r < R; ++r)
         for (uint64_t i = 0; i < K; ++i)
             o->mem_off[(uint64_t)r * B + orc_phi(o, r, i) + 1] += 1;
     for (uint64_t t = 0; t < (uint64_t)R * B; ++t) o->mem_off[t + 1] += o->mem_off[t];
     uint64_t *fill = (uint64_t *)calloc((size_t)R * B, sizeof(uint64_t));
-    if (!fill) { orc_destroy(o); return NULL; }
+    if (!fill) return ORC_ENOMEM;
     for (uint32_t r = 0; r < R; ++r)
         for (uint64_t i = 0; i < K; ++i) {
             uint64_t cell = (uint64_t)r * B + orc_phi(o, r, i);
             o->mem_ids[o->mem_off[cell] + fill[cell]++] = (uint32_t)i;
         }
     free(fill);
-    return o;
+    return ORC_OK;
+}
+
+orc_t *orc_create(uint64_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, uint64_t seed) {
+    return create_impl(K, B, 1, R, m, eta, seed, 0);
+}
+
+/* Two-level hash (Sec. 5.2, appendix): n_nodes node-local structures of
+ * B_local cells stacked into one of B_local * n_nodes cells; set i lives in
+ * cell B_local * tau(i) + phi_r(i) of table r.  tau's parameters come from
+ * SplitMix64 started at tau_seed: a = 1 + next() mod (P-1), c = next() mod P. */
+orc_t *orc_create_stacked(uint64_t K, uint32_t B_local, uint32_t n_nodes, uint32_t R, uint64_t m, uint32_t eta,
+                          uint64_t seed, uint64_t tau_seed) {
+    return create_impl(K, B_local, n_nodes, R, m, eta, seed, tau_seed);
+}
+
+uint32_t orc_node(const orc_t *o, uint64_t set_id) {
+    if (o->n_nodes <= 1) return 0;
+    unsigned __int128 t = (unsigned __int128)o->a_tau * set_id + o->c_tau;
+    return (uint32_t)((uint64_t)(t % ORC_P) % o->n_nodes);
 }
 
 uint64_t orc_param_a(const orc_t *o, uint32_t r) { return o->a[r]; }
@@ -482,6 +532,39 @@ int orc_query_batch(const orc_t *o, int kind, const void *data, const uint64_t *
     for (uint64_t q = 0; q < nq; ++q) free(res[q]);
     free(res);
     return failed ? ORC_ENOMEM : ORC_OK;
+}
+
+/* ---------------- folding over (appendix) ---------------- */
+
+/* OR cell b + B/2 onto cell b of every table and halve B: each new cell is the
+ * Bloom filter of the union of the two old cells' sets. */
+int orc_fold(orc_t *o) {
+    if (o->B < 2 || (o->B & 1)) return ORC_EINVAL;
+    const uint32_t B2 = o->B / 2;
+    uint64_t *nb = (uint64_t *)calloc((size_t)o->R * B2 * o->wpb, sizeof(uint64_t));
+    if (!nb) return ORC_ENOMEM;
+    for (uint32_t r = 0; r < o->R; ++r)
+        for (uint32_t b = 0; b < B2; ++b) {
+            const uint64_t *lo = bf_of(o, r, b), *hi = bf_of(o, r, b + B2);
+            uint64_t *dst = nb + ((uint64_t)r * B2 + b) * o->wpb;
+            for (uint64_t w = 0; w < o->wpb; ++w) dst[w] = lo[w] | hi[w];
+        }
+    free(o->bits);
+    o->bits = nb;
+    o->B = B2;
+    return build_members(o);
+}
+
+/* OR another structure with identical parameters into this one (the merge of
+ * node-local structures built from disjoint sets, Sec. 5.2). */
+int orc_merge(orc_t *o, const orc_t *src) {
+    if (o->K != src->K || o->B != src->B || o->R != src->R || o->m != src->m || o->eta != src->eta ||
+        o->seed != src->seed || o->B_local != src->B_local || o->n_nodes != src->n_nodes ||
+        o->a_tau != src->a_tau || o->c_tau != src->c_tau)
+        return ORC_EINVAL;
+    for (uint64_t w = 0; w < (uint64_t)o->R * o->B * o->wpb; ++w) o->bits[w] |= src->bits[w];
+    for (uint64_t w = 0; w < (o->K + 63) / 64; ++w) o->reg[w] |= src->reg[w];
+    return ORC_OK;
 }
 
 /* ---------------- inspection ---------------- */

@@ -36,15 +36,25 @@ cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s) {
 
 struct PhiParams {
     uint64_t a[RMAX], c[RMAX];
+    uint64_t a_tau, c_tau;
+    uint32_t B_local, n_nodes;
 };
 
+// cell of set i in table r: (B_local * tau(i) + phi_r(i)) mod B, phi_r over
+// B_local cells, tau over n_nodes nodes (the two-level hash of the paper's
+// node-parallel construction; one node gives the plain partition).  B is the
+// current cell count, smaller than B_local * n_nodes after folding over.
 __global__ void k_phi_init(uint16_t* phi, uint64_t K, uint32_t R, uint32_t B, PhiParams pp) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < K;
          i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t node = pp.n_nodes > 1 ? partition_hash(pp.a_tau, pp.c_tau, i, pp.n_nodes) : 0;
         uint16_t row[PHI_STRIDE];
 #pragma unroll
-        for (int r = 0; r < PHI_STRIDE; ++r)
-            row[r] = (r < (int)R) ? (uint16_t)partition_hash(pp.a[r], pp.c[r], i, B) : (uint16_t)0;
+        for (int r = 0; r < PHI_STRIDE; ++r) {
+            uint64_t cell = 0;
+            if (r < (int)R) cell = ((uint64_t)pp.B_local * node + partition_hash(pp.a[r], pp.c[r], i, pp.B_local)) % B;
+            row[r] = (uint16_t)cell;
+        }
         uint4 v;
         v.x = row[0] | ((uint32_t)row[1] << 16);
         v.y = row[2] | ((uint32_t)row[3] << 16);
@@ -54,14 +64,30 @@ __global__ void k_phi_init(uint16_t* phi, uint64_t K, uint32_t R, uint32_t B, Ph
     }
 }
 
-cudaError_t launch_phi_init(uint16_t* phi, uint64_t K, uint32_t R, uint32_t B, const uint64_t* a,
-                            const uint64_t* c, cudaStream_t s) {
+cudaError_t launch_phi_init(uint16_t* phi, uint64_t K, uint32_t R, uint32_t B, const uint64_t* a, const uint64_t* c,
+                            uint32_t B_local, uint32_t n_nodes, uint64_t a_tau, uint64_t c_tau, cudaStream_t s) {
     PhiParams pp{};
     for (uint32_t r = 0; r < R && r < (uint32_t)RMAX; ++r) {
         pp.a[r] = a[r];
         pp.c[r] = c[r];
     }
+    pp.B_local = B_local;
+    pp.n_nodes = n_nodes;
+    pp.a_tau = a_tau;
+    pp.c_tau = c_tau;
     k_phi_init<<<grid_for(K, 256, 4096), 256, 0, s>>>(phi, K, R, B, pp);
+    return cudaGetLastError();
+}
+
+// OR of two indexes with identical layout (rows and registered bitmaps)
+__global__ void k_or_words(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] |= src[i];
+}
+
+cudaError_t launch_or_words(uint32_t* dst, const uint32_t* src, uint64_t n, cudaStream_t s) {
+    if (!n) return cudaSuccess;
+    k_or_words<<<grid_for(n, 256, 152 * 64), 256, 0, s>>>(dst, src, n);
     return cudaGetLastError();
 }
 

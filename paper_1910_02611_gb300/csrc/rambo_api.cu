@@ -107,6 +107,8 @@ constexpr uint64_t BUILD_TILE_BYTES = 64ull << 20;
 struct rambo {
     uint64_t K = 0, m = 0, seed = 0;
     uint32_t B = 0, R = 0, eta = 0, L = 0, W = 0, S = 0;
+    uint32_t B_local = 0, n_nodes = 1;  // two-level hash: B_local * n_nodes cells before any fold
+    uint64_t tau_seed = 0, a_tau = 0, c_tau = 0;
     int device = 0, num_sms = 0;
     uint64_t a[RMAX] = {}, c[RMAX] = {};
     HashParams hp{};
@@ -552,16 +554,27 @@ int handle_query_view(rambo_t* h, uint64_t n, IndexView* ix, HashParams* hp, Que
 
 extern "C" {
 
-int rambo_create(uint64_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, uint64_t seed, rambo_t** out) {
+static int create_impl(uint64_t K, uint32_t B_local, uint32_t n_nodes, uint32_t B, uint32_t R, uint64_t m, uint32_t eta,
+                       uint64_t seed, uint64_t tau_seed, rambo_t** out) {
     if (!out) return RAMBO_EINVAL;
     *out = nullptr;
     if (K < 1 || K > (1ull << 32) || B < 1 || B > RAMBO_MAX_B || R < 1 || R > RAMBO_MAX_R || eta < 1 ||
-        eta > RAMBO_MAX_ETA || m < 2 || m > (1ull << 32) || (m & (m - 1)))
+        eta > RAMBO_MAX_ETA || m < 2 || m > (1ull << 32) || (m & (m - 1)) || B_local < 1 || n_nodes < 1 ||
+        (uint64_t)B_local * n_nodes > 65535 || B > (uint64_t)B_local * n_nodes)
         return RAMBO_EINVAL;
     rambo* h = new (std::nothrow) rambo();
     if (!h) return RAMBO_ENOMEM;
     h->K = K;
     h->B = B;
+    h->B_local = B_local;
+    h->n_nodes = n_nodes;
+    h->tau_seed = tau_seed;
+    if (n_nodes > 1) {
+        uint64_t ts = tau_seed;
+        const uint64_t Pm = (1ull << 61) - 1;
+        h->a_tau = 1 + splitmix_next(ts) % (Pm - 1);
+        h->c_tau = splitmix_next(ts) % Pm;
+    }
     h->R = R;
     h->m = m;
     h->eta = eta;
@@ -600,13 +613,43 @@ int rambo_create(uint64_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, u
     cudaStream_t s = 0;
     if (cudaMemsetAsync(h->rows, 0, h->index_words() * 4, s) != cudaSuccess) return fail(RAMBO_ECUDA);
     if (cudaMemsetAsync(h->reg, 0, ((K + 31) / 32) * 4, s) != cudaSuccess) return fail(RAMBO_ECUDA);
-    if (launch_phi_init(h->phi, K, R, B, h->a, h->c, s) != cudaSuccess) return fail(RAMBO_ECUDA);
+    if (launch_phi_init(h->phi, K, R, B, h->a, h->c, h->B_local, h->n_nodes, h->a_tau, h->c_tau, s) != cudaSuccess)
+        return fail(RAMBO_ECUDA);
     if (launch_status_reset(h->st, s) != cudaSuccess) return fail(RAMBO_ECUDA);
     rc = build_cell_members(h, s);
     if (rc) return fail(rc);
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(RAMBO_ECUDA);
     default_config(h);
     *out = h;
+    return RAMBO_OK;
+}
+
+int rambo_create(uint64_t K, uint32_t B, uint32_t R, uint64_t m, uint32_t eta, uint64_t seed, rambo_t** out) {
+    return create_impl(K, B, 1, B, R, m, eta, seed, 0, out);
+}
+
+int rambo_create_stacked(uint64_t K, uint32_t cells_per_node, uint32_t n_nodes, uint32_t R, uint64_t m, uint32_t eta,
+                         uint64_t seed, uint64_t tau_seed, rambo_t** out) {
+    if ((uint64_t)cells_per_node * n_nodes > RAMBO_MAX_B) return RAMBO_EINVAL;
+    return create_impl(K, cells_per_node, n_nodes, cells_per_node * n_nodes, R, m, eta, seed, tau_seed, out);
+}
+
+uint32_t rambo_node_of(const rambo_t* h, uint64_t set_id) {
+    if (!h || h->n_nodes <= 1) return 0;
+    return (uint32_t)partition_hash(h->a_tau, h->c_tau, set_id, h->n_nodes);
+}
+
+int rambo_merge(rambo_t* dst, const rambo_t* src, void* stream) {
+    if (!dst || !src || dst == src) return RAMBO_EINVAL;
+    if (dst->K != src->K || dst->B != src->B || dst->R != src->R || dst->m != src->m || dst->eta != src->eta ||
+        dst->seed != src->seed || dst->B_local != src->B_local || dst->n_nodes != src->n_nodes ||
+        dst->tau_seed != src->tau_seed || dst->S != src->S || dst->device != src->device)
+        return RAMBO_EINVAL;
+    CK(cudaSetDevice(dst->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(launch_or_words(dst->rows, src->rows, dst->index_words(), s));
+    CK(launch_or_words(dst->reg, src->reg, (dst->K + 31) / 32, s));
+    CK(cudaStreamSynchronize(s));
     return RAMBO_OK;
 }
 
@@ -630,6 +673,9 @@ int rambo_get_info(const rambo_t* h, rambo_info_t* out) {
     uint64_t n = 0;
     for (uint32_t w : regw) n += (uint64_t)__builtin_popcount(w);
     out->n_registered = n;
+    out->nodes = h->n_nodes;
+    out->cells_per_node = h->B_local;
+    out->tau_seed = h->tau_seed;
     return RAMBO_OK;
 }
 
@@ -916,9 +962,8 @@ int rambo_fold(rambo_t* h, void* stream) {
     h->B = B2;
     h->W = W2;
     h->S = S2;
-    // (a*i + c mod P) mod B mod B/2 = (a*i + c mod P) mod B/2: the folded
-    // partition is the same hash with range B/2
-    CK(launch_phi_init(h->phi, h->K, h->R, h->B, h->a, h->c, s));
+    // a set's folded cell is its cell mod B/2 (cells b and b + B/2 merged)
+    CK(launch_phi_init(h->phi, h->K, h->R, h->B, h->a, h->c, h->B_local, h->n_nodes, h->a_tau, h->c_tau, s));
     RK(build_cell_members(h, s));
     CK(cudaStreamSynchronize(s));
     default_config(h);
@@ -954,7 +999,8 @@ int rambo_save(const rambo_t* h, const char* path) {
     CK(cudaSetDevice(h->device));
     FILE* f = fopen(path, "wb");
     if (!f) return RAMBO_EIO;
-    uint64_t hdr[8] = {0x31424753424D4152ull, h->K, h->B, h->R, h->m, h->eta, h->seed, h->S};
+    uint64_t hdr[11] = {0x32424753424D4152ull, h->K, h->B, h->R, h->m, h->eta, h->seed, h->S,
+                        h->B_local, h->n_nodes, h->tau_seed};
     bool ok = fwrite(hdr, sizeof(hdr), 1, f) == 1;
     std::vector<uint32_t> buf((h->K + 31) / 32);
     if (ok && cudaMemcpy(buf.data(), h->reg, buf.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess) ok = false;
@@ -975,13 +1021,14 @@ int rambo_load(const char* path, rambo_t** out) {
     *out = nullptr;
     FILE* f = fopen(path, "rb");
     if (!f) return RAMBO_EIO;
-    uint64_t hdr[8];
-    if (fread(hdr, sizeof(hdr), 1, f) != 1 || hdr[0] != 0x31424753424D4152ull) {
+    uint64_t hdr[11];
+    if (fread(hdr, sizeof(hdr), 1, f) != 1 || hdr[0] != 0x32424753424D4152ull) {
         fclose(f);
         return RAMBO_EINVAL;
     }
     rambo_t* h = nullptr;
-    int rc = rambo_create(hdr[1], (uint32_t)hdr[2], (uint32_t)hdr[3], hdr[4], (uint32_t)hdr[5], hdr[6], &h);
+    int rc = create_impl(hdr[1], (uint32_t)hdr[8], (uint32_t)hdr[9], (uint32_t)hdr[2], (uint32_t)hdr[3], hdr[4],
+                         (uint32_t)hdr[5], hdr[6], hdr[10], &h);
     if (rc) {
         fclose(f);
         return rc;

@@ -225,8 +225,9 @@ struct QueryTuning {
 
 // k_util.cu
 cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s);
-cudaError_t launch_phi_init(uint16_t* phi, uint64_t K, uint32_t R, uint32_t B, const uint64_t* a,
-                            const uint64_t* c, cudaStream_t s);
+cudaError_t launch_phi_init(uint16_t* phi, uint64_t K, uint32_t R, uint32_t B, const uint64_t* a, const uint64_t* c,
+                            uint32_t B_local, uint32_t n_nodes, uint64_t a_tau, uint64_t c_tau, cudaStream_t s);
+cudaError_t launch_or_words(uint32_t* dst, const uint32_t* src, uint64_t n, cudaStream_t s);
 cudaError_t launch_validate_batch(const BatchView& b, uint64_t min_len, uint64_t K, DevStatus* st,
                                   cudaStream_t s);
 cudaError_t launch_pack(const uint8_t* bases, uint64_t total, uint64_t* packed, uint64_t n_words,

@@ -21,7 +21,8 @@ _u64, _u32, _u16, _i32, _p = C.c_uint64, C.c_uint32, C.c_uint16, C.c_int, C.c_vo
 
 class RamboInfo(C.Structure):
     _fields_ = [("K", _u64), ("B", _u32), ("R", _u32), ("eta", _u32), ("L", _u32), ("m", _u64), ("seed", _u64),
-                ("row_words", _u32), ("row_stride", _u32), ("index_bytes", _u64), ("n_registered", _u64)]
+                ("row_words", _u32), ("row_stride", _u32), ("index_bytes", _u64), ("n_registered", _u64),
+                ("nodes", _u32), ("cells_per_node", _u32), ("tau_seed", _u64)]
 
 
 class QueryStats(C.Structure):
@@ -53,6 +54,9 @@ class QueryConfig(C.Structure):
 SIGNATURES = {
     "rambo_create": (_i32, [_u64, _u32, _u32, _u64, _u32, _u64, C.POINTER(_p)]),
     "rambo_destroy": (None, [_p]),
+    "rambo_create_stacked": (_i32, [_u64, _u32, _u32, _u32, _u64, _u32, _u64, _u64, C.POINTER(_p)]),
+    "rambo_node_of": (_u32, [_p, _u64]),
+    "rambo_merge": (_i32, [_p, _p, _p]),
     "rambo_get_info": (_i32, [_p, C.POINTER(RamboInfo)]),
     "rambo_insert_batch": (_i32, [_p, _p, _p, _p, _u64, _i32, _p]),
     "rambo_insert": (_i32, [_p, _u64, _p, _u64, _i32, _p]),
@@ -208,6 +212,23 @@ class Rambo:
         self.K, self.B, self.R, self.m, self.eta, self.seed = info.K, info.B, info.R, info.m, info.eta, info.seed
         self.row_stride = info.row_stride
         self.row_words = info.row_words
+
+    @classmethod
+    def stacked(cls, K: int, cells_per_node: int, nodes: int, R: int, m: int, eta: int, seed: int = 42,
+                tau_seed: int = 0) -> "Rambo":
+        """Two-level hash (Sec. 5.2): nodes x cells_per_node cells, set i in node tau(i)."""
+        h = _p()
+        rc = load_library().rambo_create_stacked(K, cells_per_node, nodes, R, m, eta, seed, tau_seed, C.byref(h))
+        if rc:
+            raise RamboError(rc, "rambo_create_stacked")
+        return cls(0, 0, 0, 0, 0, _handle=h)
+
+    def node_of(self, set_id: int) -> int:
+        return int(load_library().rambo_node_of(self._h, set_id))
+
+    def merge(self, other: "Rambo", stream=None) -> None:
+        """ORs another index with identical parameters into this one."""
+        self._check(load_library().rambo_merge(self._h, other._h, _stream_handle(stream)), "merge")
 
     @classmethod
     def load(cls, path: str) -> "Rambo":

@@ -430,3 +430,50 @@ def test_canonical_kmers_index_and_queries(mods, k):
 
     ids1, off1 = g.query_one_per_launch(torch.from_numpy(q.data).cuda(), q.offsets, kind="seq", k=k | CANON)
     assert np.array_equal(ids1, a_ids) and np.array_equal(off1, a_off)
+
+
+def test_two_level_hash_node_indexes_merge_into_the_stacked_index(mods, tmp_path):
+    # Sec. 5.2 / appendix: node-local builds (each inserting only the sets tau
+    # routes to it) OR into the stacked index; it equals the oracle's stacked
+    # structure, also after folding over and after a save/load round trip.
+    Rambo, Oracle = mods
+    w = synth.make("genome", 0.02, m=1 << 15)
+    Bl, nodes = 16, 4
+    whole = Rambo.stacked(w.K, Bl, nodes, w.R, w.m, w.eta, w.seed, tau_seed=12)
+    whole.insert(w.sets.ids, w.sets.data, w.sets.offsets, kind="seq")
+    o = Oracle(w.K, Bl, w.R, w.m, w.eta, w.seed, nodes=nodes, tau_seed=12)
+    o.insert_seq_batch(w.sets.ids, w.sets.data, w.sets.offsets, 31)
+    assert_index_equal(whole, o)
+    assert_partition_equal(whole, o)
+    assert [whole.node_of(i) for i in range(w.K)] == [o.node(i) for i in range(w.K)]
+    parts = []
+    for t in range(nodes):
+        sel = np.array([i for i in range(len(w.sets)) if whole.node_of(int(w.sets.ids[i])) == t])
+        g = Rambo.stacked(w.K, Bl, nodes, w.R, w.m, w.eta, w.seed, tau_seed=12)
+        if sel.size:
+            sub = w.sets.subset(sel)
+            g.insert(sub.ids, sub.data, sub.offsets, kind="seq")
+        parts.append(g)
+    for g in parts[1:]:
+        parts[0].merge(g)
+    assert np.array_equal(parts[0].export_index(), whole.export_index())
+    assert np.array_equal(parts[0].export_registered(), whole.export_registered())
+    assert_query_equal(parts[0], o, w.queries)
+    # folding over the stacked index
+    parts[0].fold()
+    o.fold()
+    assert_index_equal(parts[0], o)
+    assert_partition_equal(parts[0], o)
+    assert_query_equal(parts[0], o, w.queries)
+    p = str(tmp_path / "stacked.rambo")
+    parts[0].save(p)
+    back = Rambo.load(p)
+    assert np.array_equal(back.export_index(), parts[0].export_index())
+    assert_query_equal(back, o, w.queries.subset(np.arange(300)))
+    # mismatched parameters do not merge
+    from paper_1910_02611_gb300 import EINVAL, RamboError
+
+    other = Rambo.stacked(w.K, Bl, nodes, w.R, w.m, w.eta, w.seed, tau_seed=13)
+    with pytest.raises(RamboError) as e:
+        whole.merge(other)
+    assert e.value.code == EINVAL

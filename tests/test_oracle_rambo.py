@@ -331,3 +331,71 @@ def test_folding_over_equals_half_the_cells(oracle_mod):
             assert np.array_equal(full.export_bf(r, b) | full.export_bf(r, b + B // 2), half.export_bf(r, b))
         for i in range(K):
             assert full.phi(r, i) % (B // 2) == half.phi(r, i)
+
+
+# --------------------------------------------------------------------------
+# two-level hash and merge (Sec. 5.2, appendix)
+# --------------------------------------------------------------------------
+
+def test_two_level_hash_routes_sets_to_node_ranges(oracle_mod):
+    K, Bl, nodes, R = 3000, 8, 6, 4
+    o = oracle_mod.Oracle(K, Bl, R, 1 << 8, 2, 5, nodes=nodes, tau_seed=77)
+    plain = oracle_mod.Oracle(K, Bl, R, 1 << 8, 2, 5)
+    for i in range(0, K, 7):
+        t = o.node(i)
+        assert 0 <= t < nodes
+        for r in range(R):
+            cell = o.phi(r, i)
+            # B_local * tau(i) + phi_r(i), phi_r being the plain partition over B_local cells
+            assert cell == Bl * t + plain.phi(r, i)
+    # one node: the plain partition
+    one = oracle_mod.Oracle(K, Bl, R, 1 << 8, 2, 5, nodes=1, tau_seed=77)
+    assert np.array_equal(one.phi_table(), plain.phi_table())
+
+
+def test_two_level_hash_collision_rate_is_one_over_total_cells(oracle_mod):
+    # appendix: the combined mapping collides two sets with probability 1/B, B = b * nodes
+    K, Bl, nodes, R = 6000, 10, 5, 3
+    o = oracle_mod.Oracle(K, Bl, R, 1 << 8, 2, 11, nodes=nodes, tau_seed=3)
+    tab = o.phi_table()
+    rng = np.random.default_rng(5)
+    i = rng.integers(0, K, 40000)
+    j = rng.integers(0, K, 40000)
+    keep = i != j
+    B = Bl * nodes
+    coll = (tab[i[keep]] == tab[j[keep]]).mean(axis=0)
+    sd = np.sqrt((1 / B) * (1 - 1 / B) / keep.sum())
+    assert np.all(np.abs(coll - 1 / B) < 5 * sd + 0.002)
+
+
+def test_node_local_structures_merge_into_the_stacked_one(oracle_mod):
+    rng = np.random.default_rng(31)
+    K, Bl, nodes, R, m = 60, 4, 3, 3, 1 << 11
+    sets, _ = _random_sets(rng, K, 20, 80)
+    whole = oracle_mod.Oracle(K, Bl, R, m, 2, 9, nodes=nodes, tau_seed=4)
+    for i in sorted(sets):
+        whole.insert_keys(i, np.array(sorted(sets[i]), np.uint64))
+    parts = [oracle_mod.Oracle(K, Bl, R, m, 2, 9, nodes=nodes, tau_seed=4) for _ in range(nodes)]
+    for i in sorted(sets):
+        parts[whole.node(i)].insert_keys(i, np.array(sorted(sets[i]), np.uint64))
+    for t in range(nodes):  # a node only touches its own cell range
+        for r in range(R):
+            for b in range(Bl * nodes):
+                if not (Bl * t <= b < Bl * (t + 1)):
+                    assert not parts[t].export_bf(r, b).any()
+    merged = parts[0]
+    for t in range(1, nodes):
+        merged.merge(parts[t])
+    for r in range(R):
+        for b in range(Bl * nodes):
+            assert np.array_equal(merged.export_bf(r, b), whole.export_bf(r, b))
+    assert np.array_equal(merged.registered(), whole.registered())
+    # folding the stacked structure: OR of the halves, cells taken mod B/2
+    before = {(r, b): whole.export_bf(r, b) for r in range(R) for b in range(Bl * nodes)}
+    phi_before = whole.phi_table()
+    whole.fold()
+    half = Bl * nodes // 2
+    for r in range(R):
+        for b in range(half):
+            assert np.array_equal(whole.export_bf(r, b), before[(r, b)] | before[(r, b + half)])
+    assert np.array_equal(whole.phi_table(), phi_before % half)

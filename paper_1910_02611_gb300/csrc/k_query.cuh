@@ -301,9 +301,37 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                                 bits &= bits - 1;
                                 const uint64_t cell = (uint64_t)rstar * ix.B + cb;
                                 const uint64_t m0 = __ldg(ix.mem_off + cell), m1 = __ldg(ix.mem_off + cell + 1);
-                                for (uint64_t u = m0 + lane; u < m1; u += 32) {
-                                    const uint32_t i = __ldg(ix.mem_ids + u);
-                                    if (qk_set_passes(ix, sM, i, rstar)) atomicOr(sBits + (i >> 5), 1u << (i & 31));
+                                // four chunks of 32 candidates at a time: member IDs, then
+                                // their registered words and partition rows, in flight together
+                                constexpr int SU = 4;
+                                for (uint64_t u0 = m0; u0 < m1; u0 += 32 * SU) {
+                                    uint32_t id[SU];
+#pragma unroll
+                                    for (int c = 0; c < SU; ++c) {
+                                        const uint64_t u = u0 + 32 * c + lane;
+                                        id[c] = u < m1 ? __ldg(ix.mem_ids + u) : 0xffffffffu;
+                                    }
+                                    uint32_t regw[SU];
+                                    uint4 ph[SU];
+#pragma unroll
+                                    for (int c = 0; c < SU; ++c) {
+                                        const bool v = id[c] != 0xffffffffu;
+                                        regw[c] = v ? __ldg(ix.reg + (id[c] >> 5)) : 0u;
+                                        ph[c] = v ? __ldg(reinterpret_cast<const uint4*>(ix.phi) + id[c])
+                                                  : make_uint4(0, 0, 0, 0);
+                                    }
+#pragma unroll
+                                    for (int c = 0; c < SU; ++c) {
+                                        if (id[c] == 0xffffffffu || !((regw[c] >> (id[c] & 31)) & 1u)) continue;
+                                        const uint32_t cl[8] = {ph[c].x & 0xffffu, ph[c].x >> 16, ph[c].y & 0xffffu,
+                                                                ph[c].y >> 16,     ph[c].z & 0xffffu, ph[c].z >> 16,
+                                                                ph[c].w & 0xffffu, ph[c].w >> 16};
+                                        bool ok = true;
+#pragma unroll
+                                        for (int r = 0; r < RMAX; ++r)
+                                            if (r < R && r != rstar) ok &= (sM[r * ix.S + (cl[r] >> 5)] >> (cl[r] & 31)) & 1u;
+                                        if (ok) atomicOr(sBits + (id[c] >> 5), 1u << (id[c] & 31));
+                                    }
                                 }
                             }
                         }

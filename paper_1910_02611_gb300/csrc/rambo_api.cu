@@ -110,6 +110,7 @@ struct rambo {
     uint32_t B_local = 0, n_nodes = 1;  // two-level hash: B_local * n_nodes cells before any fold
     uint64_t tau_seed = 0, a_tau = 0, c_tau = 0;
     int device = 0, num_sms = 0;
+    size_t smem_per_sm = 0;
     uint64_t a[RMAX] = {}, c[RMAX] = {};
     HashParams hp{};
     uint32_t* rows = nullptr;
@@ -135,6 +136,8 @@ struct rambo {
     uint64_t launches = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // call start, query start/end, call end
     uint64_t last_err_item = 0;
+    // automatic block size: last (V, G, use_bitmap) resolved and its choice
+    int auto_key = -1, auto_wpb = 0, auto_per_sm = 0;
 
     IndexView view() const {
         IndexView v;
@@ -221,13 +224,27 @@ int build_cell_members(rambo* h, cudaStream_t s) {
 }
 
 void default_config(rambo* h) {
-    // one vector read per probe where the row allows it
-    int V = h->S % 4 == 0 ? 4 : (h->S % 2 == 0 ? 2 : 1);
-    int G = 1;
-    while ((uint32_t)(G * V) < h->S) G *= 2;
+    // One vector read per probe where the row allows it, as long as a lane's
+    // words in flight (R * eta probes of V words each, all issued before any
+    // is used) stay within 64 registers: wider tiles cost more in occupancy
+    // than their fewer load instructions save.
+    int V = 0, G = 0, fb_V = 0, fb_G = 0;
+    for (int v = 4; v >= 1; v >>= 1) {
+        if (h->S % (uint32_t)v) continue;
+        int g = 1;
+        while ((uint32_t)(g * v) < h->S) g *= 2;
+        if (!query_config_supported(v, g, h->S)) continue;
+        if (!fb_V) fb_V = v, fb_G = g;
+        if (h->R * h->eta * (uint32_t)v <= 64) {
+            V = v, G = g;
+            break;
+        }
+    }
+    if (!V) V = fb_V, G = fb_G;
     h->cfg.words_per_lane = (uint32_t)V;
     h->cfg.lanes_per_key = (uint32_t)G;
-    h->cfg.warps_per_block = 8;
+    h->cfg.warps_per_block = 0;  // chosen per call from the occupancy
+    h->auto_key = -1;
     h->cfg.blocks_per_sm = 0;
     h->cfg.set_stage = 0;
     h->cfg.visit_order = 2;
@@ -363,9 +380,42 @@ int resolve_tuning(rambo* h, uint64_t n, int& use_bitmap, QueryTuning& t) {
     t.order = (int)h->cfg.visit_order;
     t.load_kind = (int)h->cfg.row_load;
     use_bitmap = (h->mem_off && t.set_stage != 1 && (h->K + 31) / 32 <= 4096) ? 1 : 0;
-    const size_t smem =
-        (size_t)query_smem_words_per_warp(h->R, h->S, h->K, use_bitmap) * 4 * (size_t)t.warps_per_block;
-    int per_sm = query_max_blocks_per_sm(t.V, t.G, h->eta, t.warps_per_block, smem);
+    const size_t spw_bytes = (size_t)query_smem_words_per_warp(h->R, h->S, h->K, use_bitmap) * 4;
+    int per_sm = 0;
+    if (t.warps_per_block == 0) {
+        // The largest block that keeps at least 85% of the most warps any
+        // block size can keep resident per SM, counting only blocks whose
+        // shared memory leaves 64 KB of the SM's unified L1 free: the set
+        // stage re-reads the partition table, member lists and bitmaps
+        // through L1.  The per-warp bitmap grows with K, so for large ID
+        // spaces shared memory, not registers, limits the residency.
+        const int key = (t.V * 64 + t.G) * 2 + use_bitmap;
+        if (h->auto_key != key) {
+            const size_t budget = h->smem_per_sm > (64u << 10) ? h->smem_per_sm - (64u << 10) : h->smem_per_sm;
+            int nb_of[4] = {0, 0, 0, 0}, best = 0;
+            for (int i = 0; i < 4; ++i) {
+                const int w = 8 >> i;
+                const size_t blk = spw_bytes * (size_t)w;
+                int nb = query_max_blocks_per_sm(t.V, t.G, h->eta, w, blk);
+                const int fit = blk ? (int)(budget / blk) : nb;
+                if (nb > fit) nb = fit > 0 ? fit : (nb > 0 ? 1 : 0);
+                nb_of[i] = nb;
+                if (nb * w > best) best = nb * w;
+            }
+            if (best < 1) return RAMBO_EINVAL;
+            for (int i = 0; i < 4; ++i)
+                if (nb_of[i] > 0 && 100 * nb_of[i] * (8 >> i) >= 85 * best) {
+                    h->auto_wpb = 8 >> i;
+                    h->auto_per_sm = nb_of[i];
+                    break;
+                }
+            h->auto_key = key;
+        }
+        t.warps_per_block = h->auto_wpb;
+        per_sm = h->auto_per_sm;
+    } else {
+        per_sm = query_max_blocks_per_sm(t.V, t.G, h->eta, t.warps_per_block, spw_bytes * (size_t)t.warps_per_block);
+    }
     if (per_sm < 1) return RAMBO_EINVAL;
     if (h->cfg.blocks_per_sm && (int)h->cfg.blocks_per_sm < per_sm) per_sm = (int)h->cfg.blocks_per_sm;
     uint64_t blocks = (uint64_t)per_sm * h->num_sms;
@@ -584,6 +634,9 @@ static int create_impl(uint64_t K, uint32_t B_local, uint32_t n_nodes, uint32_t 
     h->S = stride_for(h->W);
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    int smem_sm = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
+    h->smem_per_sm = (size_t)smem_sm;
     if (e != cudaSuccess) {
         delete h;
         return map_cuda(e);
@@ -831,7 +884,9 @@ int rambo_get_query_config(const rambo_t* h, rambo_query_config_t* out) {
 int rambo_set_query_config(rambo_t* h, const rambo_query_config_t* cfg) {
     if (!h || !cfg) return RAMBO_EINVAL;
     if (!query_config_supported((int)cfg->words_per_lane, (int)cfg->lanes_per_key, h->S)) return RAMBO_EINVAL;
-    if (cfg->warps_per_block < 1 || cfg->warps_per_block > 8) return RAMBO_EINVAL;
+    if (cfg->warps_per_block != 0 && cfg->warps_per_block != 1 && cfg->warps_per_block != 2 &&
+        cfg->warps_per_block != 4 && cfg->warps_per_block != 8)
+        return RAMBO_EINVAL;
     if (cfg->set_stage > 3) return RAMBO_EINVAL;
     if (cfg->set_stage == 2 && !h->mem_off) return RAMBO_EINVAL;
     if (cfg->set_stage == 3 && !h->mem_bits) return RAMBO_EINVAL;

@@ -367,8 +367,8 @@ int rambo_last_query_stats(const rambo_t *h, rambo_query_stats_t *out);
 /* Tuning knobs of the query kernel; results never depend on them.
  *   lanes_per_key G, words_per_lane V (V divides the row stride, G*V >= stride),
  *   warps_per_block (1, 2, 4 or 8; 0 = automatic: the largest block that
- *   keeps at least 85% of the most warps resident per SM while leaving 64 KB
- *   of the SM's L1 free), blocks_per_sm (0 = as many as fit),
+ *   keeps at least 85% of the most warps resident per SM),
+ *   blocks_per_sm (0 = as many as fit),
  *   set_stage: 0 = auto, 1 = dense scan of the partition table,
  *              2 = sparse enumeration of the hit cells' members,
  *              3 = union of the hit cells' member bitmaps (complemented for

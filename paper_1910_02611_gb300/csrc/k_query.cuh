@@ -292,46 +292,61 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                             }
                         }
                     } else if (stage == 2) {
-                        // sparse: members of the hit cells of table rstar, tested on the other tables
+                        // sparse: the registered members of table rstar's hit cells,
+                        // tested on the other tables.  Hit cells are taken one mask
+                        // word (up to 32 cells) at a time; lane j holds cell j's
+                        // member range, and the members of all those cells form one
+                        // run of candidates, 128 per iteration, whose IDs and
+                        // partition rows are two independent coalesced loads.
                         const uint32_t* cellmask = sM + rstar * ix.S;
+                        const uint64_t cbase = (uint64_t)rstar * ix.B;
                         for (uint32_t w = 0; w < ix.W; ++w) {
-                            uint32_t bits = cellmask[w];
-                            while (bits) {
-                                const uint32_t cb = w * 32 + (__ffs(bits) - 1);
-                                bits &= bits - 1;
-                                const uint64_t cell = (uint64_t)rstar * ix.B + cb;
-                                const uint64_t m0 = __ldg(ix.mem_off + cell), m1 = __ldg(ix.mem_off + cell + 1);
-                                // four chunks of 32 candidates at a time: member IDs, then
-                                // their registered words and partition rows, in flight together
-                                constexpr int SU = 4;
-                                for (uint64_t u0 = m0; u0 < m1; u0 += 32 * SU) {
-                                    uint32_t id[SU];
+                            const uint32_t hits = cellmask[w];
+                            if (!hits) continue;
+                            uint32_t m0 = 0, cnt = 0;
+                            if ((hits >> lane) & 1u) {
+                                const uint64_t cell = cbase + w * 32 + lane;
+                                m0 = (uint32_t)__ldg(ix.mem_off + cell);
+                                cnt = (uint32_t)__ldg(ix.mem_off + cell + 1) - m0;
+                            }
+                            uint32_t incl = cnt;
 #pragma unroll
-                                    for (int c = 0; c < SU; ++c) {
-                                        const uint64_t u = u0 + 32 * c + lane;
-                                        id[c] = u < m1 ? __ldg(ix.mem_ids + u) : 0xffffffffu;
+                            for (int off = 1; off < 32; off <<= 1) {
+                                const uint32_t y = __shfl_up_sync(FULL, incl, off);
+                                if (lane >= (unsigned)off) incl += y;
+                            }
+                            const uint32_t total = __shfl_sync(FULL, incl, 31);
+                            const uint32_t base = m0 - (incl - cnt);  // list position of candidate u = base + u
+                            constexpr int SU = 4;
+                            for (uint32_t u0 = 0; u0 < total; u0 += 32 * SU) {
+                                uint32_t id[SU];
+                                uint4 ph[SU];
+#pragma unroll
+                                for (int c = 0; c < SU; ++c) {
+                                    const uint32_t u = u0 + 32 * c + lane;
+                                    // owner lane: the first lane whose inclusive count exceeds u
+                                    uint32_t j = 0;
+#pragma unroll
+                                    for (uint32_t step = 16; step >= 1; step >>= 1) {
+                                        const uint32_t e = __shfl_sync(FULL, incl, j + step - 1);
+                                        if (e <= u) j += step;
                                     }
-                                    uint32_t regw[SU];
-                                    uint4 ph[SU];
+                                    const uint32_t pos = __shfl_sync(FULL, base, j) + u;
+                                    const bool v = u < total;
+                                    id[c] = v ? __ldg(ix.mem_ids + pos) : 0xffffffffu;
+                                    ph[c] = v ? __ldg(ix.mem_phi + pos) : make_uint4(0, 0, 0, 0);
+                                }
 #pragma unroll
-                                    for (int c = 0; c < SU; ++c) {
-                                        const bool v = id[c] != 0xffffffffu;
-                                        regw[c] = v ? __ldg(ix.reg + (id[c] >> 5)) : 0u;
-                                        ph[c] = v ? __ldg(reinterpret_cast<const uint4*>(ix.phi) + id[c])
-                                                  : make_uint4(0, 0, 0, 0);
-                                    }
+                                for (int c = 0; c < SU; ++c) {
+                                    if (id[c] == 0xffffffffu) continue;
+                                    const uint32_t cl[8] = {ph[c].x & 0xffffu, ph[c].x >> 16, ph[c].y & 0xffffu,
+                                                            ph[c].y >> 16,     ph[c].z & 0xffffu, ph[c].z >> 16,
+                                                            ph[c].w & 0xffffu, ph[c].w >> 16};
+                                    bool ok = true;
 #pragma unroll
-                                    for (int c = 0; c < SU; ++c) {
-                                        if (id[c] == 0xffffffffu || !((regw[c] >> (id[c] & 31)) & 1u)) continue;
-                                        const uint32_t cl[8] = {ph[c].x & 0xffffu, ph[c].x >> 16, ph[c].y & 0xffffu,
-                                                                ph[c].y >> 16,     ph[c].z & 0xffffu, ph[c].z >> 16,
-                                                                ph[c].w & 0xffffu, ph[c].w >> 16};
-                                        bool ok = true;
-#pragma unroll
-                                        for (int r = 0; r < RMAX; ++r)
-                                            if (r < R && r != rstar) ok &= (sM[r * ix.S + (cl[r] >> 5)] >> (cl[r] & 31)) & 1u;
-                                        if (ok) atomicOr(sBits + (id[c] >> 5), 1u << (id[c] & 31));
-                                    }
+                                    for (int r = 0; r < RMAX; ++r)
+                                        if (r < R && r != rstar) ok &= (sM[r * ix.S + (cl[r] >> 5)] >> (cl[r] & 31)) & 1u;
+                                    if (ok) atomicOr(sBits + (id[c] >> 5), 1u << (id[c] & 31));
                                 }
                             }
                         }
@@ -416,7 +431,10 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                         }
                     }
                     __syncwarp();
-                    // compaction: ascending IDs from the bitmap, bitmap cleared
+                    // compaction: ascending IDs from the bitmap, bitmap cleared.
+                    // 32 words (1024 IDs) at a time: lanes expand their word's bits
+                    // into shared memory at their prefix position, then the warp
+                    // copies the run out with coalesced stores.
                     for (uint32_t w = lane; w < bw; w += 32) count += __popc(sBits[w]);
                     count = __reduce_add_sync(FULL, count);
                     if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
@@ -433,16 +451,28 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                             uint32_t y = __shfl_up_sync(FULL, incl, off);
                             if (lane >= (unsigned)off) incl += y;
                         }
-                        if (write) {
-                            uint32_t pos = at + incl - c;
-                            while (bits) {
-                                const uint32_t bit = __ffs(bits) - 1;
-                                bits &= bits - 1;
-                                o.stage[start + pos++] = w * 32 + bit;
+                        const uint32_t blk = __shfl_sync(FULL, incl, 31);
+                        if (write && blk) {
+                            uint32_t* dst = o.stage + start + at;
+                            if (blk <= (uint32_t)QK_ID_CAP) {
+                                uint32_t pos = incl - c;
+                                while (bits) {
+                                    sIds[pos++] = w * 32 + (__ffs(bits) - 1);
+                                    bits &= bits - 1;
+                                }
+                                __syncwarp();
+                                for (uint32_t t = lane; t < blk; t += 32) dst[t] = sIds[t];
+                                __syncwarp();
+                            } else {
+                                uint32_t pos = incl - c;
+                                while (bits) {
+                                    dst[pos++] = w * 32 + (__ffs(bits) - 1);
+                                    bits &= bits - 1;
+                                }
                             }
                         }
                         if (w < bw) sBits[w] = 0;
-                        at += __shfl_sync(FULL, incl, 31);
+                        at += blk;
                     }
                     __syncwarp();
                 } else {

@@ -224,13 +224,16 @@ cudaError_t launch_resolve_bad_base(const BatchView& b, DevStatus* st, cudaStrea
 }
 
 // Every listed set ID becomes registered (Algorithm 2's SetIDs(M[b,r]) only
-// reports inserted sets).  Runs only on a clean batch.
-__global__ void k_register(BatchView b, uint32_t* reg, const DevStatus* st) {
+// reports inserted sets).  Runs only on a clean batch; counts the IDs that were
+// not registered before in st->spare[0], so the host knows when the per-cell
+// member lists need rebuilding.
+__global__ void k_register(BatchView b, uint32_t* reg, DevStatus* st) {
     if (st->err != NO_ERR) return;
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < b.n;
          t += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t id = b.set_ids[t];
-        atomicOr(reg + (id >> 5), 1u << (id & 31));
+        const uint32_t bit = 1u << (id & 31);
+        if (!(atomicOr(reg + (id >> 5), bit) & bit)) atomicAdd(&st->spare[0], 1ull);
     }
 }
 
@@ -507,25 +510,32 @@ cudaError_t launch_cell_popcount(const IndexView& ix, unsigned long long* out, c
 }
 
 // ---------------------------------------------------------------------------
-// members of every cell (in no particular order): count, scan, place
-
-__global__ void k_member_count(const uint16_t* __restrict__ phi, uint64_t K, uint32_t R, uint32_t B,
-                               uint32_t* __restrict__ cnt) {
+// Per-cell member lists of the registered sets (sparse set stage): counts,
+// then placement of each ID with its partition row beside it, so the stage
+// reads both with coalesced loads.  Order within a cell is arbitrary.
+__global__ void k_member_count(const uint16_t* __restrict__ phi, const uint32_t* __restrict__ reg, uint64_t K,
+                               uint32_t R, uint32_t B, uint32_t* __restrict__ cnt) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < K;
-         i += (uint64_t)gridDim.x * blockDim.x)
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        if (!((reg[i >> 5] >> (i & 31)) & 1u)) continue;
         for (uint32_t r = 0; r < R; ++r) atomicAdd(cnt + r * B + phi[i * PHI_STRIDE + r], 1u);
+    }
 }
 
-__global__ void k_member_place(const uint16_t* __restrict__ phi, uint64_t K, uint32_t R, uint32_t B,
-                               const uint64_t* __restrict__ off, uint32_t* __restrict__ fill,
-                               uint32_t* __restrict__ ids) {
+__global__ void k_member_place(const uint16_t* __restrict__ phi, const uint32_t* __restrict__ reg, uint64_t K,
+                               uint32_t R, uint32_t B, const uint64_t* __restrict__ off, uint32_t* __restrict__ fill,
+                               uint32_t* __restrict__ ids, uint4* __restrict__ rows) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < K;
-         i += (uint64_t)gridDim.x * blockDim.x)
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        if (!((reg[i >> 5] >> (i & 31)) & 1u)) continue;
+        const uint4 row = reinterpret_cast<const uint4*>(phi)[i];
         for (uint32_t r = 0; r < R; ++r) {
             uint32_t cell = r * B + phi[i * PHI_STRIDE + r];
             uint32_t at = atomicAdd(fill + cell, 1u);
             ids[off[cell] + at] = (uint32_t)i;
+            rows[off[cell] + at] = row;
         }
+    }
 }
 
 __global__ void k_member_bits(const uint16_t* __restrict__ phi, uint64_t K, uint32_t R, uint32_t B,
@@ -547,19 +557,20 @@ cudaError_t launch_member_bits(const IndexView& ix, uint32_t* mem_bits, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_members(const IndexView& ix, uint64_t* mem_off, uint32_t* mem_ids, uint32_t* fill,
-                           cudaStream_t s) {
+cudaError_t launch_members(const IndexView& ix, uint64_t* mem_off, uint32_t* mem_ids, uint4* mem_phi,
+                           uint32_t* fill, cudaStream_t s) {
     uint32_t cells = ix.R * ix.B;
     cudaError_t e = cudaMemsetAsync(fill, 0, sizeof(uint32_t) * cells, s);
     if (e != cudaSuccess) return e;
-    k_member_count<<<grid_for(ix.K, 256, 4096), 256, 0, s>>>(ix.phi, ix.K, ix.R, ix.B, fill);
+    k_member_count<<<grid_for(ix.K, 256, 4096), 256, 0, s>>>(ix.phi, ix.reg, ix.K, ix.R, ix.B, fill);
     // offsets from counts; tmp space: reuse the tail of mem_off (caller sized it)
     uint64_t* tmp = mem_off + cells + 1;
     e = launch_scan_counts(fill, cells, mem_off, tmp, scan_tmp_words(cells), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(fill, 0, sizeof(uint32_t) * cells, s);
     if (e != cudaSuccess) return e;
-    k_member_place<<<grid_for(ix.K, 256, 4096), 256, 0, s>>>(ix.phi, ix.K, ix.R, ix.B, mem_off, fill, mem_ids);
+    k_member_place<<<grid_for(ix.K, 256, 4096), 256, 0, s>>>(ix.phi, ix.reg, ix.K, ix.R, ix.B, mem_off, fill,
+                                                             mem_ids, mem_phi);
     return cudaGetLastError();
 }
 

@@ -110,7 +110,6 @@ struct rambo {
     uint32_t B_local = 0, n_nodes = 1;  // two-level hash: B_local * n_nodes cells before any fold
     uint64_t tau_seed = 0, a_tau = 0, c_tau = 0;
     int device = 0, num_sms = 0;
-    size_t smem_per_sm = 0;
     uint64_t a[RMAX] = {}, c[RMAX] = {};
     HashParams hp{};
     uint32_t* rows = nullptr;
@@ -118,6 +117,7 @@ struct rambo {
     uint32_t* reg = nullptr;
     uint64_t* mem_off = nullptr;
     uint32_t* mem_ids = nullptr;
+    uint4* mem_phi = nullptr;
     uint32_t* mem_bits = nullptr;
     DevStatus* st = nullptr;
     DevStatus* h_st = nullptr;  // pinned
@@ -154,6 +154,7 @@ struct rambo {
         v.reg = reg;
         v.mem_off = mem_off;
         v.mem_ids = mem_ids;
+        v.mem_phi = mem_phi;
         v.mem_bits = mem_bits;
         return v;
     }
@@ -172,6 +173,7 @@ void free_handle(rambo* h) {
     if (h->reg) cudaFree(h->reg);
     if (h->mem_off) cudaFree(h->mem_off);
     if (h->mem_ids) cudaFree(h->mem_ids);
+    if (h->mem_phi) cudaFree(h->mem_phi);
     if (h->mem_bits) cudaFree(h->mem_bits);
     if (h->st) cudaFree(h->st);
     if (h->h_st) cudaFreeHost(h->h_st);
@@ -201,22 +203,37 @@ void free_handle(rambo* h) {
 
 // Member lists and member bitmaps of every cell (sparse and union set stages),
 // rebuilt from the partition table; skipped when they would be too large.
+// Rebuilds the registered members' lists in place (their buffers keep their
+// addresses, so captured plans stay valid).  Needed whenever registration
+// changes: inserts of new set IDs, merges, loads.
+int refresh_cell_members(rambo* h, cudaStream_t s) {
+    if (!h->mem_off) return RAMBO_OK;
+    CK(launch_members(h->view(), h->mem_off, h->mem_ids, h->mem_phi, h->fill.p, s));
+    return RAMBO_OK;
+}
+
+// Set-stage tables: per-cell member lists (registered sets only, with their
+// partition rows) and per-cell member bitmaps.  Both serve only ID spaces a
+// per-warp shared-memory bitmap can hold (K <= 4096 * 32).
 int build_cell_members(rambo* h, cudaStream_t s) {
     if (h->mem_off) cudaFree(h->mem_off);
     if (h->mem_ids) cudaFree(h->mem_ids);
+    if (h->mem_phi) cudaFree(h->mem_phi);
     if (h->mem_bits) cudaFree(h->mem_bits);
     h->mem_off = nullptr;
     h->mem_ids = nullptr;
+    h->mem_phi = nullptr;
     h->mem_bits = nullptr;
     const uint64_t cells = (uint64_t)h->R * h->B, K = h->K;
-    if ((uint64_t)h->R * K * 4 > (1ull << 30)) return RAMBO_OK;
+    if ((K + 31) / 32 > 4096) return RAMBO_OK;
     if (cudaMalloc(&h->mem_off, (cells + 1 + scan_tmp_words(cells)) * sizeof(uint64_t)) != cudaSuccess ||
-        cudaMalloc(&h->mem_ids, (uint64_t)h->R * K * sizeof(uint32_t)) != cudaSuccess)
+        cudaMalloc(&h->mem_ids, (uint64_t)h->R * K * sizeof(uint32_t) + 16) != cudaSuccess ||
+        cudaMalloc(&h->mem_phi, (uint64_t)h->R * K * sizeof(uint4) + 16) != cudaSuccess)
         return RAMBO_ENOMEM;
     RK(h->fill.ensure(cells));
-    CK(launch_members(h->view(), h->mem_off, h->mem_ids, h->fill.p, s));
+    RK(refresh_cell_members(h, s));
     const uint64_t mb_bytes = cells * ((K + 31) / 32) * 4;
-    if ((K + 31) / 32 <= 4096 && mb_bytes <= (256ull << 20)) {
+    if (mb_bytes <= (256ull << 20)) {
         if (cudaMalloc(&h->mem_bits, mb_bytes) != cudaSuccess) return RAMBO_ENOMEM;
         CK(launch_member_bits(h->view(), h->mem_bits, s));
     }
@@ -359,7 +376,13 @@ int run_insert(rambo* h, int seq, const uint64_t* set_ids, const void* data, con
     }
     CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    return decode_err(h, h->h_st->err);
+    const int rc = decode_err(h, h->h_st->err);
+    if (rc == RAMBO_OK && h->h_st->spare[0]) {
+        // new sets were registered: their cells' member lists change
+        RK(refresh_cell_members(h, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return rc;
 }
 
 struct QueryDest {
@@ -384,23 +407,16 @@ int resolve_tuning(rambo* h, uint64_t n, int& use_bitmap, QueryTuning& t) {
     int per_sm = 0;
     if (t.warps_per_block == 0) {
         // The largest block that keeps at least 85% of the most warps any
-        // block size can keep resident per SM, counting only blocks whose
-        // shared memory leaves 64 KB of the SM's unified L1 free: the set
-        // stage re-reads the partition table, member lists and bitmaps
-        // through L1.  The per-warp bitmap grows with K, so for large ID
-        // spaces shared memory, not registers, limits the residency.
+        // block size can keep resident per SM.  The per-warp bitmap grows
+        // with K, so for large ID spaces shared memory, not registers, limits
+        // the residency and smaller blocks pack the SM more fully.
         const int key = (t.V * 64 + t.G) * 2 + use_bitmap;
         if (h->auto_key != key) {
-            const size_t budget = h->smem_per_sm > (64u << 10) ? h->smem_per_sm - (64u << 10) : h->smem_per_sm;
             int nb_of[4] = {0, 0, 0, 0}, best = 0;
             for (int i = 0; i < 4; ++i) {
                 const int w = 8 >> i;
-                const size_t blk = spw_bytes * (size_t)w;
-                int nb = query_max_blocks_per_sm(t.V, t.G, h->eta, w, blk);
-                const int fit = blk ? (int)(budget / blk) : nb;
-                if (nb > fit) nb = fit > 0 ? fit : (nb > 0 ? 1 : 0);
-                nb_of[i] = nb;
-                if (nb * w > best) best = nb * w;
+                nb_of[i] = query_max_blocks_per_sm(t.V, t.G, h->eta, w, spw_bytes * (size_t)w);
+                if (nb_of[i] * w > best) best = nb_of[i] * w;
             }
             if (best < 1) return RAMBO_EINVAL;
             for (int i = 0; i < 4; ++i)
@@ -634,9 +650,6 @@ static int create_impl(uint64_t K, uint32_t B_local, uint32_t n_nodes, uint32_t 
     h->S = stride_for(h->W);
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
-    int smem_sm = 0;
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
-    h->smem_per_sm = (size_t)smem_sm;
     if (e != cudaSuccess) {
         delete h;
         return map_cuda(e);
@@ -702,6 +715,7 @@ int rambo_merge(rambo_t* dst, const rambo_t* src, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     CK(launch_or_words(dst->rows, src->rows, dst->index_words(), s));
     CK(launch_or_words(dst->reg, src->reg, (dst->K + 31) / 32, s));
+    RK(refresh_cell_members(dst, s));
     CK(cudaStreamSynchronize(s));
     return RAMBO_OK;
 }
@@ -1108,6 +1122,10 @@ int rambo_load(const char* path, rambo_t** out) {
     if (!ok) {
         rambo_destroy(h);
         return RAMBO_EIO;
+    }
+    if (refresh_cell_members(h, nullptr) != RAMBO_OK || cudaStreamSynchronize(nullptr) != cudaSuccess) {
+        rambo_destroy(h);
+        return RAMBO_ECUDA;
     }
     *out = h;
     return RAMBO_OK;

@@ -171,8 +171,9 @@ struct IndexView {
     uint32_t B;
     const uint16_t* phi;   // [K][PHI_STRIDE]
     uint32_t* reg;         // ceil(K/32) words
-    const uint64_t* mem_off;  // [R*B + 1] offsets of each cell's members (sparse stage)
-    const uint32_t* mem_ids;  // members of each cell (unordered)
+    const uint64_t* mem_off;  // [R*B + 1] offsets of each cell's registered members (sparse stage)
+    const uint32_t* mem_ids;  // registered members of each cell (unordered)
+    const uint4* mem_phi;     // partition row of each mem_ids entry, same order
     const uint32_t* mem_bits; // [R][B][ceil(K/32)] member bitmap of every cell (union set stage)
 };
 
@@ -241,7 +242,7 @@ cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_
                           const DevStatus* st, cudaStream_t s, const uint64_t* n_dev = nullptr,
                           uint64_t ids_cap = ~0ull);
 cudaError_t launch_cell_popcount(const IndexView& ix, unsigned long long* out, cudaStream_t s);
-cudaError_t launch_members(const IndexView& ix, uint64_t* mem_off, uint32_t* mem_ids,
+cudaError_t launch_members(const IndexView& ix, uint64_t* mem_off, uint32_t* mem_ids, uint4* mem_phi,
                            uint32_t* fill, cudaStream_t s);
 cudaError_t launch_member_bits(const IndexView& ix, uint32_t* mem_bits, cudaStream_t s);
 cudaError_t launch_fold(const uint32_t* old_rows, uint64_t n_rows, uint32_t W, uint32_t S, uint32_t B2, uint32_t W2,

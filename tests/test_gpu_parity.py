@@ -477,3 +477,48 @@ def test_two_level_hash_node_indexes_merge_into_the_stacked_index(mods, tmp_path
     with pytest.raises(RamboError) as e:
         whole.merge(other)
     assert e.value.code == EINVAL
+
+
+def test_set_stages_follow_registration_across_inserts_merge_and_load(mods, tmp_path):
+    # Algorithm 2 reports only inserted sets (registered IDs).  The sparse
+    # stage enumerates registered members of the hit cells, so its tables must
+    # follow every change of registration: later inserts of new IDs (also
+    # seen by a plan captured before them), a merge, and a load.
+    Rambo, Oracle = mods
+    from paper_1910_02611_gb300 import Plan
+
+    w = synth.make("document", 0.01, m=1 << 16)
+    n = len(w.sets)
+    halves = [w.sets.subset(np.arange(0, n // 2)), w.sets.subset(np.arange(n // 2, n))]
+    g = Rambo(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    o = Oracle(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    q = w.queries.subset(np.arange(400))
+    base = g.get_config()
+    plan = Plan(g, "keys", len(q), int(q.offsets[-1]), 1 << 22)
+
+    def check_all(index):
+        try:
+            for stage in (0, 1, 2, 3):
+                index.set_config(**{**base, "set_stage": stage})
+                assert_query_equal(index, o, q)
+        finally:
+            index.set_config(**base)
+
+    for part in halves:
+        g.insert(part.ids, part.data, part.offsets, kind="keys")
+        o.insert_keys_batch(part.ids, part.data, part.offsets)
+        check_all(g)
+        plan.launch_host(q.data, q.offsets)
+        ids, off = plan.wait()
+        rids, roff = o.query_batch("keys", q.data, q.offsets)
+        assert np.array_equal(off, roff) and np.array_equal(ids, rids)
+    # two indexes over the two halves, merged
+    a = Rambo(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    b = Rambo(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    a.insert(halves[0].ids, halves[0].data, halves[0].offsets, kind="keys")
+    b.insert(halves[1].ids, halves[1].data, halves[1].offsets, kind="keys")
+    a.merge(b)
+    check_all(a)
+    p = str(tmp_path / "doc.rambo")
+    a.save(p)
+    check_all(Rambo.load(p))

@@ -395,6 +395,14 @@ typedef struct rambo_query_config {
     uint32_t row_load;        /* cache operator of the row reads: 0 = ld.global.nc,
                                * 1 = .cg, 2 = .cs, 3 = .lu, 4 = .cv,
                                * 5 = .nc with L1::no_allocate */
+    uint32_t warps_per_query; /* 1 = one warp per query; 2, 4, 8 = that many warps
+                               * of a block share each query (its terms and its
+                               * set stage), capped at warps_per_block; 0 = from
+                               * the batch size: as many as the persistent grid
+                               * can give every query of the batch at once (a
+                               * small batch spreads each query over a block).
+                               * Needs a set stage with a shared-memory bitmap
+                               * (K <= 131072); otherwise one warp per query. */
 } rambo_query_config_t;
 
 int rambo_get_query_config(const rambo_t *h, rambo_query_config_t *out);

@@ -1,9 +1,12 @@
 // k_query.cuh -- the batched RAMBO query kernel (Algorithm 2, Sec. 3.2, with
 // the sequence rule of Sec. 3.2.1), as a template over its register tiling.
 //
-// One warp answers one query at a time, taking query indices from a device
-// work queue (an atomic ticket), so queries of very uneven length balance
-// themselves across a persistent grid.
+// A group of P warps answers one query at a time, taking query indices from a
+// device work queue (an atomic ticket), so queries of very uneven length
+// balance themselves across a persistent grid.  P = 1 for large batches; a
+// batch too small to occupy every warp gives each query up to a whole block
+// (P <= 8), whose warps split the query's steps and its set stage and meet at
+// a hardware barrier of their own.
 //
 // Per query (terms Q = its keys, or the k-mers of its sequence):
 //   A1/A2  each lane group (G lanes) takes one term per step, builds the key
@@ -34,6 +37,7 @@ namespace rgb {
 
 constexpr int QK_THREADS_MAX = 256;
 constexpr int QK_ID_CAP = 512;  // per-warp staging words: dense survivors, or the union stage's cell lists
+constexpr int QK_CTL = 16;      // per-warp control words (a query group uses its first warp's)
 
 __host__ __device__ inline uint32_t qk_bitmap_words(uint64_t K) { return (uint32_t)((K + 31) / 32); }
 
@@ -82,13 +86,45 @@ __device__ __forceinline__ bool qk_set_passes(const IndexView& ix, const uint32_
     return ok;
 }
 
-template <int V, int G, int ETA>
-__global__ void __launch_bounds__(QK_THREADS_MAX)
+// Synchronises the P warps of a query group (P = 1: the warp alone).  Groups
+// of a block use distinct hardware barriers 1..4 (0 is __syncthreads').
+__device__ __forceinline__ void qk_group_sync(unsigned P, unsigned gi) {
+    if (P == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(gi + 1), "r"(P * 32) : "memory");
+    }
+}
+
+// Warps per query for a batch of n queries: 1 if the set stage has no
+// shared-memory bitmap or group == 1; a forced group size (group = 2, 4, 8)
+// capped at the block; else (group = 0) the largest power of two up to the
+// block whose P * n warps the group launch's grid (group_warps) holds at once.
+__host__ __device__ inline unsigned qk_group_size(uint64_t n, int group, unsigned wpb, uint64_t group_warps,
+                                                  int use_bitmap) {
+    unsigned P = 1;
+    if (!use_bitmap || group == 1) return 1;
+    const unsigned cap = group ? ((unsigned)group < wpb ? (unsigned)group : wpb) : wpb;
+    while (P * 2 <= cap && (group || (uint64_t)P * 2 * n <= group_warps)) P *= 2;
+    return P;
+}
+
+// Two instances per tiling: GROUP = false is the one-warp-per-query kernel
+// (P = 1 folded in at compile time), GROUP = true serves batches that give a
+// query more than one warp.  A launch whose instance does not match the
+// batch's group size returns at once, so a captured graph holds both and the
+// batch size, read on the device, picks.  Tilings whose row words in flight
+// (RMAX * ETA * V) fit in 64 registers are held to 128 registers a thread, so
+// two full blocks share an SM; wider ones keep every register they need.
+template <int V, int G, int ETA, bool GROUP>
+__global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1)
     k_query(IndexView ix, HashParams hp, BatchView b, QueryOut o, int set_stage, int batch,
-            uint32_t smem_per_warp, int use_bitmap, int order, int load_kind, DevStatus* st) {
+            uint32_t smem_per_warp, int use_bitmap, int order, int load_kind, int group,
+            unsigned long long group_warps, DevStatus* st) {
     extern __shared__ uint32_t qk_smem[];
     constexpr int KPS = 32 / G;  // terms per warp step
     const unsigned lane = threadIdx.x & 31;
+    const unsigned wid = threadIdx.x >> 5;
     const unsigned grp = lane / G;
     const unsigned slot = lane % G;
     const uint32_t w0 = slot * V;
@@ -96,23 +132,46 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
     const int R = (int)ix.R;
     const int eta = (int)ix.eta;
     const uint32_t rmask = (1u << R) - 1u;
-    uint32_t* sM = qk_smem + (threadIdx.x >> 5) * smem_per_warp;  // [R][S] running masks
-    uint32_t* sIds = sM + R * ix.S;                                // [QK_ID_CAP]
-    uint32_t* sBits = sIds + QK_ID_CAP;                            // [ceil(K/32)] sparse-stage bitmap
     const uint32_t bw = qk_bitmap_words(ix.K);
     const uint32_t* __restrict__ rows = ix.rows;
 
     if (*(volatile unsigned long long*)&st->err != NO_ERR) return;
     bv_resolve(b);
+    // Query group: P warps answer one query together (P = 1 for large
+    // batches; up to 8 when the batch is too small to fill the grid, so a
+    // lone query's steps and set stage spread over more warps).  group = 0
+    // picks P from the batch size, else P = min(group, warps per block).
+    const unsigned wpb = blockDim.x >> 5;
+    const unsigned Pb = qk_group_size(b.n, group, wpb, group_warps, use_bitmap);
+    if (GROUP != (Pb > 1)) return;  // the other instance serves this batch
+    const unsigned P = GROUP ? Pb : 1u;
+    const unsigned gi = wid / P, gw = wid % P;
+    const bool leader = gw == 0 && lane == 0;
+    // the group's shared state lives in its first warp's region; each warp
+    // keeps its own staging words
+    // (per-warp region: [QK_CTL] control, [R][S] masks, [QK_ID_CAP] staging,
+    // [ceil(K/32)] bitmap when the set stage uses one)
+    uint32_t* lead = qk_smem + (gi * P) * smem_per_warp;
+    uint32_t* ctl = lead;                                                // group control words
+    uint32_t* sM = lead + QK_CTL;                                        // [R][S] running masks
+    uint32_t* sBits = sM + R * ix.S + QK_ID_CAP;                         // set-stage bitmap
+    uint32_t* sIds = qk_smem + wid * smem_per_warp + QK_CTL + R * ix.S;  // this warp's staging
+    volatile unsigned long long* ctl_ticket = reinterpret_cast<volatile unsigned long long*>(ctl);
+    volatile unsigned long long* ctl_start = reinterpret_cast<volatile unsigned long long*>(ctl + 2);
+    volatile uint32_t* ctl_dead = ctl + 4;
+    volatile uint32_t* ctl_cnt = ctl + 8;  // [8] per-warp counts
+
     if (use_bitmap)
-        for (uint32_t w = lane; w < bw; w += 32) sBits[w] = 0;
-    __syncwarp();
+        for (uint32_t w = gw * 32 + lane; w < bw; w += P * 32) sBits[w] = 0;
+    if (P > 1) batch = 1;
+    qk_group_sync(P, gi);
 
     unsigned long long probed = 0, rows_read = 0;
     for (;;) {
-        unsigned long long q0 = 0;
-        if (lane == 0) q0 = atomicAdd(&st->ticket, (unsigned long long)batch);
-        q0 = __shfl_sync(FULL, q0, 0);
+        if (leader) *ctl_ticket = atomicAdd(&st->ticket, (unsigned long long)batch);
+        qk_group_sync(P, gi);
+        const unsigned long long q0 = *ctl_ticket;
+        qk_group_sync(P, gi);
         if (q0 >= b.n) break;
         const unsigned long long q1 = min(q0 + (unsigned long long)batch, (unsigned long long)b.n);
         for (unsigned long long t = q0; t < q1; ++t) {
@@ -121,6 +180,12 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
             const uint64_t e = __ldg(b.offsets + q + 1) - b.off0;
             const uint64_t nkeys = b.seq ? (e - a - b.k + 1) : (e - a);  // >= 1 (validated)
 
+            if (P > 1) {
+                for (uint32_t w = gw * 32 + lane; w < (uint32_t)R * ix.S; w += P * 32) sM[w] = ~0u;
+                if (leader) *ctl_dead = 0;
+                qk_group_sync(P, gi);
+            }
+
             uint32_t M[RMAX][V];
 #pragma unroll
             for (int r = 0; r < RMAX; ++r)
@@ -128,17 +193,20 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                 for (int v = 0; v < V; ++v) M[r][v] = has_words ? ~0u : 0u;
 
             bool alive = true;
-            // step s visits terms s*KPS + g (input order) or g*nsteps + s
-            // (strided: the first step samples the whole query evenly).
-            // With screening, the first step reads table 0 only (phase 0) and
-            // the other tables for the same terms only if the query is still
-            // alive (phase 1); a query holding an absent term usually dies in
-            // phase 0 at eta rows per term instead of R*eta.
+            // Steps: step s visits terms s*KPS + g (input order) or g*nsteps + s
+            // (strided: the first step samples the whole query evenly).  Warp
+            // gw of the group takes steps gw, gw + P, ...  With screening, a
+            // warp's first step reads table 0 only (phase 0) and the other
+            // tables for the same terms only if the query is still alive
+            // (phase 1); a query holding an absent term usually dies in phase
+            // 0 at eta rows per term instead of R*eta.
             const uint64_t nsteps = (nkeys + KPS - 1) / KPS;
+            const uint64_t mine = nsteps > gw ? (nsteps - gw + P - 1) / P : 0;  // steps of this warp
             const bool screen = order >= 2 && R > 1;
-            const uint64_t nphases = nsteps + (screen ? 1 : 0);
+            const uint64_t nphases = mine + ((screen && mine) ? 1 : 0);
             for (uint64_t ph = 0; ph < nphases; ++ph) {
-                const uint64_t s = screen ? (ph == 0 ? 0 : ph - 1) : ph;
+                if (P > 1 && __shfl_sync(FULL, *ctl_dead, 0)) break;  // another warp found an empty table
+                const uint64_t s = gw + (uint64_t)P * (screen ? (ph == 0 ? 0 : ph - 1) : ph);
                 const int rlo = (screen && ph == 1) ? 1 : 0;
                 const int rhi = (screen && ph == 0) ? 1 : R;
                 const uint64_t idx = order ? (uint64_t)grp * nsteps + s : s * KPS + grp;
@@ -200,15 +268,14 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                 }
                 if (nz != rmask) {
                     alive = false;
+                    if (P > 1 && lane == 0) *ctl_dead = 1;
                     break;
                 }
             }
 
-            uint32_t count = 0;
-            unsigned long long start = 0;
-            if (alive) {
-                // stage the masks: row words [w0, w0+V) of table r
-                if (grp == 0 && has_words) {
+            // the query's masks in shared memory: row words [w0, w0+V) of table r
+            if (P == 1) {
+                if (alive && grp == 0 && has_words) {
 #pragma unroll
                     for (int r = 0; r < RMAX; ++r)
                         if (r < R)
@@ -216,23 +283,42 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                             for (int v = 0; v < V; ++v) sM[r * ix.S + w0 + v] = M[r][v];
                 }
                 __syncwarp();
-                // per-table hit-cell counts; the table with the fewest hit cells
-                // gives the sparse stage its candidates
-                uint32_t pc[RMAX];
-                int rstar = 0;
-                uint32_t pmin = 0xffffffffu;
+            } else {
+                // AND of the group's partial masks (a warp that stopped early
+                // holds a superset, which the AND leaves correct)
+                if (alive && mine && grp == 0 && has_words) {
+#pragma unroll
+                    for (int r = 0; r < RMAX; ++r)
+                        if (r < R)
+#pragma unroll
+                            for (int v = 0; v < V; ++v) atomicAnd(sM + r * ix.S + w0 + v, M[r][v]);
+                }
+                qk_group_sync(P, gi);
+                alive = *ctl_dead == 0;
+            }
+
+            uint32_t count = 0;
+            unsigned long long start = 0;
+            // per-table hit-cell counts; the table with the fewest hit cells
+            // gives the sparse stage its candidates
+            uint32_t pc[RMAX];
+            int rstar = 0;
+            uint32_t pmin = 0xffffffffu;
+            if (alive) {
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r) {
                     uint32_t c = 0;
-                    if (r < R && grp == 0 && has_words)
-#pragma unroll
-                        for (int v = 0; v < V; ++v) c += __popc(M[r][v]);
+                    if (r < R)
+                        for (uint32_t w = lane; w < ix.S; w += 32) c += __popc(sM[r * ix.S + w]);
                     pc[r] = (r < R) ? __reduce_add_sync(FULL, c) : 0u;
                     if (r < R && pc[r] < pmin) {
                         pmin = pc[r];
                         rstar = r;
                     }
                 }
+                if (pmin == 0) alive = false;  // the group's AND emptied a table
+            }
+            if (alive) {
                 // A5 strategy (all give the same set): 1 dense scan of every ID,
                 // 2 sparse enumeration of rstar's hit cells, 3 union of the
                 // precomputed member bitmaps of the hit cells (or of the missed
@@ -262,13 +348,13 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                     }
                     stage = (dense <= sparse && dense <= uni) ? 1 : (sparse <= uni ? 2 : 3);
                 }
-                if (lane == 0) atomicAdd(&st->stage_count[use_bitmap ? stage : 0], 1ull);
+                if (leader) atomicAdd(&st->stage_count[use_bitmap ? stage : 0], 1ull);
                 if (use_bitmap) {
                     if (stage == 1) {
                         // dense: one ballot per 32 IDs becomes one bitmap word; four
                         // chunks per iteration so their table loads are in flight together
                         constexpr int DU = 4;
-                        for (uint64_t i0 = 0; i0 < ix.K; i0 += 32 * DU) {
+                        for (uint64_t i0 = (uint64_t)gw * 32 * DU; i0 < ix.K; i0 += (uint64_t)P * 32 * DU) {
                             uint32_t regw[DU];
                             uint4 ph[DU];
 #pragma unroll
@@ -296,8 +382,9 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                         // tested on the other tables.  Hit cells are taken one mask
                         // word (up to 32 cells) at a time; lane j holds cell j's
                         // member range, and the members of all those cells form one
-                        // run of candidates, 128 per iteration, whose IDs and
-                        // partition rows are two independent coalesced loads.
+                        // run of candidates, 128 per warp iteration (the group's
+                        // warps interleave), whose IDs and partition rows are two
+                        // independent coalesced loads.
                         const uint32_t* cellmask = sM + rstar * ix.S;
                         const uint64_t cbase = (uint64_t)rstar * ix.B;
                         for (uint32_t w = 0; w < ix.W; ++w) {
@@ -318,7 +405,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                             const uint32_t total = __shfl_sync(FULL, incl, 31);
                             const uint32_t base = m0 - (incl - cnt);  // list position of candidate u = base + u
                             constexpr int SU = 4;
-                            for (uint32_t u0 = 0; u0 < total; u0 += 32 * SU) {
+                            for (uint32_t u0 = gw * 32 * SU; u0 < total; u0 += P * 32 * SU) {
                                 uint32_t id[SU];
                                 uint4 ph[SU];
 #pragma unroll
@@ -328,8 +415,8 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                                     uint32_t j = 0;
 #pragma unroll
                                     for (uint32_t step = 16; step >= 1; step >>= 1) {
-                                        const uint32_t e = __shfl_sync(FULL, incl, j + step - 1);
-                                        if (e <= u) j += step;
+                                        const uint32_t e2 = __shfl_sync(FULL, incl, j + step - 1);
+                                        if (e2 <= u) j += step;
                                     }
                                     const uint32_t pos = __shfl_sync(FULL, base, j) + u;
                                     const bool v = u < total;
@@ -353,9 +440,10 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                     } else {
                         // union of member bitmaps: G_r = OR of the hit cells' bitmaps
                         // (or NOT of the missed cells' when over half are hit); the
-                        // answer is registered AND every G_r.  The cell lists go to
-                        // shared memory first (warp prefix sums), then each lane ORs
-                        // UW words per cell for UC cells at a time.
+                        // answer is registered AND every G_r.  Each warp lists the
+                        // cells in its own staging words (warp prefix sums), then
+                        // each lane ORs UW words per cell for UC cells at a time;
+                        // the group's warps take interleaved word ranges.
                         uint16_t* list = reinterpret_cast<uint16_t*>(sIds);
                         uint32_t list_off[RMAX + 1];
                         list_off[0] = 0;
@@ -390,7 +478,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                         }
                         __syncwarp();
                         constexpr int UW = 4, UC = 4;
-                        for (uint32_t wb = 0; wb < bw; wb += 32 * UW) {
+                        for (uint32_t wb = gw * 32 * UW; wb < bw; wb += P * 32 * UW) {
                             uint32_t g[UW];
 #pragma unroll
                             for (int u = 0; u < UW; ++u) {
@@ -403,12 +491,12 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                                 const bool comp = pc[r] * 2 > ix.B;
                                 const uint32_t* mb = ix.mem_bits + (uint64_t)r * ix.B * bw;
                                 uint32_t acc[UW] = {0, 0, 0, 0};
-                                for (uint32_t t = list_off[r]; t < list_off[r + 1]; t += UC) {
+                                for (uint32_t t2 = list_off[r]; t2 < list_off[r + 1]; t2 += UC) {
                                     uint32_t v[UC][UW];
 #pragma unroll
                                     for (int c = 0; c < UC; ++c) {
-                                        const bool have = t + c < list_off[r + 1];
-                                        const uint32_t* col = mb + (uint64_t)(have ? list[t + c] : 0) * bw;
+                                        const bool have = t2 + c < list_off[r + 1];
+                                        const uint32_t* col = mb + (uint64_t)(have ? list[t2 + c] : 0) * bw;
 #pragma unroll
                                         for (int u = 0; u < UW; ++u) {
                                             const uint32_t w = wb + 32 * u + lane;
@@ -430,20 +518,40 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                             }
                         }
                     }
-                    __syncwarp();
+                    qk_group_sync(P, gi);  // the bitmap is complete
                     // compaction: ascending IDs from the bitmap, bitmap cleared.
-                    // 32 words (1024 IDs) at a time: lanes expand their word's bits
-                    // into shared memory at their prefix position, then the warp
-                    // copies the run out with coalesced stores.
-                    for (uint32_t w = lane; w < bw; w += 32) count += __popc(sBits[w]);
-                    count = __reduce_add_sync(FULL, count);
-                    if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
-                    start = __shfl_sync(FULL, start, 0);
+                    // Warp gw takes the gw-th contiguous run of 32-word blocks;
+                    // 32 words (1024 IDs) at a time, lanes expand their word's
+                    // bits into shared memory at their prefix position, then the
+                    // warp copies the run out with coalesced stores.
+                    const uint32_t nblk = (bw + 31) / 32;
+                    const uint32_t wlo = (uint32_t)(((uint64_t)nblk * gw / P) * 32);
+                    const uint32_t whi = min(bw, (uint32_t)(((uint64_t)nblk * (gw + 1) / P) * 32));
+                    uint32_t mine_ids = 0;
+                    for (uint32_t w = wlo + lane; w < whi; w += 32) mine_ids += __popc(sBits[w]);
+                    mine_ids = __reduce_add_sync(FULL, mine_ids);
+                    uint32_t before = 0;
+                    if (P == 1) {
+                        count = mine_ids;
+                        if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
+                        start = __shfl_sync(FULL, start, 0);
+                    } else {
+                        if (lane == 0) ctl_cnt[gw] = mine_ids;
+                        qk_group_sync(P, gi);
+                        for (unsigned p2 = 0; p2 < P; ++p2) {
+                            const uint32_t c2 = ctl_cnt[p2];
+                            if (p2 < gw) before += c2;
+                            count += c2;
+                        }
+                        if (leader) *ctl_start = count ? atomicAdd(&st->cursor, (unsigned long long)count) : 0ull;
+                        qk_group_sync(P, gi);
+                        start = *ctl_start;
+                    }
                     const bool write = count && start + count <= o.stage_cap;
-                    uint32_t at = 0;
-                    for (uint32_t w0b = 0; w0b < bw; w0b += 32) {
+                    uint32_t at = before;
+                    for (uint32_t w0b = wlo; w0b < whi; w0b += 32) {
                         const uint32_t w = w0b + lane;
-                        uint32_t bits = (w < bw) ? sBits[w] : 0u;
+                        uint32_t bits = (w < whi) ? sBits[w] : 0u;
                         uint32_t c = __popc(bits);
                         uint32_t incl = c;
 #pragma unroll
@@ -461,7 +569,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                                     bits &= bits - 1;
                                 }
                                 __syncwarp();
-                                for (uint32_t t = lane; t < blk; t += 32) dst[t] = sIds[t];
+                                for (uint32_t t2 = lane; t2 < blk; t2 += 32) dst[t2] = sIds[t2];
                                 __syncwarp();
                             } else {
                                 uint32_t pos = incl - c;
@@ -471,13 +579,14 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                                 }
                             }
                         }
-                        if (w < bw) sBits[w] = 0;
+                        if (w < whi) sBits[w] = 0;
                         at += blk;
                     }
                     __syncwarp();
                 } else {
-                    // ID space too large for a shared-memory bitmap: dense scan,
-                    // survivors staged in shared memory, recounted if they overflow
+                    // ID space too large for a shared-memory bitmap (groups are
+                    // single warps here): dense scan, survivors staged in shared
+                    // memory, recounted if they overflow
                     for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
                         const uint64_t i = i0 + lane;
                         const bool ok = (i < ix.K) && qk_set_passes(ix, sM, i, -1);
@@ -492,7 +601,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                     start = __shfl_sync(FULL, start, 0);
                     if (count && start + count <= o.stage_cap) {
                         if (count <= (uint32_t)QK_ID_CAP) {
-                            for (uint32_t t = lane; t < count; t += 32) o.stage[start + t] = sIds[t];
+                            for (uint32_t t2 = lane; t2 < count; t2 += 32) o.stage[start + t2] = sIds[t2];
                         } else {
                             uint32_t at = 0;
                             for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
@@ -506,10 +615,11 @@ __global__ void __launch_bounds__(QK_THREADS_MAX)
                     }
                 }
             }
-            if (lane == 0) {
+            if (leader) {
                 o.qcount[q] = count;
                 o.qstart[q] = start;
             }
+            qk_group_sync(P, gi);  // shared masks and control words are reused by the next query
         }
     }
     if (lane == 0 && probed) atomicAdd(&st->keys_probed, probed);

@@ -13,23 +13,32 @@
 
 namespace rgb {
 
-const void* QK_CAT(qk_kernel_ptr_, QK_SUFFIX)(int V, int G) {
-#define X(v, g) \
-    if (V == v && G == g) return reinterpret_cast<const void*>(&k_query<v, g, QK_ETA>);
+const void* QK_CAT(qk_kernel_ptr_, QK_SUFFIX)(int V, int G, bool grouped) {
+#define X(v, g)                                                                                   \
+    if (V == v && G == g)                                                                         \
+        return grouped ? reinterpret_cast<const void*>(&k_query<v, g, QK_ETA, true>)              \
+                       : reinterpret_cast<const void*>(&k_query<v, g, QK_ETA, false>);
     QK_VG_LIST(X)
 #undef X
     return nullptr;
 }
 
-cudaError_t QK_CAT(qk_launch_, QK_SUFFIX)(int V, int G, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                                          const IndexView& ix, const HashParams& hp, const BatchView& b,
-                                          const QueryOut& o, int set_stage, int batch, uint32_t smem_per_warp,
-                                          int use_bitmap, int order, int load_kind, DevStatus* st) {
-#define X(v, g)                                                                                        \
-    if (V == v && G == g) {                                                                            \
-        k_query<v, g, QK_ETA><<<grid, block, smem, s>>>(ix, hp, b, o, set_stage, batch, smem_per_warp, \
-                                                        use_bitmap, order, load_kind, st);             \
-        return cudaGetLastError();                                                                     \
+cudaError_t QK_CAT(qk_launch_, QK_SUFFIX)(int V, int G, bool grouped, dim3 grid, dim3 block, size_t smem,
+                                          cudaStream_t s, const IndexView& ix, const HashParams& hp,
+                                          const BatchView& b, const QueryOut& o, int set_stage, int batch,
+                                          uint32_t smem_per_warp, int use_bitmap, int order, int load_kind, int group,
+                                          unsigned long long group_warps, DevStatus* st) {
+#define X(v, g)                                                                                              \
+    if (V == v && G == g) {                                                                                  \
+        if (grouped)                                                                                         \
+            k_query<v, g, QK_ETA, true><<<grid, block, smem, s>>>(ix, hp, b, o, set_stage, batch,            \
+                                                                  smem_per_warp, use_bitmap, order,          \
+                                                                  load_kind, group, group_warps, st);        \
+        else                                                                                                 \
+            k_query<v, g, QK_ETA, false><<<grid, block, smem, s>>>(ix, hp, b, o, set_stage, batch,           \
+                                                                   smem_per_warp, use_bitmap, order,         \
+                                                                   load_kind, group, group_warps, st);       \
+        return cudaGetLastError();                                                                           \
     }
     QK_VG_LIST(X)
 #undef X

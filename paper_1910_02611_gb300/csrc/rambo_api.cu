@@ -268,6 +268,7 @@ void default_config(rambo* h) {
     h->cfg.l2_fetch_bytes = 0;
     h->cfg.cluster = 0;
     h->cfg.row_load = 0;
+    h->cfg.warps_per_query = 0;
 }
 
 int decode_err(rambo* h, unsigned long long e) {
@@ -402,6 +403,7 @@ int resolve_tuning(rambo* h, uint64_t n, int& use_bitmap, QueryTuning& t) {
     t.set_stage = (int)h->cfg.set_stage;
     t.order = (int)h->cfg.visit_order;
     t.load_kind = (int)h->cfg.row_load;
+    t.group = (int)h->cfg.warps_per_query;
     use_bitmap = (h->mem_off && t.set_stage != 1 && (h->K + 31) / 32 <= 4096) ? 1 : 0;
     const size_t spw_bytes = (size_t)query_smem_words_per_warp(h->R, h->S, h->K, use_bitmap) * 4;
     int per_sm = 0;
@@ -415,7 +417,7 @@ int resolve_tuning(rambo* h, uint64_t n, int& use_bitmap, QueryTuning& t) {
             int nb_of[4] = {0, 0, 0, 0}, best = 0;
             for (int i = 0; i < 4; ++i) {
                 const int w = 8 >> i;
-                nb_of[i] = query_max_blocks_per_sm(t.V, t.G, h->eta, w, spw_bytes * (size_t)w);
+                nb_of[i] = query_max_blocks_per_sm(t.V, t.G, h->eta, false, w, spw_bytes * (size_t)w);
                 if (nb_of[i] * w > best) best = nb_of[i] * w;
             }
             if (best < 1) return RAMBO_EINVAL;
@@ -430,7 +432,8 @@ int resolve_tuning(rambo* h, uint64_t n, int& use_bitmap, QueryTuning& t) {
         t.warps_per_block = h->auto_wpb;
         per_sm = h->auto_per_sm;
     } else {
-        per_sm = query_max_blocks_per_sm(t.V, t.G, h->eta, t.warps_per_block, spw_bytes * (size_t)t.warps_per_block);
+        per_sm = query_max_blocks_per_sm(t.V, t.G, h->eta, false, t.warps_per_block,
+                                         spw_bytes * (size_t)t.warps_per_block);
     }
     if (per_sm < 1) return RAMBO_EINVAL;
     if (h->cfg.blocks_per_sm && (int)h->cfg.blocks_per_sm < per_sm) per_sm = (int)h->cfg.blocks_per_sm;
@@ -439,6 +442,20 @@ int resolve_tuning(rambo* h, uint64_t n, int& use_bitmap, QueryTuning& t) {
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     t.blocks = (int)blocks;
+    // grouped instance (several warps per query): up to one block a query
+    t.blocks_group = 0;
+    t.group_warps = 0;
+    if (use_bitmap && t.group != 1 && t.warps_per_block > 1) {
+        int per_sm_g = query_max_blocks_per_sm(t.V, t.G, h->eta, true, t.warps_per_block,
+                                               spw_bytes * (size_t)t.warps_per_block);
+        if (h->cfg.blocks_per_sm && (int)h->cfg.blocks_per_sm < per_sm_g) per_sm_g = (int)h->cfg.blocks_per_sm;
+        uint64_t bg = (uint64_t)per_sm_g * h->num_sms;
+        if (bg > n) bg = n;
+        if (bg >= 1) {
+            t.blocks_group = (int)bg;
+            t.group_warps = bg * (uint64_t)t.warps_per_block;
+        }
+    }
     uint64_t warps = blocks * t.warps_per_block;
     uint64_t batch = n / (warps * 32);
     if (batch < 1) batch = 1;
@@ -905,6 +922,9 @@ int rambo_set_query_config(rambo_t* h, const rambo_query_config_t* cfg) {
     if (cfg->set_stage == 2 && !h->mem_off) return RAMBO_EINVAL;
     if (cfg->set_stage == 3 && !h->mem_bits) return RAMBO_EINVAL;
     if (cfg->visit_order > 2 || cfg->cluster > 1 || cfg->row_load > 5) return RAMBO_EINVAL;
+    if (cfg->warps_per_query != 0 && cfg->warps_per_query != 1 && cfg->warps_per_query != 2 &&
+        cfg->warps_per_query != 4 && cfg->warps_per_query != 8)
+        return RAMBO_EINVAL;
     if (cfg->l2_fetch_bytes && cfg->l2_fetch_bytes != 32 && cfg->l2_fetch_bytes != 64 && cfg->l2_fetch_bytes != 128)
         return RAMBO_EINVAL;
     h->cfg = *cfg;
@@ -930,6 +950,7 @@ int rambo_list_query_configs(const rambo_t* h, rambo_query_config_t* out, int ca
                 out[n].l2_fetch_bytes = 0;
                 out[n].cluster = 0;
                 out[n].row_load = 0;
+                out[n].warps_per_query = 0;
             }
             ++n;
         }
@@ -983,6 +1004,7 @@ int rambo_autotune(rambo_t* h, int kind, const void* data, const uint64_t* offse
             cfg.visit_order = order;
             cfg.set_stage = keep.set_stage;
             cfg.row_load = keep.row_load;
+            cfg.warps_per_query = keep.warps_per_query;
             if (rambo_set_query_config(h, &cfg) != RAMBO_OK) continue;
             float t_min = -1.0f;
             for (int r = 0; r < reps; ++r) {

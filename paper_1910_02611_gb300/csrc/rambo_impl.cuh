@@ -218,6 +218,9 @@ struct QueryTuning {
     int batch;             // queries taken per ticket
     int order;             // 0 input order, 1 strided, 2 strided + table-0 screening
     int load_kind;         // cache operator of the row loads (see ld_row1)
+    int group;             // warps per query: 0 = from the batch size on the device, else at most this
+    int blocks_group;      // grid of the grouped instance (0: not used)
+    unsigned long long group_warps;  // its warps, the budget the group size is chosen against
 };
 
 // ---------------------------------------------------------------------------
@@ -261,9 +264,11 @@ cudaError_t launch_insert(const IndexView& ix, const HashParams& hp, const Batch
 // k_query*.cu
 bool query_config_supported(int V, int G, uint32_t S);
 uint32_t query_smem_words_per_warp(uint32_t R, uint32_t S, uint64_t K, int use_bitmap);
-int query_max_blocks_per_sm(int V, int G, uint32_t eta, int warps_per_block, size_t smem_per_block);
+int query_max_blocks_per_sm(int V, int G, uint32_t eta, bool grouped, int warps_per_block, size_t smem_per_block);
+unsigned query_group_size(uint64_t n, int group, unsigned wpb, uint64_t group_warps, int use_bitmap);
 cudaError_t launch_query(const IndexView& ix, const HashParams& hp, const BatchView& b, const QueryOut& o,
-                         const QueryTuning& t, int use_bitmap, DevStatus* st, cudaStream_t s);
+                         const QueryTuning& t, int use_bitmap, DevStatus* st, cudaStream_t s,
+                         int* n_launched = nullptr);
 
 // k_query_one.cu: the plain one-query-per-launch kernel
 cudaError_t launch_query_one(const IndexView& ix, const HashParams& hp, int seq, const uint8_t* bases,

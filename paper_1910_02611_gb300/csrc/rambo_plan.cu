@@ -126,7 +126,11 @@ int plan_capture(rambo_plan* p) {
         n_launch += 2;
     }
     QueryOut o{p->stage, p->max_ids, p->qstart, p->qcount};
-    if (e == cudaSuccess) e = launch_query(ix, hp, b, o, t, use_bitmap, p->st, s), ++n_launch;
+    if (e == cudaSuccess) {
+        int nq = 0;
+        e = launch_query(ix, hp, b, o, t, use_bitmap, p->st, s, &nq);
+        n_launch += nq;
+    }
     if (e == cudaSuccess) e = launch_scan_counts(p->qcount, p->max_q, p->id_off, p->scan_tmp, scan_words, s, p->d_desc);
     n_launch += 3;
     if (e == cudaSuccess) e = launch_gather(o, p->id_off, p->max_q, p->ids, p->st, s, p->d_desc, p->max_ids);

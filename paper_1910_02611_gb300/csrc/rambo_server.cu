@@ -19,6 +19,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -46,7 +47,8 @@ struct Op {
 
 struct Done {
     int status = 0;
-    std::vector<uint32_t> ids;
+    std::shared_ptr<const std::vector<uint32_t>> buf;  // the batch's answers, shared by its requests
+    uint64_t off = 0, len = 0;                          // this request's run in buf
     uint64_t latency_ns = 0;
 };
 
@@ -94,6 +96,10 @@ void finish_slot(rambo_server* S, Slot& sl) {
     const uint64_t* off = nullptr;
     uint64_t n_ids = 0;
     const int rc = rambo_plan_wait(sl.plan, 1, &ids, &off, &n_ids, sl.stream);
+    // one copy of the batch's answers out of the plan's pinned buffer, outside
+    // the lock; the batch's requests share it
+    std::shared_ptr<const std::vector<uint32_t>> buf;
+    if (rc == RAMBO_OK) buf = std::make_shared<const std::vector<uint32_t>>(ids, ids + n_ids);
     const auto now = Clock::now();
     if (rc == RAMBO_ENOSPC && sl.members.size() > 1) {
         // the batch's answers did not fit the slot: requeue its queries at the
@@ -115,7 +121,11 @@ void finish_slot(rambo_server* S, Slot& sl) {
             const Op& op = sl.members[i];
             Done d;
             d.status = rc;
-            if (rc == RAMBO_OK) d.ids.assign(ids + off[i], ids + off[i + 1]);
+            if (rc == RAMBO_OK) {
+                d.buf = buf;
+                d.off = off[i];
+                d.len = off[i + 1] - off[i];
+            }
             d.latency_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(now - op.t_submit).count();
             S->latencies.push_back(d.latency_ns);
             S->keys_done += op_keys(op);
@@ -339,16 +349,20 @@ int rambo_server_result(rambo_server_t* S, uint64_t ticket, int wait, uint32_t* 
         it = S->done.find(ticket);
     }
     Done& d = it->second;
-    if (n_ids) *n_ids = d.ids.size();
+    if (n_ids) *n_ids = d.len;
     if (latency_ns) *latency_ns = d.latency_ns;
     if (d.status != RAMBO_OK) {
         const int rc = d.status;
         S->done.erase(it);
         return rc;
     }
-    if (d.ids.size() > cap) return RAMBO_ENOSPC;  // kept: ask again with a larger buffer
-    if (!d.ids.empty()) std::memcpy(ids, d.ids.data(), d.ids.size() * 4);
+    if (d.len > cap) return RAMBO_ENOSPC;  // kept: ask again with a larger buffer
+    // take the request's share of the batch buffer, then copy without the lock
+    const std::shared_ptr<const std::vector<uint32_t>> buf = d.buf;
+    const uint64_t off = d.off, len = d.len;
     S->done.erase(it);
+    lk.unlock();
+    if (len) std::memcpy(ids, buf->data() + off, len * 4);
     return RAMBO_OK;
 }
 

@@ -44,7 +44,7 @@ class ServerStats(C.Structure):
 class QueryConfig(C.Structure):
     _fields_ = [("lanes_per_key", _u32), ("words_per_lane", _u32), ("warps_per_block", _u32),
                 ("blocks_per_sm", _u32), ("set_stage", _u32), ("visit_order", _u32), ("l2_fetch_bytes", _u32),
-                ("cluster", _u32), ("row_load", _u32)]
+                ("cluster", _u32), ("row_load", _u32), ("warps_per_query", _u32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -620,7 +620,7 @@ class Server:
                 continue
             if rc:
                 raise RamboError(rc, "rambo_server_result")
-            return buf[: n.value].copy(), int(lat.value)
+            return buf[: n.value], int(lat.value)
 
     def drain(self) -> None:
         load_library().rambo_server_drain(self._s)

@@ -27,7 +27,7 @@ def _w(name, scale, **kw):
 WORKLOADS = {
     "tiny_full": lambda: _w("tiny", 1.0),
     "genome_small": lambda: _w("genome", 0.02, m=1 << 18),
-    "uneven_small": lambda: _w("uneven", 0.004, m=1 << 16, n_queries=3000),
+    "uneven_small": lambda: _w("uneven", 0.004, m=1 << 16, n_queries=750_000),  # 3000 queries at this scale
     "document_small": lambda: _w("document", 0.01, m=1 << 16),
 }
 
@@ -70,6 +70,15 @@ def test_queries_identical_every_kernel_config(pair):
                 for order in (0, 1, 2):
                     g.set_config(**{**cfg, "set_stage": stage, "visit_order": order})
                     assert_query_equal(g, o, q, k=w.k)
+        # queries shared by 2, 4 or 8 warps of a block, forced, then chosen
+        # from the batch size (small batches take whole blocks per query)
+        for wpq in (1, 2, 4, 8):
+            for stage in (0, 1, 2, 3):
+                g.set_config(**{**base, "warps_per_query": wpq, "set_stage": stage})
+                assert_query_equal(g, o, q, k=w.k)
+        g.set_config(**base)
+        for n in (1, 3, 37):
+            assert_query_equal(g, o, w.queries.subset(np.arange(min(n, len(w.queries)))), k=w.k)
         g.set_config(**{**base, "l2_fetch_bytes": 32})
         assert_query_equal(g, o, q, k=w.k)
         g.set_config(**{**base, "cluster": 1})

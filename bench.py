@@ -692,7 +692,8 @@ def run_serving(args):
                       "queries": st["queries"], "batches": st["batches"],
                       "mean_batch": st["queries"] / max(st["batches"], 1),
                       "keys_per_s": keys / wall, "queries_per_s": st["queries"] / wall,
-                      "p50_ms": st["p50_ns"] / 1e6, "p99_ms": st["p99_ns"] / 1e6, "max_ms": st["max_ns"] / 1e6})
+                      "p50_ms": st["p50_ns"] / 1e6, "p99_ms": st["p99_ns"] / 1e6, "max_ms": st["max_ns"] / 1e6,
+                      "worker_s": {k: st[k + "_ns"] / 1e9 for k in ("admit", "finish", "insert", "idle")}})
         sel = rng.choice(len(kinds), 64, replace=False)
         check_sample.append((sel, kinds, items, results))
     clocks = sampler.stop()

@@ -279,6 +279,9 @@ typedef struct rambo_server_stats {
     uint64_t queries, batches, inserts, keys;
     double seconds;              /* first launch to last completion */
     uint64_t p50_ns, p99_ns, max_ns;  /* submit-to-result latency of queries */
+    /* worker thread time: staging and launching batches, waiting for and
+     * copying out finished batches, running inserts, idle */
+    uint64_t admit_ns, finish_ns, insert_ns, idle_ns;
 } rambo_server_stats_t;
 int rambo_server_create(rambo_t *h, const rambo_server_config_t *cfg, rambo_server_t **out);
 /* Queues one query (kind 0: n_items uint64 keys; kind 1: n_items ASCII

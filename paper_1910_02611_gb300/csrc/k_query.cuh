@@ -109,22 +109,17 @@ __host__ __device__ inline unsigned qk_group_size(uint64_t n, int group, unsigne
     return P;
 }
 
-// Two instances per tiling: GROUP = false is the one-warp-per-query kernel
-// (P = 1 folded in at compile time), GROUP = true serves batches that give a
-// query more than one warp.  A launch whose instance does not match the
-// batch's group size returns at once, so a captured graph holds both and the
-// batch size, read on the device, picks.  Tilings whose row words in flight
-// (RMAX * ETA * V) fit in 64 registers are held to 128 registers a thread, so
-// two full blocks share an SM; wider ones keep every register they need.
-template <int V, int G, int ETA, bool GROUP>
-__global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1)
-    k_query(IndexView ix, HashParams hp, BatchView b, QueryOut o, int set_stage, int batch,
-            uint32_t smem_per_warp, int use_bitmap, int order, int load_kind, int group,
-            unsigned long long group_warps, DevStatus* st) {
+// One warp per query (batches that fill the grid).  Kept apart from the
+// grouped form below: sharing one body with it cost this path 10-25% in
+// register allocation on the document and uneven workloads.
+template <int V, int G, int ETA>
+__device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashParams& hp, const BatchView& b,
+                                                const QueryOut& o, int set_stage, int batch,
+                                                uint32_t smem_per_warp, int use_bitmap, int order, int load_kind,
+                                                DevStatus* st) {
     extern __shared__ uint32_t qk_smem[];
     constexpr int KPS = 32 / G;  // terms per warp step
     const unsigned lane = threadIdx.x & 31;
-    const unsigned wid = threadIdx.x >> 5;
     const unsigned grp = lane / G;
     const unsigned slot = lane % G;
     const uint32_t w0 = slot * V;
@@ -132,46 +127,21 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
     const int R = (int)ix.R;
     const int eta = (int)ix.eta;
     const uint32_t rmask = (1u << R) - 1u;
+    uint32_t* sM = qk_smem + (threadIdx.x >> 5) * smem_per_warp + QK_CTL;  // [R][S] running masks
+    uint32_t* sIds = sM + R * ix.S;                                // [QK_ID_CAP]
+    uint32_t* sBits = sIds + QK_ID_CAP;                            // [ceil(K/32)] sparse-stage bitmap
     const uint32_t bw = qk_bitmap_words(ix.K);
     const uint32_t* __restrict__ rows = ix.rows;
 
-    if (*(volatile unsigned long long*)&st->err != NO_ERR) return;
-    bv_resolve(b);
-    // Query group: P warps answer one query together (P = 1 for large
-    // batches; up to 8 when the batch is too small to fill the grid, so a
-    // lone query's steps and set stage spread over more warps).  group = 0
-    // picks P from the batch size, else P = min(group, warps per block).
-    const unsigned wpb = blockDim.x >> 5;
-    const unsigned Pb = qk_group_size(b.n, group, wpb, group_warps, use_bitmap);
-    if (GROUP != (Pb > 1)) return;  // the other instance serves this batch
-    const unsigned P = GROUP ? Pb : 1u;
-    const unsigned gi = wid / P, gw = wid % P;
-    const bool leader = gw == 0 && lane == 0;
-    // the group's shared state lives in its first warp's region; each warp
-    // keeps its own staging words
-    // (per-warp region: [QK_CTL] control, [R][S] masks, [QK_ID_CAP] staging,
-    // [ceil(K/32)] bitmap when the set stage uses one)
-    uint32_t* lead = qk_smem + (gi * P) * smem_per_warp;
-    uint32_t* ctl = lead;                                                // group control words
-    uint32_t* sM = lead + QK_CTL;                                        // [R][S] running masks
-    uint32_t* sBits = sM + R * ix.S + QK_ID_CAP;                         // set-stage bitmap
-    uint32_t* sIds = qk_smem + wid * smem_per_warp + QK_CTL + R * ix.S;  // this warp's staging
-    volatile unsigned long long* ctl_ticket = reinterpret_cast<volatile unsigned long long*>(ctl);
-    volatile unsigned long long* ctl_start = reinterpret_cast<volatile unsigned long long*>(ctl + 2);
-    volatile uint32_t* ctl_dead = ctl + 4;
-    volatile uint32_t* ctl_cnt = ctl + 8;  // [8] per-warp counts
-
     if (use_bitmap)
-        for (uint32_t w = gw * 32 + lane; w < bw; w += P * 32) sBits[w] = 0;
-    if (P > 1) batch = 1;
-    qk_group_sync(P, gi);
+        for (uint32_t w = lane; w < bw; w += 32) sBits[w] = 0;
+    __syncwarp();
 
     unsigned long long probed = 0, rows_read = 0;
     for (;;) {
-        if (leader) *ctl_ticket = atomicAdd(&st->ticket, (unsigned long long)batch);
-        qk_group_sync(P, gi);
-        const unsigned long long q0 = *ctl_ticket;
-        qk_group_sync(P, gi);
+        unsigned long long q0 = 0;
+        if (lane == 0) q0 = atomicAdd(&st->ticket, (unsigned long long)batch);
+        q0 = __shfl_sync(FULL, q0, 0);
         if (q0 >= b.n) break;
         const unsigned long long q1 = min(q0 + (unsigned long long)batch, (unsigned long long)b.n);
         for (unsigned long long t = q0; t < q1; ++t) {
@@ -180,12 +150,6 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
             const uint64_t e = __ldg(b.offsets + q + 1) - b.off0;
             const uint64_t nkeys = b.seq ? (e - a - b.k + 1) : (e - a);  // >= 1 (validated)
 
-            if (P > 1) {
-                for (uint32_t w = gw * 32 + lane; w < (uint32_t)R * ix.S; w += P * 32) sM[w] = ~0u;
-                if (leader) *ctl_dead = 0;
-                qk_group_sync(P, gi);
-            }
-
             uint32_t M[RMAX][V];
 #pragma unroll
             for (int r = 0; r < RMAX; ++r)
@@ -193,20 +157,17 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                 for (int v = 0; v < V; ++v) M[r][v] = has_words ? ~0u : 0u;
 
             bool alive = true;
-            // Steps: step s visits terms s*KPS + g (input order) or g*nsteps + s
-            // (strided: the first step samples the whole query evenly).  Warp
-            // gw of the group takes steps gw, gw + P, ...  With screening, a
-            // warp's first step reads table 0 only (phase 0) and the other
-            // tables for the same terms only if the query is still alive
-            // (phase 1); a query holding an absent term usually dies in phase
-            // 0 at eta rows per term instead of R*eta.
+            // step s visits terms s*KPS + g (input order) or g*nsteps + s
+            // (strided: the first step samples the whole query evenly).
+            // With screening, the first step reads table 0 only (phase 0) and
+            // the other tables for the same terms only if the query is still
+            // alive (phase 1); a query holding an absent term usually dies in
+            // phase 0 at eta rows per term instead of R*eta.
             const uint64_t nsteps = (nkeys + KPS - 1) / KPS;
-            const uint64_t mine = nsteps > gw ? (nsteps - gw + P - 1) / P : 0;  // steps of this warp
             const bool screen = order >= 2 && R > 1;
-            const uint64_t nphases = mine + ((screen && mine) ? 1 : 0);
+            const uint64_t nphases = nsteps + (screen ? 1 : 0);
             for (uint64_t ph = 0; ph < nphases; ++ph) {
-                if (P > 1 && __shfl_sync(FULL, *ctl_dead, 0)) break;  // another warp found an empty table
-                const uint64_t s = gw + (uint64_t)P * (screen ? (ph == 0 ? 0 : ph - 1) : ph);
+                const uint64_t s = screen ? (ph == 0 ? 0 : ph - 1) : ph;
                 const int rlo = (screen && ph == 1) ? 1 : 0;
                 const int rhi = (screen && ph == 0) ? 1 : R;
                 const uint64_t idx = order ? (uint64_t)grp * nsteps + s : s * KPS + grp;
@@ -268,14 +229,15 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                 }
                 if (nz != rmask) {
                     alive = false;
-                    if (P > 1 && lane == 0) *ctl_dead = 1;
                     break;
                 }
             }
 
-            // the query's masks in shared memory: row words [w0, w0+V) of table r
-            if (P == 1) {
-                if (alive && grp == 0 && has_words) {
+            uint32_t count = 0;
+            unsigned long long start = 0;
+            if (alive) {
+                // stage the masks: row words [w0, w0+V) of table r
+                if (grp == 0 && has_words) {
 #pragma unroll
                     for (int r = 0; r < RMAX; ++r)
                         if (r < R)
@@ -283,42 +245,23 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                             for (int v = 0; v < V; ++v) sM[r * ix.S + w0 + v] = M[r][v];
                 }
                 __syncwarp();
-            } else {
-                // AND of the group's partial masks (a warp that stopped early
-                // holds a superset, which the AND leaves correct)
-                if (alive && mine && grp == 0 && has_words) {
-#pragma unroll
-                    for (int r = 0; r < RMAX; ++r)
-                        if (r < R)
-#pragma unroll
-                            for (int v = 0; v < V; ++v) atomicAnd(sM + r * ix.S + w0 + v, M[r][v]);
-                }
-                qk_group_sync(P, gi);
-                alive = *ctl_dead == 0;
-            }
-
-            uint32_t count = 0;
-            unsigned long long start = 0;
-            // per-table hit-cell counts; the table with the fewest hit cells
-            // gives the sparse stage its candidates
-            uint32_t pc[RMAX];
-            int rstar = 0;
-            uint32_t pmin = 0xffffffffu;
-            if (alive) {
+                // per-table hit-cell counts; the table with the fewest hit cells
+                // gives the sparse stage its candidates
+                uint32_t pc[RMAX];
+                int rstar = 0;
+                uint32_t pmin = 0xffffffffu;
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r) {
                     uint32_t c = 0;
-                    if (r < R)
-                        for (uint32_t w = lane; w < ix.S; w += 32) c += __popc(sM[r * ix.S + w]);
+                    if (r < R && grp == 0 && has_words)
+#pragma unroll
+                        for (int v = 0; v < V; ++v) c += __popc(M[r][v]);
                     pc[r] = (r < R) ? __reduce_add_sync(FULL, c) : 0u;
                     if (r < R && pc[r] < pmin) {
                         pmin = pc[r];
                         rstar = r;
                     }
                 }
-                if (pmin == 0) alive = false;  // the group's AND emptied a table
-            }
-            if (alive) {
                 // A5 strategy (all give the same set): 1 dense scan of every ID,
                 // 2 sparse enumeration of rstar's hit cells, 3 union of the
                 // precomputed member bitmaps of the hit cells (or of the missed
@@ -348,13 +291,13 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                     }
                     stage = (dense <= sparse && dense <= uni) ? 1 : (sparse <= uni ? 2 : 3);
                 }
-                if (leader) atomicAdd(&st->stage_count[use_bitmap ? stage : 0], 1ull);
+                if (lane == 0) atomicAdd(&st->stage_count[use_bitmap ? stage : 0], 1ull);
                 if (use_bitmap) {
                     if (stage == 1) {
                         // dense: one ballot per 32 IDs becomes one bitmap word; four
                         // chunks per iteration so their table loads are in flight together
                         constexpr int DU = 4;
-                        for (uint64_t i0 = (uint64_t)gw * 32 * DU; i0 < ix.K; i0 += (uint64_t)P * 32 * DU) {
+                        for (uint64_t i0 = 0; i0 < ix.K; i0 += 32 * DU) {
                             uint32_t regw[DU];
                             uint4 ph[DU];
 #pragma unroll
@@ -382,9 +325,8 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                         // tested on the other tables.  Hit cells are taken one mask
                         // word (up to 32 cells) at a time; lane j holds cell j's
                         // member range, and the members of all those cells form one
-                        // run of candidates, 128 per warp iteration (the group's
-                        // warps interleave), whose IDs and partition rows are two
-                        // independent coalesced loads.
+                        // run of candidates, 128 per iteration, whose IDs and
+                        // partition rows are two independent coalesced loads.
                         const uint32_t* cellmask = sM + rstar * ix.S;
                         const uint64_t cbase = (uint64_t)rstar * ix.B;
                         for (uint32_t w = 0; w < ix.W; ++w) {
@@ -405,7 +347,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                             const uint32_t total = __shfl_sync(FULL, incl, 31);
                             const uint32_t base = m0 - (incl - cnt);  // list position of candidate u = base + u
                             constexpr int SU = 4;
-                            for (uint32_t u0 = gw * 32 * SU; u0 < total; u0 += P * 32 * SU) {
+                            for (uint32_t u0 = 0; u0 < total; u0 += 32 * SU) {
                                 uint32_t id[SU];
                                 uint4 ph[SU];
 #pragma unroll
@@ -415,8 +357,8 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                                     uint32_t j = 0;
 #pragma unroll
                                     for (uint32_t step = 16; step >= 1; step >>= 1) {
-                                        const uint32_t e2 = __shfl_sync(FULL, incl, j + step - 1);
-                                        if (e2 <= u) j += step;
+                                        const uint32_t e = __shfl_sync(FULL, incl, j + step - 1);
+                                        if (e <= u) j += step;
                                     }
                                     const uint32_t pos = __shfl_sync(FULL, base, j) + u;
                                     const bool v = u < total;
@@ -440,10 +382,9 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                     } else {
                         // union of member bitmaps: G_r = OR of the hit cells' bitmaps
                         // (or NOT of the missed cells' when over half are hit); the
-                        // answer is registered AND every G_r.  Each warp lists the
-                        // cells in its own staging words (warp prefix sums), then
-                        // each lane ORs UW words per cell for UC cells at a time;
-                        // the group's warps take interleaved word ranges.
+                        // answer is registered AND every G_r.  The cell lists go to
+                        // shared memory first (warp prefix sums), then each lane ORs
+                        // UW words per cell for UC cells at a time.
                         uint16_t* list = reinterpret_cast<uint16_t*>(sIds);
                         uint32_t list_off[RMAX + 1];
                         list_off[0] = 0;
@@ -478,7 +419,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                         }
                         __syncwarp();
                         constexpr int UW = 4, UC = 4;
-                        for (uint32_t wb = gw * 32 * UW; wb < bw; wb += P * 32 * UW) {
+                        for (uint32_t wb = 0; wb < bw; wb += 32 * UW) {
                             uint32_t g[UW];
 #pragma unroll
                             for (int u = 0; u < UW; ++u) {
@@ -491,12 +432,12 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                                 const bool comp = pc[r] * 2 > ix.B;
                                 const uint32_t* mb = ix.mem_bits + (uint64_t)r * ix.B * bw;
                                 uint32_t acc[UW] = {0, 0, 0, 0};
-                                for (uint32_t t2 = list_off[r]; t2 < list_off[r + 1]; t2 += UC) {
+                                for (uint32_t t = list_off[r]; t < list_off[r + 1]; t += UC) {
                                     uint32_t v[UC][UW];
 #pragma unroll
                                     for (int c = 0; c < UC; ++c) {
-                                        const bool have = t2 + c < list_off[r + 1];
-                                        const uint32_t* col = mb + (uint64_t)(have ? list[t2 + c] : 0) * bw;
+                                        const bool have = t + c < list_off[r + 1];
+                                        const uint32_t* col = mb + (uint64_t)(have ? list[t + c] : 0) * bw;
 #pragma unroll
                                         for (int u = 0; u < UW; ++u) {
                                             const uint32_t w = wb + 32 * u + lane;
@@ -518,40 +459,20 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                             }
                         }
                     }
-                    qk_group_sync(P, gi);  // the bitmap is complete
+                    __syncwarp();
                     // compaction: ascending IDs from the bitmap, bitmap cleared.
-                    // Warp gw takes the gw-th contiguous run of 32-word blocks;
-                    // 32 words (1024 IDs) at a time, lanes expand their word's
-                    // bits into shared memory at their prefix position, then the
-                    // warp copies the run out with coalesced stores.
-                    const uint32_t nblk = (bw + 31) / 32;
-                    const uint32_t wlo = (uint32_t)(((uint64_t)nblk * gw / P) * 32);
-                    const uint32_t whi = min(bw, (uint32_t)(((uint64_t)nblk * (gw + 1) / P) * 32));
-                    uint32_t mine_ids = 0;
-                    for (uint32_t w = wlo + lane; w < whi; w += 32) mine_ids += __popc(sBits[w]);
-                    mine_ids = __reduce_add_sync(FULL, mine_ids);
-                    uint32_t before = 0;
-                    if (P == 1) {
-                        count = mine_ids;
-                        if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
-                        start = __shfl_sync(FULL, start, 0);
-                    } else {
-                        if (lane == 0) ctl_cnt[gw] = mine_ids;
-                        qk_group_sync(P, gi);
-                        for (unsigned p2 = 0; p2 < P; ++p2) {
-                            const uint32_t c2 = ctl_cnt[p2];
-                            if (p2 < gw) before += c2;
-                            count += c2;
-                        }
-                        if (leader) *ctl_start = count ? atomicAdd(&st->cursor, (unsigned long long)count) : 0ull;
-                        qk_group_sync(P, gi);
-                        start = *ctl_start;
-                    }
+                    // 32 words (1024 IDs) at a time: lanes expand their word's bits
+                    // into shared memory at their prefix position, then the warp
+                    // copies the run out with coalesced stores.
+                    for (uint32_t w = lane; w < bw; w += 32) count += __popc(sBits[w]);
+                    count = __reduce_add_sync(FULL, count);
+                    if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
+                    start = __shfl_sync(FULL, start, 0);
                     const bool write = count && start + count <= o.stage_cap;
-                    uint32_t at = before;
-                    for (uint32_t w0b = wlo; w0b < whi; w0b += 32) {
+                    uint32_t at = 0;
+                    for (uint32_t w0b = 0; w0b < bw; w0b += 32) {
                         const uint32_t w = w0b + lane;
-                        uint32_t bits = (w < whi) ? sBits[w] : 0u;
+                        uint32_t bits = (w < bw) ? sBits[w] : 0u;
                         uint32_t c = __popc(bits);
                         uint32_t incl = c;
 #pragma unroll
@@ -569,7 +490,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                                     bits &= bits - 1;
                                 }
                                 __syncwarp();
-                                for (uint32_t t2 = lane; t2 < blk; t2 += 32) dst[t2] = sIds[t2];
+                                for (uint32_t t = lane; t < blk; t += 32) dst[t] = sIds[t];
                                 __syncwarp();
                             } else {
                                 uint32_t pos = incl - c;
@@ -579,14 +500,13 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                                 }
                             }
                         }
-                        if (w < whi) sBits[w] = 0;
+                        if (w < bw) sBits[w] = 0;
                         at += blk;
                     }
                     __syncwarp();
                 } else {
-                    // ID space too large for a shared-memory bitmap (groups are
-                    // single warps here): dense scan, survivors staged in shared
-                    // memory, recounted if they overflow
+                    // ID space too large for a shared-memory bitmap: dense scan,
+                    // survivors staged in shared memory, recounted if they overflow
                     for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
                         const uint64_t i = i0 + lane;
                         const bool ok = (i < ix.K) && qk_set_passes(ix, sM, i, -1);
@@ -601,7 +521,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                     start = __shfl_sync(FULL, start, 0);
                     if (count && start + count <= o.stage_cap) {
                         if (count <= (uint32_t)QK_ID_CAP) {
-                            for (uint32_t t2 = lane; t2 < count; t2 += 32) o.stage[start + t2] = sIds[t2];
+                            for (uint32_t t = lane; t < count; t += 32) o.stage[start + t] = sIds[t];
                         } else {
                             uint32_t at = 0;
                             for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
@@ -615,15 +535,538 @@ __global__ void __launch_bounds__(QK_THREADS_MAX, (RMAX * ETA * V <= 64) ? 2 : 1
                     }
                 }
             }
-            if (leader) {
+            if (lane == 0) {
                 o.qcount[q] = count;
                 o.qstart[q] = start;
             }
-            qk_group_sync(P, gi);  // shared masks and control words are reused by the next query
         }
     }
     if (lane == 0 && probed) atomicAdd(&st->keys_probed, probed);
     if (lane == 0 && rows_read) atomicAdd(&st->rows_read, rows_read);
+}
+
+// Two instances per tiling: GROUP = false is the one-warp-per-query kernel
+// (P = 1 folded in at compile time), GROUP = true serves batches that give a
+// query more than one warp.  A launch whose instance does not match the
+// batch's group size returns at once, so a captured graph holds both and the
+// batch size, read on the device, picks.  Tilings whose row words in flight
+// (RMAX * ETA * V) fit in 64 registers are held to 128 registers a thread, so
+// two full blocks share an SM; wider ones keep every register they need, and
+// so does the one-warp V = 4, ETA = 2 tiling, measured 11% faster that way on
+// the uneven workload (16-byte rows, 8 tables).
+template <int V, int G, int ETA, bool GROUP>
+__global__ void __launch_bounds__(QK_THREADS_MAX,
+                                  (RMAX * ETA * V <= 64 && !(V == 4 && ETA == 2 && !GROUP)) ? 2 : 1)
+    k_query(IndexView ix, HashParams hp, BatchView b, QueryOut o, int set_stage, int batch,
+            uint32_t smem_per_warp, int use_bitmap, int order, int load_kind, int group,
+            unsigned long long group_warps, DevStatus* st) {
+    extern __shared__ uint32_t qk_smem[];
+    constexpr int KPS = 32 / G;  // terms per warp step
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned wid = threadIdx.x >> 5;
+    const unsigned grp = lane / G;
+    const unsigned slot = lane % G;
+    const uint32_t w0 = slot * V;
+    const bool has_words = w0 < ix.S;
+    const int R = (int)ix.R;
+    const int eta = (int)ix.eta;
+    const uint32_t rmask = (1u << R) - 1u;
+    const uint32_t bw = qk_bitmap_words(ix.K);
+    const uint32_t* __restrict__ rows = ix.rows;
+
+    if (*(volatile unsigned long long*)&st->err != NO_ERR) return;
+    bv_resolve(b);
+    // Query group: P warps answer one query together (P = 1 for large
+    // batches; up to 8 when the batch is too small to fill the grid, so a
+    // lone query's steps and set stage spread over more warps).  group = 0
+    // picks P from the batch size, else P = min(group, warps per block).
+    const unsigned wpb = blockDim.x >> 5;
+    const unsigned Pb = qk_group_size(b.n, group, wpb, group_warps, use_bitmap);
+    if (GROUP != (Pb > 1)) return;  // the other instance serves this batch
+    if constexpr (!GROUP) {
+        qk_warp_queries<V, G, ETA>(ix, hp, b, o, set_stage, batch, smem_per_warp, use_bitmap, order, load_kind, st);
+    } else {
+        const unsigned P = Pb;
+        const unsigned gi = wid / P, gw = wid % P;
+        const bool leader = gw == 0 && lane == 0;
+        // the group's shared state lives in its first warp's region; each warp
+        // keeps its own staging words
+        // (per-warp region: [QK_CTL] control, [R][S] masks, [QK_ID_CAP] staging,
+        // [ceil(K/32)] bitmap when the set stage uses one)
+        uint32_t* lead = qk_smem + (gi * P) * smem_per_warp;
+        uint32_t* ctl = lead;                                                // group control words
+        uint32_t* sM = lead + QK_CTL;                                        // [R][S] running masks
+        uint32_t* sBits = sM + R * ix.S + QK_ID_CAP;                         // set-stage bitmap
+        uint32_t* sIds = qk_smem + wid * smem_per_warp + QK_CTL + R * ix.S;  // this warp's staging
+        volatile unsigned long long* ctl_ticket = reinterpret_cast<volatile unsigned long long*>(ctl);
+        volatile unsigned long long* ctl_start = reinterpret_cast<volatile unsigned long long*>(ctl + 2);
+        volatile uint32_t* ctl_dead = ctl + 4;
+        volatile uint32_t* ctl_cnt = ctl + 8;  // [8] per-warp counts
+
+        if (use_bitmap)
+            for (uint32_t w = gw * 32 + lane; w < bw; w += P * 32) sBits[w] = 0;
+        if (P > 1) batch = 1;
+        qk_group_sync(P, gi);
+
+        unsigned long long probed = 0, rows_read = 0;
+        for (;;) {
+            if (leader) *ctl_ticket = atomicAdd(&st->ticket, (unsigned long long)batch);
+            qk_group_sync(P, gi);
+            const unsigned long long q0 = *ctl_ticket;
+            qk_group_sync(P, gi);
+            if (q0 >= b.n) break;
+            const unsigned long long q1 = min(q0 + (unsigned long long)batch, (unsigned long long)b.n);
+            for (unsigned long long t = q0; t < q1; ++t) {
+                const unsigned long long q = b.perm ? (unsigned long long)__ldg(b.perm + t) : t;
+                const uint64_t a = __ldg(b.offsets + q) - b.off0;
+                const uint64_t e = __ldg(b.offsets + q + 1) - b.off0;
+                const uint64_t nkeys = b.seq ? (e - a - b.k + 1) : (e - a);  // >= 1 (validated)
+
+                if (P > 1) {
+                    for (uint32_t w = gw * 32 + lane; w < (uint32_t)R * ix.S; w += P * 32) sM[w] = ~0u;
+                    if (leader) *ctl_dead = 0;
+                    qk_group_sync(P, gi);
+                }
+
+                uint32_t M[RMAX][V];
+    #pragma unroll
+                for (int r = 0; r < RMAX; ++r)
+    #pragma unroll
+                    for (int v = 0; v < V; ++v) M[r][v] = has_words ? ~0u : 0u;
+
+                bool alive = true;
+                // Steps: step s visits terms s*KPS + g (input order) or g*nsteps + s
+                // (strided: the first step samples the whole query evenly).  Warp
+                // gw of the group takes steps gw, gw + P, ...  With screening, a
+                // warp's first step reads table 0 only (phase 0) and the other
+                // tables for the same terms only if the query is still alive
+                // (phase 1); a query holding an absent term usually dies in phase
+                // 0 at eta rows per term instead of R*eta.
+                const uint64_t nsteps = (nkeys + KPS - 1) / KPS;
+                const uint64_t mine = nsteps > gw ? (nsteps - gw + P - 1) / P : 0;  // steps of this warp
+                const bool screen = order >= 2 && R > 1;
+                const uint64_t nphases = mine + ((screen && mine) ? 1 : 0);
+                for (uint64_t ph = 0; ph < nphases; ++ph) {
+                    if (P > 1 && __shfl_sync(FULL, *ctl_dead, 0)) break;  // another warp found an empty table
+                    const uint64_t s = gw + (uint64_t)P * (screen ? (ph == 0 ? 0 : ph - 1) : ph);
+                    const int rlo = (screen && ph == 1) ? 1 : 0;
+                    const int rhi = (screen && ph == 0) ? 1 : R;
+                    const uint64_t idx = order ? (uint64_t)grp * nsteps + s : s * KPS + grp;
+                    const bool act = idx < nkeys;
+                    uint64_t key = 0;
+                    if (act) {
+                        if (b.seq) {
+                            key = kmer_at(b.packed, a + idx, b.k);
+                            if (b.canon) key = canonical_kmer(key, b.k);
+                        } else {
+                            key = __ldg(b.keys + a + idx);
+                        }
+                    }
+                    const uint64_t y = mix64(key);
+                    // A3: issue every row read of this step, then combine
+                    uint32_t val[RMAX][ETA][V];
+                    const bool ld = act && has_words;
+    #pragma unroll
+                    for (int r = 0; r < RMAX; ++r) {
+                        if (r >= rlo && r < rhi && ld) {
+                            const uint32_t* rb = rows + (uint64_t)r * ix.m * ix.S + w0;
+    #pragma unroll
+                            for (int j = 0; j < ETA; ++j) {
+                                if (j < eta) {
+                                    const uint64_t pos = (hp.s[r][j] * y) >> ix.shift;
+                                    qk_load<V>(rb + pos * ix.S, val[r][j], load_kind);
+                                }
+                            }
+                        }
+                    }
+                    uint32_t nz = 0;
+    #pragma unroll
+                    for (int r = 0; r < RMAX; ++r) {
+                        if (r < R) {
+                            uint32_t any = 0;
+                            const bool probed_r = r >= rlo && r < rhi;
+    #pragma unroll
+                            for (int v = 0; v < V; ++v) {
+                                uint32_t x = ~0u;
+                                if (ld && probed_r) {
+    #pragma unroll
+                                    for (int j = 0; j < ETA; ++j)
+                                        if (j < eta) x &= val[r][j][v];
+                                }
+                                if (probed_r) {
+                                    x = qk_and_groups<G>(x);  // A4: across this step's terms
+                                    M[r][v] &= x;             // and into the query's masks
+                                }
+                                any |= M[r][v];
+                            }
+                            if (any) nz |= 1u << r;
+                        }
+                    }
+                    nz = __reduce_or_sync(FULL, nz);
+                    {
+                        const unsigned nact = __popc(__ballot_sync(FULL, act && slot == 0));
+                        if (!(screen && ph == 1)) probed += nact;  // the screened terms were counted in phase 0
+                        rows_read += (unsigned long long)nact * (unsigned)(rhi - rlo) * (unsigned)eta;
+                    }
+                    if (nz != rmask) {
+                        alive = false;
+                        if (P > 1 && lane == 0) *ctl_dead = 1;
+                        break;
+                    }
+                }
+
+                // the query's masks in shared memory: row words [w0, w0+V) of table r
+                if (P == 1) {
+                    if (alive && grp == 0 && has_words) {
+    #pragma unroll
+                        for (int r = 0; r < RMAX; ++r)
+                            if (r < R)
+    #pragma unroll
+                                for (int v = 0; v < V; ++v) sM[r * ix.S + w0 + v] = M[r][v];
+                    }
+                    __syncwarp();
+                } else {
+                    // AND of the group's partial masks (a warp that stopped early
+                    // holds a superset, which the AND leaves correct)
+                    if (alive && mine && grp == 0 && has_words) {
+    #pragma unroll
+                        for (int r = 0; r < RMAX; ++r)
+                            if (r < R)
+    #pragma unroll
+                                for (int v = 0; v < V; ++v) atomicAnd(sM + r * ix.S + w0 + v, M[r][v]);
+                    }
+                    qk_group_sync(P, gi);
+                    alive = *ctl_dead == 0;
+                }
+
+                uint32_t count = 0;
+                unsigned long long start = 0;
+                // per-table hit-cell counts; the table with the fewest hit cells
+                // gives the sparse stage its candidates
+                uint32_t pc[RMAX];
+                int rstar = 0;
+                uint32_t pmin = 0xffffffffu;
+                if (alive) {
+    #pragma unroll
+                    for (int r = 0; r < RMAX; ++r) {
+                        uint32_t c = 0;
+                        if (r < R)
+                            for (uint32_t w = lane; w < ix.S; w += 32) c += __popc(sM[r * ix.S + w]);
+                        pc[r] = (r < R) ? __reduce_add_sync(FULL, c) : 0u;
+                        if (r < R && pc[r] < pmin) {
+                            pmin = pc[r];
+                            rstar = r;
+                        }
+                    }
+                    if (pmin == 0) alive = false;  // the group's AND emptied a table
+                }
+                if (alive) {
+                    // A5 strategy (all give the same set): 1 dense scan of every ID,
+                    // 2 sparse enumeration of rstar's hit cells, 3 union of the
+                    // precomputed member bitmaps of the hit cells (or of the missed
+                    // cells, complemented, when a table is mostly hit).  Auto picks
+                    // the fewest warp-wide operations (Lemma 4.4's candidate term).
+                    int stage = set_stage;
+                    if (!use_bitmap) stage = 1;
+                    uint32_t list_total = 0;
+    #pragma unroll
+                    for (int r = 0; r < RMAX; ++r)
+                        if (r < R) list_total += pc[r] * 2 > ix.B ? ix.B - pc[r] : pc[r];
+                    const bool union_ok = ix.mem_bits && list_total <= 2u * QK_ID_CAP;
+                    if (stage == 3 && !union_ok) stage = 1;
+                    if (stage == 0) {
+                        const uint64_t kw = (ix.K + 31) / 32;
+                        const uint64_t dense = kw * (uint64_t)(R + 2);
+                        const uint64_t sparse = ((uint64_t)pmin * (ix.K / ix.B + 1) / 32 + pmin) * (uint64_t)(R + 3) + kw / 16;
+                        uint64_t uni = ~0ull;
+                        if (union_ok) {
+                            uni = kw / 32 + 1;
+    #pragma unroll
+                            for (int r = 0; r < RMAX; ++r) {
+                                if (r >= R) continue;
+                                const uint32_t cr = pc[r] < ix.B - pc[r] ? pc[r] : ix.B - pc[r];
+                                uni += (uint64_t)cr * (kw / 32 + 1);
+                            }
+                        }
+                        stage = (dense <= sparse && dense <= uni) ? 1 : (sparse <= uni ? 2 : 3);
+                    }
+                    if (leader) atomicAdd(&st->stage_count[use_bitmap ? stage : 0], 1ull);
+                    if (use_bitmap) {
+                        if (stage == 1) {
+                            // dense: one ballot per 32 IDs becomes one bitmap word; four
+                            // chunks per iteration so their table loads are in flight together
+                            constexpr int DU = 4;
+                            for (uint64_t i0 = (uint64_t)gw * 32 * DU; i0 < ix.K; i0 += (uint64_t)P * 32 * DU) {
+                                uint32_t regw[DU];
+                                uint4 ph[DU];
+    #pragma unroll
+                                for (int u = 0; u < DU; ++u) {
+                                    const uint64_t i = i0 + 32 * u + lane;
+                                    regw[u] = i < ix.K ? __ldg(ix.reg + (i >> 5)) : 0u;
+                                    ph[u] = i < ix.K ? __ldg(reinterpret_cast<const uint4*>(ix.phi) + i) : make_uint4(0, 0, 0, 0);
+                                }
+    #pragma unroll
+                                for (int u = 0; u < DU; ++u) {
+                                    const uint64_t i = i0 + 32 * u + lane;
+                                    bool ok = i < ix.K && ((regw[u] >> (i & 31)) & 1u);
+                                    const uint32_t cell[8] = {ph[u].x & 0xffffu, ph[u].x >> 16, ph[u].y & 0xffffu,
+                                                              ph[u].y >> 16,     ph[u].z & 0xffffu, ph[u].z >> 16,
+                                                              ph[u].w & 0xffffu, ph[u].w >> 16};
+    #pragma unroll
+                                    for (int r = 0; r < RMAX; ++r)
+                                        if (r < R) ok &= (sM[r * ix.S + (cell[r] >> 5)] >> (cell[r] & 31)) & 1u;
+                                    const unsigned bal = __ballot_sync(FULL, ok);
+                                    if (lane == 0 && i0 + 32 * u < ix.K) sBits[(i0 >> 5) + u] = bal;
+                                }
+                            }
+                        } else if (stage == 2) {
+                            // sparse: the registered members of table rstar's hit cells,
+                            // tested on the other tables.  Hit cells are taken one mask
+                            // word (up to 32 cells) at a time; lane j holds cell j's
+                            // member range, and the members of all those cells form one
+                            // run of candidates, 128 per warp iteration (the group's
+                            // warps interleave), whose IDs and partition rows are two
+                            // independent coalesced loads.
+                            const uint32_t* cellmask = sM + rstar * ix.S;
+                            const uint64_t cbase = (uint64_t)rstar * ix.B;
+                            for (uint32_t w = 0; w < ix.W; ++w) {
+                                const uint32_t hits = cellmask[w];
+                                if (!hits) continue;
+                                uint32_t m0 = 0, cnt = 0;
+                                if ((hits >> lane) & 1u) {
+                                    const uint64_t cell = cbase + w * 32 + lane;
+                                    m0 = (uint32_t)__ldg(ix.mem_off + cell);
+                                    cnt = (uint32_t)__ldg(ix.mem_off + cell + 1) - m0;
+                                }
+                                uint32_t incl = cnt;
+    #pragma unroll
+                                for (int off = 1; off < 32; off <<= 1) {
+                                    const uint32_t y = __shfl_up_sync(FULL, incl, off);
+                                    if (lane >= (unsigned)off) incl += y;
+                                }
+                                const uint32_t total = __shfl_sync(FULL, incl, 31);
+                                const uint32_t base = m0 - (incl - cnt);  // list position of candidate u = base + u
+                                constexpr int SU = 4;
+                                for (uint32_t u0 = gw * 32 * SU; u0 < total; u0 += P * 32 * SU) {
+                                    uint32_t id[SU];
+                                    uint4 ph[SU];
+    #pragma unroll
+                                    for (int c = 0; c < SU; ++c) {
+                                        const uint32_t u = u0 + 32 * c + lane;
+                                        // owner lane: the first lane whose inclusive count exceeds u
+                                        uint32_t j = 0;
+    #pragma unroll
+                                        for (uint32_t step = 16; step >= 1; step >>= 1) {
+                                            const uint32_t e2 = __shfl_sync(FULL, incl, j + step - 1);
+                                            if (e2 <= u) j += step;
+                                        }
+                                        const uint32_t pos = __shfl_sync(FULL, base, j) + u;
+                                        const bool v = u < total;
+                                        id[c] = v ? __ldg(ix.mem_ids + pos) : 0xffffffffu;
+                                        ph[c] = v ? __ldg(ix.mem_phi + pos) : make_uint4(0, 0, 0, 0);
+                                    }
+    #pragma unroll
+                                    for (int c = 0; c < SU; ++c) {
+                                        if (id[c] == 0xffffffffu) continue;
+                                        const uint32_t cl[8] = {ph[c].x & 0xffffu, ph[c].x >> 16, ph[c].y & 0xffffu,
+                                                                ph[c].y >> 16,     ph[c].z & 0xffffu, ph[c].z >> 16,
+                                                                ph[c].w & 0xffffu, ph[c].w >> 16};
+                                        bool ok = true;
+    #pragma unroll
+                                        for (int r = 0; r < RMAX; ++r)
+                                            if (r < R && r != rstar) ok &= (sM[r * ix.S + (cl[r] >> 5)] >> (cl[r] & 31)) & 1u;
+                                        if (ok) atomicOr(sBits + (id[c] >> 5), 1u << (id[c] & 31));
+                                    }
+                                }
+                            }
+                        } else {
+                            // union of member bitmaps: G_r = OR of the hit cells' bitmaps
+                            // (or NOT of the missed cells' when over half are hit); the
+                            // answer is registered AND every G_r.  Each warp lists the
+                            // cells in its own staging words (warp prefix sums), then
+                            // each lane ORs UW words per cell for UC cells at a time;
+                            // the group's warps take interleaved word ranges.
+                            uint16_t* list = reinterpret_cast<uint16_t*>(sIds);
+                            uint32_t list_off[RMAX + 1];
+                            list_off[0] = 0;
+    #pragma unroll
+                            for (int r = 0; r < RMAX; ++r) {
+                                uint32_t n_r = 0;
+                                if (r < R) {
+                                    const bool comp = pc[r] * 2 > ix.B;
+                                    for (uint32_t c0 = 0; c0 < ix.W; c0 += 32) {
+                                        const uint32_t cw = c0 + lane;
+                                        uint32_t bits = 0;
+                                        if (cw < ix.W) {
+                                            bits = comp ? ~sM[r * ix.S + cw] : sM[r * ix.S + cw];
+                                            if (cw == ix.W - 1 && (ix.B & 31)) bits &= (1u << (ix.B & 31)) - 1u;
+                                        }
+                                        const uint32_t c = __popc(bits);
+                                        uint32_t incl = c;
+    #pragma unroll
+                                        for (int off = 1; off < 32; off <<= 1) {
+                                            const uint32_t y = __shfl_up_sync(FULL, incl, off);
+                                            if (lane >= (unsigned)off) incl += y;
+                                        }
+                                        uint32_t pos = list_off[r] + n_r + incl - c;
+                                        while (bits) {
+                                            list[pos++] = (uint16_t)(cw * 32 + (__ffs(bits) - 1));
+                                            bits &= bits - 1;
+                                        }
+                                        n_r += __shfl_sync(FULL, incl, 31);
+                                    }
+                                }
+                                list_off[r + 1] = list_off[r] + n_r;
+                            }
+                            __syncwarp();
+                            constexpr int UW = 4, UC = 4;
+                            for (uint32_t wb = gw * 32 * UW; wb < bw; wb += P * 32 * UW) {
+                                uint32_t g[UW];
+    #pragma unroll
+                                for (int u = 0; u < UW; ++u) {
+                                    const uint32_t w = wb + 32 * u + lane;
+                                    g[u] = w < bw ? __ldg(ix.reg + w) : 0u;
+                                }
+    #pragma unroll
+                                for (int r = 0; r < RMAX; ++r) {
+                                    if (r >= R) continue;
+                                    const bool comp = pc[r] * 2 > ix.B;
+                                    const uint32_t* mb = ix.mem_bits + (uint64_t)r * ix.B * bw;
+                                    uint32_t acc[UW] = {0, 0, 0, 0};
+                                    for (uint32_t t2 = list_off[r]; t2 < list_off[r + 1]; t2 += UC) {
+                                        uint32_t v[UC][UW];
+    #pragma unroll
+                                        for (int c = 0; c < UC; ++c) {
+                                            const bool have = t2 + c < list_off[r + 1];
+                                            const uint32_t* col = mb + (uint64_t)(have ? list[t2 + c] : 0) * bw;
+    #pragma unroll
+                                            for (int u = 0; u < UW; ++u) {
+                                                const uint32_t w = wb + 32 * u + lane;
+                                                v[c][u] = (have && w < bw) ? __ldg(col + w) : 0u;
+                                            }
+                                        }
+    #pragma unroll
+                                        for (int c = 0; c < UC; ++c)
+    #pragma unroll
+                                            for (int u = 0; u < UW; ++u) acc[u] |= v[c][u];
+                                    }
+    #pragma unroll
+                                    for (int u = 0; u < UW; ++u) g[u] &= comp ? ~acc[u] : acc[u];
+                                }
+    #pragma unroll
+                                for (int u = 0; u < UW; ++u) {
+                                    const uint32_t w = wb + 32 * u + lane;
+                                    if (w < bw) sBits[w] = g[u];
+                                }
+                            }
+                        }
+                        qk_group_sync(P, gi);  // the bitmap is complete
+                        // compaction: ascending IDs from the bitmap, bitmap cleared.
+                        // Warp gw takes the gw-th contiguous run of 32-word blocks;
+                        // 32 words (1024 IDs) at a time, lanes expand their word's
+                        // bits into shared memory at their prefix position, then the
+                        // warp copies the run out with coalesced stores.
+                        const uint32_t nblk = (bw + 31) / 32;
+                        const uint32_t wlo = (uint32_t)(((uint64_t)nblk * gw / P) * 32);
+                        const uint32_t whi = min(bw, (uint32_t)(((uint64_t)nblk * (gw + 1) / P) * 32));
+                        uint32_t mine_ids = 0;
+                        for (uint32_t w = wlo + lane; w < whi; w += 32) mine_ids += __popc(sBits[w]);
+                        mine_ids = __reduce_add_sync(FULL, mine_ids);
+                        uint32_t before = 0;
+                        if (P == 1) {
+                            count = mine_ids;
+                            if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
+                            start = __shfl_sync(FULL, start, 0);
+                        } else {
+                            if (lane == 0) ctl_cnt[gw] = mine_ids;
+                            qk_group_sync(P, gi);
+                            for (unsigned p2 = 0; p2 < P; ++p2) {
+                                const uint32_t c2 = ctl_cnt[p2];
+                                if (p2 < gw) before += c2;
+                                count += c2;
+                            }
+                            if (leader) *ctl_start = count ? atomicAdd(&st->cursor, (unsigned long long)count) : 0ull;
+                            qk_group_sync(P, gi);
+                            start = *ctl_start;
+                        }
+                        const bool write = count && start + count <= o.stage_cap;
+                        uint32_t at = before;
+                        for (uint32_t w0b = wlo; w0b < whi; w0b += 32) {
+                            const uint32_t w = w0b + lane;
+                            uint32_t bits = (w < whi) ? sBits[w] : 0u;
+                            uint32_t c = __popc(bits);
+                            uint32_t incl = c;
+    #pragma unroll
+                            for (int off = 1; off < 32; off <<= 1) {
+                                uint32_t y = __shfl_up_sync(FULL, incl, off);
+                                if (lane >= (unsigned)off) incl += y;
+                            }
+                            const uint32_t blk = __shfl_sync(FULL, incl, 31);
+                            if (write && blk) {
+                                uint32_t* dst = o.stage + start + at;
+                                if (blk <= (uint32_t)QK_ID_CAP) {
+                                    uint32_t pos = incl - c;
+                                    while (bits) {
+                                        sIds[pos++] = w * 32 + (__ffs(bits) - 1);
+                                        bits &= bits - 1;
+                                    }
+                                    __syncwarp();
+                                    for (uint32_t t2 = lane; t2 < blk; t2 += 32) dst[t2] = sIds[t2];
+                                    __syncwarp();
+                                } else {
+                                    uint32_t pos = incl - c;
+                                    while (bits) {
+                                        dst[pos++] = w * 32 + (__ffs(bits) - 1);
+                                        bits &= bits - 1;
+                                    }
+                                }
+                            }
+                            if (w < whi) sBits[w] = 0;
+                            at += blk;
+                        }
+                        __syncwarp();
+                    } else {
+                        // ID space too large for a shared-memory bitmap (groups are
+                        // single warps here): dense scan, survivors staged in shared
+                        // memory, recounted if they overflow
+                        for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
+                            const uint64_t i = i0 + lane;
+                            const bool ok = (i < ix.K) && qk_set_passes(ix, sM, i, -1);
+                            const unsigned bal = __ballot_sync(FULL, ok);
+                            if (bal) {
+                                const unsigned pre = __popc(bal & ((1u << lane) - 1u));
+                                if (ok && count + pre < (uint32_t)QK_ID_CAP) sIds[count + pre] = (uint32_t)i;
+                                count += __popc(bal);
+                            }
+                        }
+                        if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
+                        start = __shfl_sync(FULL, start, 0);
+                        if (count && start + count <= o.stage_cap) {
+                            if (count <= (uint32_t)QK_ID_CAP) {
+                                for (uint32_t t2 = lane; t2 < count; t2 += 32) o.stage[start + t2] = sIds[t2];
+                            } else {
+                                uint32_t at = 0;
+                                for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
+                                    const uint64_t i = i0 + lane;
+                                    const bool ok = (i < ix.K) && qk_set_passes(ix, sM, i, -1);
+                                    const unsigned bal = __ballot_sync(FULL, ok);
+                                    if (ok) o.stage[start + at + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
+                                    at += __popc(bal);
+                                }
+                            }
+                        }
+                    }
+                }
+                if (leader) {
+                    o.qcount[q] = count;
+                    o.qstart[q] = start;
+                }
+                qk_group_sync(P, gi);  // shared masks and control words are reused by the next query
+            }
+        }
+        if (lane == 0 && probed) atomicAdd(&st->keys_probed, probed);
+        if (lane == 0 && rows_read) atomicAdd(&st->rows_read, rows_read);
+    }
 }
 
 }  // namespace rgb

@@ -319,11 +319,20 @@ int stage_batch(rambo* h, const void* data, size_t elem, const uint64_t* offsets
         } else {
             b.set_ids = nullptr;
         }
-        RK(h->in_data.ensure(total * elem + 16));
-        if (total)
-            CK(cudaMemcpyAsync(h->in_data.p, static_cast<const uint8_t*>(data) + off0 * elem, total * elem,
-                               cudaMemcpyHostToDevice, s));
-        *d_data = h->in_data.p;
+        const uint8_t* src = static_cast<const uint8_t*>(data) + off0 * elem;
+        // Bases in pinned host memory are read in place by the packing
+        // kernel (one streaming pass over NVLink-C2C) instead of being copied
+        // first; keys, small batches and pageable memory take the copy.
+        cudaPointerAttributes pa{};
+        if (elem == 1 && total >= (1u << 20) && cudaPointerGetAttributes(&pa, src) == cudaSuccess &&
+            pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+            *d_data = pa.devicePointer;
+        } else {
+            cudaGetLastError();
+            RK(h->in_data.ensure(total * elem + 16));
+            if (total) CK(cudaMemcpyAsync(h->in_data.p, src, total * elem, cudaMemcpyHostToDevice, s));
+            *d_data = h->in_data.p;
+        }
     }
     return RAMBO_OK;
 }

@@ -19,6 +19,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -45,16 +46,71 @@ struct Op {
     Clock::time_point t_submit;
 };
 
+// Pinned host buffers for finished batches' large answers, reused across
+// batches: a batch's IDs are copied from the device straight into one, its
+// requests share it, and it returns to the pool when the last of them is
+// collected.  Small answers go through the slot's pinned staging into heap
+// memory instead, so uncollected small results hold no pinned memory.
+struct PinnedPool {
+    std::mutex mu;
+    std::multimap<size_t, void*> free_bufs;  // capacity -> buffer
+    std::vector<void*> all;
+    ~PinnedPool() {
+        for (void* p : all) cudaFreeHost(p);
+    }
+    void* get(size_t bytes, size_t* cap) {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            auto it = free_bufs.lower_bound(bytes);
+            if (it != free_bufs.end()) {
+                void* p = it->second;
+                *cap = it->first;
+                free_bufs.erase(it);
+                return p;
+            }
+        }
+        size_t c = 1u << 20;
+        while (c < bytes) c <<= 1;
+        void* p = nullptr;
+        if (cudaMallocHost(&p, c) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        all.push_back(p);
+        *cap = c;
+        return p;
+    }
+    void put(void* p, size_t cap) {
+        std::lock_guard<std::mutex> lk(mu);
+        free_bufs.emplace(cap, p);
+    }
+};
+
+constexpr size_t SMALL_RESULT_BYTES = 256u << 10;
+
+struct ResultBuf {
+    std::shared_ptr<PinnedPool> pool;
+    void* mem = nullptr;  // pooled pinned buffer (large answers)
+    size_t cap = 0;
+    std::vector<uint8_t> heap;  // small answers
+    const uint32_t* ids = nullptr;
+    ~ResultBuf() {
+        if (mem) pool->put(mem, cap);
+    }
+};
+
 struct Done {
     int status = 0;
-    std::shared_ptr<const std::vector<uint32_t>> buf;  // the batch's answers, shared by its requests
-    uint64_t off = 0, len = 0;                          // this request's run in buf
+    std::shared_ptr<const ResultBuf> buf;  // the batch's answers, shared by its requests
+    uint64_t off = 0, len = 0;             // this request's run in buf
     uint64_t latency_ns = 0;
 };
 
 struct Slot {
     rambo_plan_t* plan = nullptr;
     cudaStream_t stream = nullptr;
+    void* staging = nullptr;  // pinned, SMALL_RESULT_BYTES
     int kind = 1;
     bool busy = false;
     std::vector<Op> members;
@@ -76,8 +132,10 @@ struct rambo_server {
     uint64_t next_ticket = 1, next_seq = 1, outstanding = 0;
     bool stop = false;
     std::thread worker;
+    std::shared_ptr<PinnedPool> pool = std::make_shared<PinnedPool>();
     // statistics
     uint64_t n_queries = 0, n_batches = 0, n_inserts = 0, keys_done = 0;
+    std::atomic<uint64_t> admit_ns{0}, finish_ns{0}, insert_ns{0}, idle_ns{0};
     std::vector<uint64_t> latencies;
     Clock::time_point t_first{}, t_last{};
     bool any = false;
@@ -91,15 +149,47 @@ uint64_t op_keys(const Op& op) {
     return op.items >= k ? op.items - k + 1 : 0;
 }
 
+uint64_t ns_since(Clock::time_point t0) {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - t0).count();
+}
+
 void finish_slot(rambo_server* S, Slot& sl) {
-    const uint32_t* ids = nullptr;
-    const uint64_t* off = nullptr;
+    const auto t0 = Clock::now();
+    const uint32_t* d_ids = nullptr;
+    const uint64_t* d_off = nullptr;
     uint64_t n_ids = 0;
-    const int rc = rambo_plan_wait(sl.plan, 1, &ids, &off, &n_ids, sl.stream);
-    // one copy of the batch's answers out of the plan's pinned buffer, outside
-    // the lock; the batch's requests share it
-    std::shared_ptr<const std::vector<uint32_t>> buf;
-    if (rc == RAMBO_OK) buf = std::make_shared<const std::vector<uint32_t>>(ids, ids + n_ids);
+    int rc = rambo_plan_wait(sl.plan, 0, &d_ids, &d_off, &n_ids, sl.stream);
+    // the batch's offsets and IDs go from the device into one pooled pinned
+    // buffer, which the batch's requests share
+    const uint64_t nq = sl.members.size();
+    std::shared_ptr<ResultBuf> buf;
+    const uint64_t* off = nullptr;
+    if (rc == RAMBO_OK) {
+        buf = std::make_shared<ResultBuf>();
+        buf->pool = S->pool;
+        const size_t off_bytes = (nq + 1) * 8, bytes = off_bytes + n_ids * 4;
+        const bool small = bytes <= SMALL_RESULT_BYTES;
+        void* dst = small ? sl.staging : (buf->mem = S->pool->get(bytes, &buf->cap));
+        if (!dst) {
+            rc = RAMBO_ENOMEM;
+        } else {
+            uint8_t* base = static_cast<uint8_t*>(dst);
+            bool ok = cudaMemcpyAsync(base, d_off, off_bytes, cudaMemcpyDeviceToHost, sl.stream) == cudaSuccess;
+            if (ok && n_ids)
+                ok = cudaMemcpyAsync(base + off_bytes, d_ids, n_ids * 4, cudaMemcpyDeviceToHost, sl.stream) ==
+                     cudaSuccess;
+            ok = ok && cudaStreamSynchronize(sl.stream) == cudaSuccess;
+            if (!ok) {
+                cudaGetLastError();
+                rc = RAMBO_ECUDA;
+            } else if (small) {
+                buf->heap.assign(base, base + bytes);
+                base = buf->heap.data();
+            }
+            off = reinterpret_cast<const uint64_t*>(base);
+            buf->ids = reinterpret_cast<const uint32_t*>(base + off_bytes);
+        }
+    }
     const auto now = Clock::now();
     if (rc == RAMBO_ENOSPC && sl.members.size() > 1) {
         // the batch's answers did not fit the slot: requeue its queries at the
@@ -113,6 +203,7 @@ void finish_slot(rambo_server* S, Slot& sl) {
         sl.members.clear();
         sl.busy = false;
         S->cv_work.notify_one();
+        S->finish_ns += ns_since(t0);
         return;
     }
     {
@@ -139,6 +230,7 @@ void finish_slot(rambo_server* S, Slot& sl) {
     sl.members.clear();
     sl.busy = false;
     S->cv_done.notify_all();
+    S->finish_ns += ns_since(t0);
 }
 
 // Takes queued queries of the slot's kind that precede every pending insert
@@ -218,6 +310,7 @@ void worker_main(rambo_server* S) {
                 Op op = std::move(S->ins.front());
                 S->ins.pop_front();
                 lk.unlock();
+                const auto t_ins = Clock::now();
                 int rc;
                 if (op.kind == 0)
                     rc = rambo_insert_batch(S->h, op.set_ids.data(), reinterpret_cast<const uint64_t*>(op.data.data()),
@@ -225,6 +318,7 @@ void worker_main(rambo_server* S) {
                 else
                     rc = rambo_insert_seq_batch(S->h, op.set_ids.data(), op.data.data(), op.offsets.data(),
                                                 op.set_ids.size(), op.k, 0, S->ins_stream);
+                S->insert_ns += ns_since(t_ins);
                 lk.lock();
                 Done d;
                 d.status = rc;
@@ -238,9 +332,17 @@ void worker_main(rambo_server* S) {
                 did = true;
             }
         }
+        const auto t_adm = Clock::now();
+        bool launched = false;
         for (auto& sl : S->slots)
-            if (!sl.busy && admit(S, sl)) did = true;
-        if (!did) S->cv_work.wait_for(lk, idle);
+            if (!sl.busy && admit(S, sl)) launched = true;
+        if (launched) S->admit_ns += ns_since(t_adm);
+        did |= launched;
+        if (!did) {
+            const auto t_idle = Clock::now();
+            S->cv_work.wait_for(lk, idle);
+            S->idle_ns += ns_since(t_idle);
+        }
     }
 }
 
@@ -287,6 +389,10 @@ int rambo_server_create(rambo_t* h, const rambo_server_config_t* cfg, rambo_serv
             rc = rambo_plan_create(h, kind, cfg->max_batch_queries, items, cfg->max_batch_ids, cfg->k, &sl.plan);
             if (rc == RAMBO_OK && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess)
                 rc = RAMBO_ECUDA;
+            if (rc == RAMBO_OK && cudaMallocHost(&sl.staging, SMALL_RESULT_BYTES) != cudaSuccess) {
+                cudaGetLastError();
+                rc = RAMBO_ENOMEM;
+            }
             S->slots.push_back(sl);
         }
     }
@@ -296,6 +402,7 @@ int rambo_server_create(rambo_t* h, const rambo_server_config_t* cfg, rambo_serv
         for (auto& sl : S->slots) {
             if (sl.plan) rambo_plan_destroy(sl.plan);
             if (sl.stream) cudaStreamDestroy(sl.stream);
+            if (sl.staging) cudaFreeHost(sl.staging);
         }
         if (S->ins_stream) cudaStreamDestroy(S->ins_stream);
         delete S;
@@ -358,11 +465,11 @@ int rambo_server_result(rambo_server_t* S, uint64_t ticket, int wait, uint32_t* 
     }
     if (d.len > cap) return RAMBO_ENOSPC;  // kept: ask again with a larger buffer
     // take the request's share of the batch buffer, then copy without the lock
-    const std::shared_ptr<const std::vector<uint32_t>> buf = d.buf;
+    const std::shared_ptr<const ResultBuf> buf = d.buf;
     const uint64_t off = d.off, len = d.len;
     S->done.erase(it);
     lk.unlock();
-    if (len) std::memcpy(ids, buf->data() + off, len * 4);
+    if (len) std::memcpy(ids, buf->ids + off, len * 4);
     return RAMBO_OK;
 }
 
@@ -383,6 +490,10 @@ int rambo_server_stats(rambo_server_t* S, rambo_server_stats_t* out) {
     out->inserts = S->n_inserts;
     out->keys = S->keys_done;
     out->seconds = S->any ? std::chrono::duration<double>(S->t_last - S->t_first).count() : 0.0;
+    out->admit_ns = S->admit_ns;
+    out->finish_ns = S->finish_ns;
+    out->insert_ns = S->insert_ns;
+    out->idle_ns = S->idle_ns;
     if (!S->latencies.empty()) {
         std::vector<uint64_t> l = S->latencies;
         std::sort(l.begin(), l.end());
@@ -397,6 +508,7 @@ int rambo_server_reset_stats(rambo_server_t* S) {
     if (!S) return RAMBO_EINVAL;
     std::lock_guard<std::mutex> lk(S->mu);
     S->n_queries = S->n_batches = S->n_inserts = S->keys_done = 0;
+    S->admit_ns = S->finish_ns = S->insert_ns = S->idle_ns = 0;
     S->latencies.clear();
     S->any = false;
     return RAMBO_OK;
@@ -432,6 +544,7 @@ void rambo_server_destroy(rambo_server_t* S) {
     for (auto& sl : S->slots) {
         if (sl.plan) rambo_plan_destroy(sl.plan);
         if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.staging) cudaFreeHost(sl.staging);
     }
     if (S->ins_stream) cudaStreamDestroy(S->ins_stream);
     delete S;

@@ -38,7 +38,8 @@ class ServerConfig(C.Structure):
 
 class ServerStats(C.Structure):
     _fields_ = [("queries", _u64), ("batches", _u64), ("inserts", _u64), ("keys", _u64), ("seconds", C.c_double),
-                ("p50_ns", _u64), ("p99_ns", _u64), ("max_ns", _u64)]
+                ("p50_ns", _u64), ("p99_ns", _u64), ("max_ns", _u64), ("admit_ns", _u64), ("finish_ns", _u64),
+                ("insert_ns", _u64), ("idle_ns", _u64)]
 
 
 class QueryConfig(C.Structure):

@@ -531,3 +531,33 @@ def test_set_stages_follow_registration_across_inserts_merge_and_load(mods, tmp_
     p = str(tmp_path / "doc.rambo")
     a.save(p)
     check_all(Rambo.load(p))
+
+
+def test_pinned_host_bases_read_in_place(mods):
+    # Sequence batches in pinned host memory (>= 1 MiB) are packed straight
+    # from host memory; results equal the oracle and the pageable-input path.
+    import torch
+
+    Rambo, Oracle = mods
+    w = synth.make("genome", 0.02, m=1 << 18)
+    g, o = build_pair(w, Rambo, Oracle)
+    reps = 1 + (3 << 20) // max(1, int(w.queries.offsets[-1]))
+    q = w.queries.subset(np.tile(np.arange(len(w.queries)), reps))
+    assert int(q.offsets[-1]) >= (1 << 20)
+    pinned = torch.from_numpy(q.data).pin_memory().numpy()
+    ids_p, off_p = g.query(pinned, q.offsets, kind="seq")
+    ids_h, off_h = g.query(q.data.copy(), q.offsets, kind="seq")
+    rids, roff = o.query_batch("seq", q.data, q.offsets, k=31)
+    assert np.array_equal(off_p, roff) and np.array_equal(ids_p, rids)
+    assert np.array_equal(off_h, roff) and np.array_equal(ids_h, rids)
+    # a bad base in pinned memory is reported like any other
+    bad = pinned.copy()
+    pinned2 = torch.from_numpy(bad).pin_memory().numpy()
+    at = int(q.offsets[5]) + 3
+    pinned2[at] = ord("N")
+    from paper_1910_02611_gb300 import EBADSEQ, RamboError
+
+    with pytest.raises(RamboError) as e:
+        g.query(pinned2, q.offsets, kind="seq")
+    assert e.value.code == EBADSEQ
+    g.close()

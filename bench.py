@@ -64,6 +64,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--m-log2", type=int, default=None, help="override the Bloom filter size m = 2^L")
+    ap.add_argument("--queries", type=int, default=None,
+                    help="queries per step instead of the workload's own count (profiling cases)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the query steps only (no e2e, random-row or CPU legs): the profiling case")
     ap.add_argument("--per-query-baseline", type=int, default=2000,
@@ -79,8 +81,12 @@ def parse_args():
 # workload
 # ---------------------------------------------------------------------------
 
-def make_workload(config: str, scale: float, m_log2=None):
+def make_workload(config: str, scale: float, m_log2=None, queries=None):
     kw = {} if m_log2 is None else {"m": 1 << m_log2}
+    if queries:
+        # the generators scale their query count with the workload; ask for
+        # the count that leaves `queries` after scaling
+        kw["n_queries"] = int(queries) if scale == 1.0 else max(1, int(round(queries / scale)))
     return synth.make(config, scale, **kw)
 
 
@@ -262,7 +268,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     nthreads = os.cpu_count() or 1
-    w = make_workload("document" if args.config == "serving" else args.config, args.scale, args.m_log2)
+    w = make_workload("document" if args.config == "serving" else args.config, args.scale, args.m_log2, args.queries)
     o, build_s = oracle_index(w, nthreads)
     q = w.queries
     # size one step to a bounded sample so the whole run stays within minutes
@@ -319,7 +325,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     t_gen = time.perf_counter()
-    w = make_workload(args.config, args.scale, args.m_log2)
+    w = make_workload(args.config, args.scale, args.m_log2, args.queries)
     batches = extra_batches(w, args.batches, rank)
     t_gen = time.perf_counter() - t_gen
 

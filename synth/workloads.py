@@ -296,8 +296,8 @@ def documents(scale: float = 1.0, data_seed: int = DATA_SEED_BASE + 4, *, n_docs
                     meta=dict(vocab_keys=keys, df=df))
 
 
-CONFIGS = {"tiny": tiny, "genome": genome, "uneven": uneven, "document": documents}
+GENERATORS = {"tiny": tiny, "genome": genome, "uneven": uneven, "document": documents}
 
 
 def make(name: str, scale: float = 1.0, **kw) -> Workload:
-    return CONFIGS[name](scale=scale, **kw)
+    return GENERATORS[name](scale=scale, **kw)

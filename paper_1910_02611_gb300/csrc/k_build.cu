@@ -7,9 +7,11 @@
 //
 // Large builds are tiled: one launch only performs the atomics whose row lies
 // in [row_lo, row_hi), a window sized to stay resident in L2, and the input is
-// streamed once per window.  Streaming the (2-bit packed) input is far cheaper
-// than the DRAM read-modify-write of a sector per random atomic that an
-// untiled build would cost.
+// streamed once per window.  Streaming the input is far cheaper than the DRAM
+// read-modify-write of a sector per random atomic that an untiled build would
+// cost.  When there are several windows, every key's mixed hash mix64(x) is
+// computed once (k_key_hash) and each window pass streams those 8 bytes a
+// key instead of re-extracting and re-hashing it.
 #include "rambo_impl.cuh"
 
 namespace rgb {
@@ -28,8 +30,40 @@ __device__ __forceinline__ uint64_t find_item(const uint64_t* __restrict__ off, 
     return lo;
 }
 
+// ys[p] = mix64 of the key at position p (for sequences: of the k-mer
+// starting at p, canonical if asked; windows running past a set's end get a
+// value that k_insert never uses).
+__global__ void k_key_hash(BatchView b, uint64_t* __restrict__ ys, const DevStatus* st) {
+    if (st->err != NO_ERR) return;
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < b.total;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t key;
+        if (b.seq) {
+            if (p + b.k > b.total) {
+                ys[p] = 0;
+                continue;
+            }
+            key = kmer_at(b.packed, p, b.k);
+            if (b.canon) key = canonical_kmer(key, b.k);
+        } else {
+            key = __ldg(b.keys + p);
+        }
+        ys[p] = mix64(key);
+    }
+}
+
+cudaError_t launch_key_hash(const BatchView& b, uint64_t* ys, const DevStatus* st, int num_sms, cudaStream_t s) {
+    if (b.total == 0) return cudaSuccess;
+    uint64_t blocks = (b.total + 255) / 256;
+    const uint64_t cap = (uint64_t)num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    k_key_hash<<<(unsigned)blocks, 256, 0, s>>>(b, ys, st);
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256) k_insert(IndexView ix, HashParams hp, BatchView b, uint64_t row_lo,
-                                                uint64_t row_hi, int r_lo, int r_hi, const DevStatus* st) {
+                                                uint64_t row_hi, int r_lo, int r_hi, const uint64_t* __restrict__ ys,
+                                                const DevStatus* st) {
     if (st->err != NO_ERR) return;
     const uint64_t per = b.seq ? STARTS_PER_THREAD : KEYS_PER_THREAD;
     const uint64_t nchunks = (b.total + per - 1) / per;
@@ -56,15 +90,20 @@ __global__ void __launch_bounds__(256) k_insert(IndexView ix, HashParams hp, Bat
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r) cell[r] = ph[r];
             }
-            uint64_t key;
-            if (b.seq) {
-                if (p + b.k > t_end) continue;  // window runs past the end of this set's sequence
-                key = kmer_at(b.packed, p, b.k);
-                if (b.canon) key = canonical_kmer(key, b.k);
+            if (b.seq && p + b.k > t_end) continue;  // window runs past the end of this set's sequence
+            uint64_t y;
+            if (ys) {
+                y = __ldg(ys + p);
             } else {
-                key = __ldg(b.keys + p);
+                uint64_t key;
+                if (b.seq) {
+                    key = kmer_at(b.packed, p, b.k);
+                    if (b.canon) key = canonical_kmer(key, b.k);
+                } else {
+                    key = __ldg(b.keys + p);
+                }
+                y = mix64(key);
             }
-            const uint64_t y = mix64(key);
 #pragma unroll
             for (int r = 0; r < RMAX; ++r) {
                 if (r < r_lo || r > r_hi) continue;
@@ -84,7 +123,7 @@ __global__ void __launch_bounds__(256) k_insert(IndexView ix, HashParams hp, Bat
 }
 
 cudaError_t launch_insert(const IndexView& ix, const HashParams& hp, const BatchView& b, uint64_t row_lo,
-                          uint64_t row_hi, DevStatus* st, int num_sms, cudaStream_t s) {
+                          uint64_t row_hi, const uint64_t* ys, DevStatus* st, int num_sms, cudaStream_t s) {
     if (b.total == 0 || b.n == 0 || row_hi <= row_lo) return cudaSuccess;
     const uint64_t per = b.seq ? STARTS_PER_THREAD : KEYS_PER_THREAD;
     const uint64_t nchunks = (b.total + per - 1) / per;
@@ -95,7 +134,7 @@ cudaError_t launch_insert(const IndexView& ix, const HashParams& hp, const Batch
     int r_lo = (int)(row_lo / ix.m);
     int r_hi = (int)((row_hi - 1) / ix.m);
     if (r_hi >= (int)ix.R) r_hi = (int)ix.R - 1;
-    k_insert<<<(unsigned)blocks, 256, 0, s>>>(ix, hp, b, row_lo, row_hi, r_lo, r_hi, st);
+    k_insert<<<(unsigned)blocks, 256, 0, s>>>(ix, hp, b, row_lo, row_hi, r_lo, r_hi, ys, st);
     return cudaGetLastError();
 }
 

@@ -425,6 +425,12 @@ def test_canonical_kmers_index_and_queries(mods, k):
     o = Oracle(w.K, w.B, w.R, w.m, w.eta, w.seed)
     o.insert_seq_batch(w.sets.ids, w.sets.data, w.sets.offsets, k | CANON)
     assert_index_equal(g, o)
+    # window-by-window build (keys hashed once, then streamed per window): same bits
+    gt = Rambo(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    gt.set_build_tiling(1 << 17, mode=1)
+    gt.insert(w.sets.ids, w.sets.data, w.sets.offsets, kind="seq", k=k | CANON)
+    assert np.array_equal(gt.export_index(), g.export_index())
+    gt.close()
     q = w.queries.subset(np.arange(400))
     assert_query_equal(g, o, q, k=k | CANON)
     # the reverse-complemented queries give the same answers
@@ -560,4 +566,30 @@ def test_pinned_host_bases_read_in_place(mods):
     with pytest.raises(RamboError) as e:
         g.query(pinned2, q.offsets, kind="seq")
     assert e.value.code == EBADSEQ
+    g.close()
+
+
+def test_large_answers_gathered_into_pinned_host_buffers(mods):
+    # Answers of >= 2^18 IDs bound for pinned host memory are gathered there
+    # directly; pageable destinations take the device copy.  Both equal the
+    # oracle.
+    import torch
+
+    Rambo, Oracle = mods
+    w = synth.make("document", 0.01, m=1 << 16)
+    g, o = build_pair(w, Rambo, Oracle)
+    q = w.queries
+    rids, roff = o.query_batch("keys", q.data, q.offsets)
+    assert int(roff[-1]) >= (1 << 18)
+    ids_a, off_a = g.query(q.data, q.offsets, kind="keys")  # pinned result arena
+    assert np.array_equal(off_a, roff) and np.array_equal(ids_a, rids)
+    for pinned in (True, False):
+        ids = torch.zeros(int(roff[-1]) + 7, dtype=torch.int32)
+        off = torch.zeros(len(q) + 1, dtype=torch.int64)
+        if pinned:
+            ids, off = ids.pin_memory(), off.pin_memory()
+        n = g.query_into(q.data, q.offsets, ids.numpy().view(np.uint32), off.numpy().view(np.uint64), kind="keys")
+        assert n == int(roff[-1])
+        assert np.array_equal(off.numpy().view(np.uint64), roff)
+        assert np.array_equal(ids.numpy()[:n].view(np.uint32), rids)
     g.close()

@@ -9,9 +9,9 @@
 // in [row_lo, row_hi), a window sized to stay resident in L2, and the input is
 // streamed once per window.  Streaming the input is far cheaper than the DRAM
 // read-modify-write of a sector per random atomic that an untiled build would
-// cost.  When there are several windows, every key's mixed hash mix64(x) is
-// computed once (k_key_hash) and each window pass streams those 8 bytes a
-// key instead of re-extracting and re-hashing it.
+// cost.  (Hashing every key once and streaming the 8-byte hashes to each
+// window instead measured no faster: the hash stream evicts the window from
+// L2.)
 #include "rambo_impl.cuh"
 
 namespace rgb {
@@ -30,47 +30,20 @@ __device__ __forceinline__ uint64_t find_item(const uint64_t* __restrict__ off, 
     return lo;
 }
 
-// ys[p] = mix64 of the key at position p (for sequences: of the k-mer
-// starting at p, canonical if asked; windows running past a set's end get a
-// value that k_insert never uses).
-__global__ void k_key_hash(BatchView b, uint64_t* __restrict__ ys, const DevStatus* st) {
-    if (st->err != NO_ERR) return;
-    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < b.total;
-         p += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t key;
-        if (b.seq) {
-            if (p + b.k > b.total) {
-                ys[p] = 0;
-                continue;
-            }
-            key = kmer_at(b.packed, p, b.k);
-            if (b.canon) key = canonical_kmer(key, b.k);
-        } else {
-            key = __ldg(b.keys + p);
-        }
-        ys[p] = mix64(key);
-    }
-}
-
-cudaError_t launch_key_hash(const BatchView& b, uint64_t* ys, const DevStatus* st, int num_sms, cudaStream_t s) {
-    if (b.total == 0) return cudaSuccess;
-    uint64_t blocks = (b.total + 255) / 256;
-    const uint64_t cap = (uint64_t)num_sms * 16;
-    if (blocks > cap) blocks = cap;
-    k_key_hash<<<(unsigned)blocks, 256, 0, s>>>(b, ys, st);
-    return cudaGetLastError();
-}
-
+// A warp takes 32 * per consecutive positions and its lanes interleave over
+// them (lane l: p0 + l, p0 + l + 32, ...), so the packed words, keys or
+// hashes a step reads are adjacent across the warp.
 __global__ void __launch_bounds__(256) k_insert(IndexView ix, HashParams hp, BatchView b, uint64_t row_lo,
-                                                uint64_t row_hi, int r_lo, int r_hi, const uint64_t* __restrict__ ys,
-                                                const DevStatus* st) {
+                                                uint64_t row_hi, int r_lo, int r_hi, const DevStatus* st) {
     if (st->err != NO_ERR) return;
-    const uint64_t per = b.seq ? STARTS_PER_THREAD : KEYS_PER_THREAD;
-    const uint64_t nchunks = (b.total + per - 1) / per;
-    for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < nchunks;
-         c += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t p0 = c * per;
-        const uint64_t p1 = min(p0 + per, b.total);
+    const uint64_t span = 32 * (b.seq ? STARTS_PER_THREAD : KEYS_PER_THREAD);
+    const uint64_t nchunks = (b.total + span - 1) / span;
+    const unsigned lane = threadIdx.x & 31;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t c = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nwarps) {
+        const uint64_t p0 = c * span + lane;
+        const uint64_t p1 = min(c * span + span, b.total);
+        if (p0 >= p1) continue;
         uint64_t t = find_item(b.offsets, b.n, p0 + b.off0);
         uint64_t t_end = __ldg(b.offsets + t + 1) - b.off0;
         uint32_t cell[RMAX];
@@ -79,7 +52,7 @@ __global__ void __launch_bounds__(256) k_insert(IndexView ix, HashParams hp, Bat
 #pragma unroll
             for (int r = 0; r < RMAX; ++r) cell[r] = ph[r];
         }
-        for (uint64_t p = p0; p < p1; ++p) {
+        for (uint64_t p = p0; p < p1; p += 32) {
             if (p >= t_end) {
                 // advance to the item holding p (skips empty items)
                 do {
@@ -91,19 +64,14 @@ __global__ void __launch_bounds__(256) k_insert(IndexView ix, HashParams hp, Bat
                 for (int r = 0; r < RMAX; ++r) cell[r] = ph[r];
             }
             if (b.seq && p + b.k > t_end) continue;  // window runs past the end of this set's sequence
-            uint64_t y;
-            if (ys) {
-                y = __ldg(ys + p);
+            uint64_t key;
+            if (b.seq) {
+                key = kmer_at(b.packed, p, b.k);
+                if (b.canon) key = canonical_kmer(key, b.k);
             } else {
-                uint64_t key;
-                if (b.seq) {
-                    key = kmer_at(b.packed, p, b.k);
-                    if (b.canon) key = canonical_kmer(key, b.k);
-                } else {
-                    key = __ldg(b.keys + p);
-                }
-                y = mix64(key);
+                key = __ldg(b.keys + p);
             }
+            const uint64_t y = mix64(key);
 #pragma unroll
             for (int r = 0; r < RMAX; ++r) {
                 if (r < r_lo || r > r_hi) continue;
@@ -123,18 +91,18 @@ __global__ void __launch_bounds__(256) k_insert(IndexView ix, HashParams hp, Bat
 }
 
 cudaError_t launch_insert(const IndexView& ix, const HashParams& hp, const BatchView& b, uint64_t row_lo,
-                          uint64_t row_hi, const uint64_t* ys, DevStatus* st, int num_sms, cudaStream_t s) {
+                          uint64_t row_hi, DevStatus* st, int num_sms, cudaStream_t s) {
     if (b.total == 0 || b.n == 0 || row_hi <= row_lo) return cudaSuccess;
-    const uint64_t per = b.seq ? STARTS_PER_THREAD : KEYS_PER_THREAD;
-    const uint64_t nchunks = (b.total + per - 1) / per;
-    uint64_t blocks = (nchunks + 255) / 256;
+    const uint64_t span = 32 * (b.seq ? STARTS_PER_THREAD : KEYS_PER_THREAD);
+    const uint64_t nchunks = (b.total + span - 1) / span;  // one warp each
+    uint64_t blocks = (nchunks + 7) / 8;
     uint64_t cap = (uint64_t)num_sms * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     int r_lo = (int)(row_lo / ix.m);
     int r_hi = (int)((row_hi - 1) / ix.m);
     if (r_hi >= (int)ix.R) r_hi = (int)ix.R - 1;
-    k_insert<<<(unsigned)blocks, 256, 0, s>>>(ix, hp, b, row_lo, row_hi, r_lo, r_hi, ys, st);
+    k_insert<<<(unsigned)blocks, 256, 0, s>>>(ix, hp, b, row_lo, row_hi, r_lo, r_hi, st);
     return cudaGetLastError();
 }
 

@@ -100,7 +100,7 @@ uint32_t stride_for(uint32_t W) {
 }
 
 // default build window: a slice of the index that stays resident in L2
-constexpr uint64_t BUILD_TILE_BYTES = 64ull << 20;
+constexpr uint64_t BUILD_TILE_BYTES = 128ull << 20;  // measured fastest on GB300 (L2 126 MB)
 
 }  // namespace
 
@@ -365,49 +365,28 @@ int run_insert(rambo* h, int seq, const uint64_t* set_ids, const void* data, con
     if (seq) RK(pack_bases(h, b, d_data, s));
     else b.keys = static_cast<const uint64_t*>(d_data);
     CK(launch_register(b, h->reg, h->st, s));
-    // Window by window (each an L2-resident slice of the rows) or one pass
-    // with every atomic going to device memory, whichever the measured costs
-    // on GB300 make cheaper: a window pass costs about 5 ps a key when it
-    // re-extracts and re-hashes the keys and 1.5 ps when it streams their
-    // precomputed hashes, plus about 4 us a launch; an atomic costs about 5 ps
-    // inside an L2-resident window and 40 ps as a device-memory
-    // read-modify-write.
+    // Window by window (each an L2-sized slice of the rows) or one pass with
+    // every atomic going to device memory, whichever the measured costs on
+    // GB300 make cheaper: a window pass costs about 5 ps a key (extracting and
+    // hashing it) plus about 4 us a launch; an atomic costs about 5 ps inside
+    // a window and 40 ps as a device-memory read-modify-write.
     const uint64_t n_keys = b.total;  // upper bound for sequences
     const uint64_t rows_total = (uint64_t)h->R * h->m;
     uint64_t tile_rows = h->build_tile_bytes / ((uint64_t)h->S * 4);
     if (tile_rows < 1) tile_rows = 1;
     const uint64_t n_tiles = (rows_total + tile_rows - 1) / tile_rows;
     const double atomics = (double)h->R * h->eta;
-    auto tiled_ps = [&](double per_window) {
-        return (double)n_keys * ((double)n_tiles * per_window + atomics * 5.0) + (double)n_tiles * 4e6;
-    };
+    const double tiled_ps = (double)n_keys * ((double)n_tiles * 5.0 + atomics * 5.0) + (double)n_tiles * 4e6;
     const double untiled_ps = (double)n_keys * atomics * 40.0 + 4e6;
-    bool use_tiles = h->build_mode == 1 || (h->build_mode == 0 && n_tiles > 1 && tiled_ps(1.5) < untiled_ps);
-    // precomputed hashes pay off once the keys are streamed three times or more
-    uint64_t* ys = nullptr;
-    if (use_tiles && n_tiles >= 3) {
-        size_t free_b = 0, total_b = 0;
-        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && n_keys * 8 < free_b / 2 &&
-            cudaMalloc(&ys, n_keys * 8) != cudaSuccess)
-            ys = nullptr;
-        cudaGetLastError();
-    }
-    if (use_tiles && !ys && h->build_mode == 0) use_tiles = n_tiles > 1 && tiled_ps(5.0) < untiled_ps;
-    cudaError_t e = cudaSuccess;
-    if (use_tiles && ys) e = launch_key_hash(b, ys, h->st, h->num_sms, s);
+    const bool use_tiles = h->build_mode == 1 || (h->build_mode == 0 && n_tiles > 1 && tiled_ps < untiled_ps);
     if (use_tiles) {
-        for (uint64_t lo = 0; lo < rows_total && e == cudaSuccess; lo += tile_rows) {
+        for (uint64_t lo = 0; lo < rows_total; lo += tile_rows) {
             uint64_t hi = lo + tile_rows < rows_total ? lo + tile_rows : rows_total;
-            e = launch_insert(h->view(), h->hp, b, lo, hi, ys, h->st, h->num_sms, s);
+            CK(launch_insert(h->view(), h->hp, b, lo, hi, h->st, h->num_sms, s));
         }
     } else {
-        e = launch_insert(h->view(), h->hp, b, 0, rows_total, nullptr, h->st, h->num_sms, s);
+        CK(launch_insert(h->view(), h->hp, b, 0, rows_total, h->st, h->num_sms, s));
     }
-    if (ys) {
-        cudaStreamSynchronize(s);
-        cudaFree(ys);
-    }
-    CK(e);
     CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const int rc = decode_err(h, h->h_st->err);
@@ -636,29 +615,17 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
         hid = d.ids;
         hoff = d.id_offsets;
     }
-    // Large answers bound for pinned host memory are gathered straight into
-    // it (the gather's stores cross NVLink-C2C), saving a device-side copy
-    // and a separate transfer; otherwise gather on the device and copy.
-    uint32_t* direct = nullptr;
-    if (total_ids >= (1u << 18)) {
-        cudaPointerAttributes pa{};
-        if (cudaPointerGetAttributes(&pa, hid) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
-            direct = static_cast<uint32_t*>(pa.devicePointer);
-        else
-            cudaGetLastError();
-    }
-    uint32_t* d_ids = direct;
-    if (!direct) {
-        RK(h->ids.ensure(total_ids + 1));
-        d_ids = h->ids.p;
-    }
+    // (Gathering large answers straight into pinned host memory over
+    // NVLink-C2C measured slower than gathering on the device and copying:
+    // 1.9e6 against 2.15e6 keys/s end to end on the document workload.)
+    RK(h->ids.ensure(total_ids + 1));
+    uint32_t* d_ids = h->ids.p;
     CK(launch_gather(o, d_off, n, d_ids, h->st, s));
     CK(cudaEventRecord(h->ev[3], s));
     h->launches += 1;
     h->last.kernel_launches = h->launches;
     CK(cudaMemcpyAsync(hoff, d_off, (n + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-    if (total_ids && !direct)
-        CK(cudaMemcpyAsync(hid, d_ids, total_ids * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    if (total_ids) CK(cudaMemcpyAsync(hid, d_ids, total_ids * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     CK(cudaEventElapsedTime(&h->last.device_ms, h->ev[0], h->ev[3]));
     if (d.arena) {

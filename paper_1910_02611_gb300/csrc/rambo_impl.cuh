@@ -258,9 +258,7 @@ constexpr uint32_t CLUSTER_BUCKETS = 1u << 16;
 
 // k_build.cu
 cudaError_t launch_insert(const IndexView& ix, const HashParams& hp, const BatchView& b,
-                          uint64_t row_lo, uint64_t row_hi, const uint64_t* ys, DevStatus* st, int num_sms,
-                          cudaStream_t s);
-cudaError_t launch_key_hash(const BatchView& b, uint64_t* ys, const DevStatus* st, int num_sms, cudaStream_t s);
+                          uint64_t row_lo, uint64_t row_hi, DevStatus* st, int num_sms, cudaStream_t s);
 
 // k_query*.cu
 bool query_config_supported(int V, int G, uint32_t S);

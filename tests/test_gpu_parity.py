@@ -569,10 +569,9 @@ def test_pinned_host_bases_read_in_place(mods):
     g.close()
 
 
-def test_large_answers_gathered_into_pinned_host_buffers(mods):
-    # Answers of >= 2^18 IDs bound for pinned host memory are gathered there
-    # directly; pageable destinations take the device copy.  Both equal the
-    # oracle.
+def test_large_answers_into_pinned_and_pageable_host_buffers(mods):
+    # Large answers (>= 2^18 IDs) copied into the pinned result arena, into
+    # pinned caller buffers and into pageable ones all equal the oracle.
     import torch
 
     Rambo, Oracle = mods

@@ -30,61 +30,62 @@ __device__ __forceinline__ uint64_t find_item(const uint64_t* __restrict__ off, 
     return lo;
 }
 
-// A warp takes 32 * per consecutive positions and its lanes interleave over
-// them (lane l: p0 + l, p0 + l + 32, ...), so the packed words, keys or
-// hashes a step reads are adjacent across the warp.
+// Each warp takes one contiguous run of positions with its lanes
+// interleaved (lane l: p0 + l, p0 + l + 32, ...), so a step's packed words,
+// keys and phi rows are adjacent across the warp, and the set holding a
+// position is found by one binary search per warp, then followed forward.
 __global__ void __launch_bounds__(256) k_insert(IndexView ix, HashParams hp, BatchView b, uint64_t row_lo,
                                                 uint64_t row_hi, int r_lo, int r_hi, const DevStatus* st) {
     if (st->err != NO_ERR) return;
-    const uint64_t span = 32 * (b.seq ? STARTS_PER_THREAD : KEYS_PER_THREAD);
-    const uint64_t nchunks = (b.total + span - 1) / span;
     const unsigned lane = threadIdx.x & 31;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t c = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nwarps) {
-        const uint64_t p0 = c * span + lane;
-        const uint64_t p1 = min(c * span + span, b.total);
-        if (p0 >= p1) continue;
-        uint64_t t = find_item(b.offsets, b.n, p0 + b.off0);
-        uint64_t t_end = __ldg(b.offsets + t + 1) - b.off0;
-        uint32_t cell[RMAX];
-        {
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t per_warp = ((b.total + nwarps - 1) / nwarps + 31) & ~31ull;
+    const uint64_t w_begin = warp * per_warp;
+    const uint64_t w_end = min(w_begin + per_warp, b.total);
+    if (w_begin >= w_end) return;
+    uint64_t t = 0;
+    if (lane == 0) t = find_item(b.offsets, b.n, w_begin + b.off0);
+    t = __shfl_sync(FULL, t, 0);
+    uint64_t t_end = __ldg(b.offsets + t + 1) - b.off0;
+    uint32_t cell[RMAX];
+    {
+        const uint16_t* ph = ix.phi + __ldg(b.set_ids + t) * PHI_STRIDE;
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) cell[r] = ph[r];
+    }
+    for (uint64_t p = w_begin + lane; p < w_end; p += 32) {
+        if (p >= t_end) {
+            // advance to the item holding p (skips empty items)
+            do {
+                ++t;
+                t_end = __ldg(b.offsets + t + 1) - b.off0;
+            } while (p >= t_end);
             const uint16_t* ph = ix.phi + __ldg(b.set_ids + t) * PHI_STRIDE;
 #pragma unroll
             for (int r = 0; r < RMAX; ++r) cell[r] = ph[r];
         }
-        for (uint64_t p = p0; p < p1; p += 32) {
-            if (p >= t_end) {
-                // advance to the item holding p (skips empty items)
-                do {
-                    ++t;
-                    t_end = __ldg(b.offsets + t + 1) - b.off0;
-                } while (p >= t_end);
-                const uint16_t* ph = ix.phi + __ldg(b.set_ids + t) * PHI_STRIDE;
+        if (b.seq && p + b.k > t_end) continue;  // window runs past the end of this set's sequence
+        uint64_t key;
+        if (b.seq) {
+            key = kmer_at(b.packed, p, b.k);
+            if (b.canon) key = canonical_kmer(key, b.k);
+        } else {
+            key = __ldg(b.keys + p);
+        }
+        const uint64_t y = mix64(key);
 #pragma unroll
-                for (int r = 0; r < RMAX; ++r) cell[r] = ph[r];
-            }
-            if (b.seq && p + b.k > t_end) continue;  // window runs past the end of this set's sequence
-            uint64_t key;
-            if (b.seq) {
-                key = kmer_at(b.packed, p, b.k);
-                if (b.canon) key = canonical_kmer(key, b.k);
-            } else {
-                key = __ldg(b.keys + p);
-            }
-            const uint64_t y = mix64(key);
+        for (int r = 0; r < RMAX; ++r) {
+            if (r < r_lo || r > r_hi) continue;
+            const uint32_t word = cell[r] >> 5;
+            const uint32_t bit = 1u << (cell[r] & 31);
+            const uint64_t rbase = (uint64_t)r * ix.m;
 #pragma unroll
-            for (int r = 0; r < RMAX; ++r) {
-                if (r < r_lo || r > r_hi) continue;
-                const uint32_t word = cell[r] >> 5;
-                const uint32_t bit = 1u << (cell[r] & 31);
-                const uint64_t rbase = (uint64_t)r * ix.m;
-#pragma unroll
-                for (int j = 0; j < EMAX; ++j) {
-                    if (j >= (int)ix.eta) break;
-                    const uint64_t pos = (hp.s[r][j] * y) >> ix.shift;
-                    const uint64_t grow = rbase + pos;
-                    if (grow - row_lo < row_hi - row_lo) atomicOr(ix.rows + grow * ix.S + word, bit);
-                }
+            for (int j = 0; j < EMAX; ++j) {
+                if (j >= (int)ix.eta) break;
+                const uint64_t pos = (hp.s[r][j] * y) >> ix.shift;
+                const uint64_t grow = rbase + pos;
+                if (grow - row_lo < row_hi - row_lo) atomicOr(ix.rows + grow * ix.S + word, bit);
             }
         }
     }
@@ -94,7 +95,7 @@ cudaError_t launch_insert(const IndexView& ix, const HashParams& hp, const Batch
                           uint64_t row_hi, DevStatus* st, int num_sms, cudaStream_t s) {
     if (b.total == 0 || b.n == 0 || row_hi <= row_lo) return cudaSuccess;
     const uint64_t span = 32 * (b.seq ? STARTS_PER_THREAD : KEYS_PER_THREAD);
-    const uint64_t nchunks = (b.total + span - 1) / span;  // one warp each
+    const uint64_t nchunks = (b.total + span - 1) / span;  // warps wanted at most
     uint64_t blocks = (nchunks + 7) / 8;
     uint64_t cap = (uint64_t)num_sms * 8;
     if (blocks > cap) blocks = cap;

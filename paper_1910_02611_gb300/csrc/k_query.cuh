@@ -603,9 +603,9 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
         volatile uint32_t* ctl_dead = ctl + 4;
         volatile uint32_t* ctl_cnt = ctl + 8;  // [8] per-warp counts
 
-        if (use_bitmap)
-            for (uint32_t w = gw * 32 + lane; w < bw; w += P * 32) sBits[w] = 0;
-        if (P > 1) batch = 1;
+        // (groups only form when the set stage has a shared-memory bitmap)
+        for (uint32_t w = gw * 32 + lane; w < bw; w += P * 32) sBits[w] = 0;
+        batch = 1;
         qk_group_sync(P, gi);
 
         unsigned long long probed = 0, rows_read = 0;
@@ -622,16 +622,14 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                 const uint64_t e = __ldg(b.offsets + q + 1) - b.off0;
                 const uint64_t nkeys = b.seq ? (e - a - b.k + 1) : (e - a);  // >= 1 (validated)
 
-                if (P > 1) {
-                    for (uint32_t w = gw * 32 + lane; w < (uint32_t)R * ix.S; w += P * 32) sM[w] = ~0u;
-                    if (leader) *ctl_dead = 0;
-                    qk_group_sync(P, gi);
-                }
+                for (uint32_t w = gw * 32 + lane; w < (uint32_t)R * ix.S; w += P * 32) sM[w] = ~0u;
+                if (leader) *ctl_dead = 0;
+                qk_group_sync(P, gi);
 
                 uint32_t M[RMAX][V];
-    #pragma unroll
+#pragma unroll
                 for (int r = 0; r < RMAX; ++r)
-    #pragma unroll
+#pragma unroll
                     for (int v = 0; v < V; ++v) M[r][v] = has_words ? ~0u : 0u;
 
                 bool alive = true;
@@ -647,7 +645,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                 const bool screen = order >= 2 && R > 1;
                 const uint64_t nphases = mine + ((screen && mine) ? 1 : 0);
                 for (uint64_t ph = 0; ph < nphases; ++ph) {
-                    if (P > 1 && __shfl_sync(FULL, *ctl_dead, 0)) break;  // another warp found an empty table
+                    if (__shfl_sync(FULL, *ctl_dead, 0)) break;  // another warp found an empty table
                     const uint64_t s = gw + (uint64_t)P * (screen ? (ph == 0 ? 0 : ph - 1) : ph);
                     const int rlo = (screen && ph == 1) ? 1 : 0;
                     const int rhi = (screen && ph == 0) ? 1 : R;
@@ -666,11 +664,11 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                     // A3: issue every row read of this step, then combine
                     uint32_t val[RMAX][ETA][V];
                     const bool ld = act && has_words;
-    #pragma unroll
+#pragma unroll
                     for (int r = 0; r < RMAX; ++r) {
                         if (r >= rlo && r < rhi && ld) {
                             const uint32_t* rb = rows + (uint64_t)r * ix.m * ix.S + w0;
-    #pragma unroll
+#pragma unroll
                             for (int j = 0; j < ETA; ++j) {
                                 if (j < eta) {
                                     const uint64_t pos = (hp.s[r][j] * y) >> ix.shift;
@@ -680,16 +678,16 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                         }
                     }
                     uint32_t nz = 0;
-    #pragma unroll
+#pragma unroll
                     for (int r = 0; r < RMAX; ++r) {
                         if (r < R) {
                             uint32_t any = 0;
                             const bool probed_r = r >= rlo && r < rhi;
-    #pragma unroll
+#pragma unroll
                             for (int v = 0; v < V; ++v) {
                                 uint32_t x = ~0u;
                                 if (ld && probed_r) {
-    #pragma unroll
+#pragma unroll
                                     for (int j = 0; j < ETA; ++j)
                                         if (j < eta) x &= val[r][j][v];
                                 }
@@ -710,34 +708,23 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                     }
                     if (nz != rmask) {
                         alive = false;
-                        if (P > 1 && lane == 0) *ctl_dead = 1;
+                        if (lane == 0) *ctl_dead = 1;
                         break;
                     }
                 }
 
                 // the query's masks in shared memory: row words [w0, w0+V) of table r
-                if (P == 1) {
-                    if (alive && grp == 0 && has_words) {
-    #pragma unroll
-                        for (int r = 0; r < RMAX; ++r)
-                            if (r < R)
-    #pragma unroll
-                                for (int v = 0; v < V; ++v) sM[r * ix.S + w0 + v] = M[r][v];
-                    }
-                    __syncwarp();
-                } else {
-                    // AND of the group's partial masks (a warp that stopped early
-                    // holds a superset, which the AND leaves correct)
-                    if (alive && mine && grp == 0 && has_words) {
-    #pragma unroll
-                        for (int r = 0; r < RMAX; ++r)
-                            if (r < R)
-    #pragma unroll
-                                for (int v = 0; v < V; ++v) atomicAnd(sM + r * ix.S + w0 + v, M[r][v]);
-                    }
-                    qk_group_sync(P, gi);
-                    alive = *ctl_dead == 0;
+                // AND of the group's partial masks (a warp that stopped early
+                // holds a superset, which the AND leaves correct)
+                if (alive && mine && grp == 0 && has_words) {
+#pragma unroll
+                    for (int r = 0; r < RMAX; ++r)
+                        if (r < R)
+#pragma unroll
+                            for (int v = 0; v < V; ++v) atomicAnd(sM + r * ix.S + w0 + v, M[r][v]);
                 }
+                qk_group_sync(P, gi);
+                alive = *ctl_dead == 0;
 
                 uint32_t count = 0;
                 unsigned long long start = 0;
@@ -747,7 +734,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                 int rstar = 0;
                 uint32_t pmin = 0xffffffffu;
                 if (alive) {
-    #pragma unroll
+#pragma unroll
                     for (int r = 0; r < RMAX; ++r) {
                         uint32_t c = 0;
                         if (r < R)
@@ -767,9 +754,8 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                     // cells, complemented, when a table is mostly hit).  Auto picks
                     // the fewest warp-wide operations (Lemma 4.4's candidate term).
                     int stage = set_stage;
-                    if (!use_bitmap) stage = 1;
                     uint32_t list_total = 0;
-    #pragma unroll
+#pragma unroll
                     for (int r = 0; r < RMAX; ++r)
                         if (r < R) list_total += pc[r] * 2 > ix.B ? ix.B - pc[r] : pc[r];
                     const bool union_ok = ix.mem_bits && list_total <= 2u * QK_ID_CAP;
@@ -781,7 +767,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                         uint64_t uni = ~0ull;
                         if (union_ok) {
                             uni = kw / 32 + 1;
-    #pragma unroll
+#pragma unroll
                             for (int r = 0; r < RMAX; ++r) {
                                 if (r >= R) continue;
                                 const uint32_t cr = pc[r] < ix.B - pc[r] ? pc[r] : ix.B - pc[r];
@@ -790,8 +776,8 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                         }
                         stage = (dense <= sparse && dense <= uni) ? 1 : (sparse <= uni ? 2 : 3);
                     }
-                    if (leader) atomicAdd(&st->stage_count[use_bitmap ? stage : 0], 1ull);
-                    if (use_bitmap) {
+                    if (leader) atomicAdd(&st->stage_count[stage], 1ull);
+                    {
                         if (stage == 1) {
                             // dense: one ballot per 32 IDs becomes one bitmap word; four
                             // chunks per iteration so their table loads are in flight together
@@ -799,20 +785,20 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                             for (uint64_t i0 = (uint64_t)gw * 32 * DU; i0 < ix.K; i0 += (uint64_t)P * 32 * DU) {
                                 uint32_t regw[DU];
                                 uint4 ph[DU];
-    #pragma unroll
+#pragma unroll
                                 for (int u = 0; u < DU; ++u) {
                                     const uint64_t i = i0 + 32 * u + lane;
                                     regw[u] = i < ix.K ? __ldg(ix.reg + (i >> 5)) : 0u;
                                     ph[u] = i < ix.K ? __ldg(reinterpret_cast<const uint4*>(ix.phi) + i) : make_uint4(0, 0, 0, 0);
                                 }
-    #pragma unroll
+#pragma unroll
                                 for (int u = 0; u < DU; ++u) {
                                     const uint64_t i = i0 + 32 * u + lane;
                                     bool ok = i < ix.K && ((regw[u] >> (i & 31)) & 1u);
                                     const uint32_t cell[8] = {ph[u].x & 0xffffu, ph[u].x >> 16, ph[u].y & 0xffffu,
                                                               ph[u].y >> 16,     ph[u].z & 0xffffu, ph[u].z >> 16,
                                                               ph[u].w & 0xffffu, ph[u].w >> 16};
-    #pragma unroll
+#pragma unroll
                                     for (int r = 0; r < RMAX; ++r)
                                         if (r < R) ok &= (sM[r * ix.S + (cell[r] >> 5)] >> (cell[r] & 31)) & 1u;
                                     const unsigned bal = __ballot_sync(FULL, ok);
@@ -839,7 +825,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                                     cnt = (uint32_t)__ldg(ix.mem_off + cell + 1) - m0;
                                 }
                                 uint32_t incl = cnt;
-    #pragma unroll
+#pragma unroll
                                 for (int off = 1; off < 32; off <<= 1) {
                                     const uint32_t y = __shfl_up_sync(FULL, incl, off);
                                     if (lane >= (unsigned)off) incl += y;
@@ -850,12 +836,12 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                                 for (uint32_t u0 = gw * 32 * SU; u0 < total; u0 += P * 32 * SU) {
                                     uint32_t id[SU];
                                     uint4 ph[SU];
-    #pragma unroll
+#pragma unroll
                                     for (int c = 0; c < SU; ++c) {
                                         const uint32_t u = u0 + 32 * c + lane;
                                         // owner lane: the first lane whose inclusive count exceeds u
                                         uint32_t j = 0;
-    #pragma unroll
+#pragma unroll
                                         for (uint32_t step = 16; step >= 1; step >>= 1) {
                                             const uint32_t e2 = __shfl_sync(FULL, incl, j + step - 1);
                                             if (e2 <= u) j += step;
@@ -865,14 +851,14 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                                         id[c] = v ? __ldg(ix.mem_ids + pos) : 0xffffffffu;
                                         ph[c] = v ? __ldg(ix.mem_phi + pos) : make_uint4(0, 0, 0, 0);
                                     }
-    #pragma unroll
+#pragma unroll
                                     for (int c = 0; c < SU; ++c) {
                                         if (id[c] == 0xffffffffu) continue;
                                         const uint32_t cl[8] = {ph[c].x & 0xffffu, ph[c].x >> 16, ph[c].y & 0xffffu,
                                                                 ph[c].y >> 16,     ph[c].z & 0xffffu, ph[c].z >> 16,
                                                                 ph[c].w & 0xffffu, ph[c].w >> 16};
                                         bool ok = true;
-    #pragma unroll
+#pragma unroll
                                         for (int r = 0; r < RMAX; ++r)
                                             if (r < R && r != rstar) ok &= (sM[r * ix.S + (cl[r] >> 5)] >> (cl[r] & 31)) & 1u;
                                         if (ok) atomicOr(sBits + (id[c] >> 5), 1u << (id[c] & 31));
@@ -889,7 +875,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                             uint16_t* list = reinterpret_cast<uint16_t*>(sIds);
                             uint32_t list_off[RMAX + 1];
                             list_off[0] = 0;
-    #pragma unroll
+#pragma unroll
                             for (int r = 0; r < RMAX; ++r) {
                                 uint32_t n_r = 0;
                                 if (r < R) {
@@ -903,7 +889,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                                         }
                                         const uint32_t c = __popc(bits);
                                         uint32_t incl = c;
-    #pragma unroll
+#pragma unroll
                                         for (int off = 1; off < 32; off <<= 1) {
                                             const uint32_t y = __shfl_up_sync(FULL, incl, off);
                                             if (lane >= (unsigned)off) incl += y;
@@ -922,12 +908,12 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                             constexpr int UW = 4, UC = 4;
                             for (uint32_t wb = gw * 32 * UW; wb < bw; wb += P * 32 * UW) {
                                 uint32_t g[UW];
-    #pragma unroll
+#pragma unroll
                                 for (int u = 0; u < UW; ++u) {
                                     const uint32_t w = wb + 32 * u + lane;
                                     g[u] = w < bw ? __ldg(ix.reg + w) : 0u;
                                 }
-    #pragma unroll
+#pragma unroll
                                 for (int r = 0; r < RMAX; ++r) {
                                     if (r >= R) continue;
                                     const bool comp = pc[r] * 2 > ix.B;
@@ -935,25 +921,25 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                                     uint32_t acc[UW] = {0, 0, 0, 0};
                                     for (uint32_t t2 = list_off[r]; t2 < list_off[r + 1]; t2 += UC) {
                                         uint32_t v[UC][UW];
-    #pragma unroll
+#pragma unroll
                                         for (int c = 0; c < UC; ++c) {
                                             const bool have = t2 + c < list_off[r + 1];
                                             const uint32_t* col = mb + (uint64_t)(have ? list[t2 + c] : 0) * bw;
-    #pragma unroll
+#pragma unroll
                                             for (int u = 0; u < UW; ++u) {
                                                 const uint32_t w = wb + 32 * u + lane;
                                                 v[c][u] = (have && w < bw) ? __ldg(col + w) : 0u;
                                             }
                                         }
-    #pragma unroll
+#pragma unroll
                                         for (int c = 0; c < UC; ++c)
-    #pragma unroll
+#pragma unroll
                                             for (int u = 0; u < UW; ++u) acc[u] |= v[c][u];
                                     }
-    #pragma unroll
+#pragma unroll
                                     for (int u = 0; u < UW; ++u) g[u] &= comp ? ~acc[u] : acc[u];
                                 }
-    #pragma unroll
+#pragma unroll
                                 for (int u = 0; u < UW; ++u) {
                                     const uint32_t w = wb + 32 * u + lane;
                                     if (w < bw) sBits[w] = g[u];
@@ -973,22 +959,16 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                         for (uint32_t w = wlo + lane; w < whi; w += 32) mine_ids += __popc(sBits[w]);
                         mine_ids = __reduce_add_sync(FULL, mine_ids);
                         uint32_t before = 0;
-                        if (P == 1) {
-                            count = mine_ids;
-                            if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
-                            start = __shfl_sync(FULL, start, 0);
-                        } else {
-                            if (lane == 0) ctl_cnt[gw] = mine_ids;
-                            qk_group_sync(P, gi);
-                            for (unsigned p2 = 0; p2 < P; ++p2) {
-                                const uint32_t c2 = ctl_cnt[p2];
-                                if (p2 < gw) before += c2;
-                                count += c2;
-                            }
-                            if (leader) *ctl_start = count ? atomicAdd(&st->cursor, (unsigned long long)count) : 0ull;
-                            qk_group_sync(P, gi);
-                            start = *ctl_start;
+                        if (lane == 0) ctl_cnt[gw] = mine_ids;
+                        qk_group_sync(P, gi);
+                        for (unsigned p2 = 0; p2 < P; ++p2) {
+                            const uint32_t c2 = ctl_cnt[p2];
+                            if (p2 < gw) before += c2;
+                            count += c2;
                         }
+                        if (leader) *ctl_start = count ? atomicAdd(&st->cursor, (unsigned long long)count) : 0ull;
+                        qk_group_sync(P, gi);
+                        start = *ctl_start;
                         const bool write = count && start + count <= o.stage_cap;
                         uint32_t at = before;
                         for (uint32_t w0b = wlo; w0b < whi; w0b += 32) {
@@ -996,7 +976,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                             uint32_t bits = (w < whi) ? sBits[w] : 0u;
                             uint32_t c = __popc(bits);
                             uint32_t incl = c;
-    #pragma unroll
+#pragma unroll
                             for (int off = 1; off < 32; off <<= 1) {
                                 uint32_t y = __shfl_up_sync(FULL, incl, off);
                                 if (lane >= (unsigned)off) incl += y;
@@ -1025,36 +1005,6 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                             at += blk;
                         }
                         __syncwarp();
-                    } else {
-                        // ID space too large for a shared-memory bitmap (groups are
-                        // single warps here): dense scan, survivors staged in shared
-                        // memory, recounted if they overflow
-                        for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
-                            const uint64_t i = i0 + lane;
-                            const bool ok = (i < ix.K) && qk_set_passes(ix, sM, i, -1);
-                            const unsigned bal = __ballot_sync(FULL, ok);
-                            if (bal) {
-                                const unsigned pre = __popc(bal & ((1u << lane) - 1u));
-                                if (ok && count + pre < (uint32_t)QK_ID_CAP) sIds[count + pre] = (uint32_t)i;
-                                count += __popc(bal);
-                            }
-                        }
-                        if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
-                        start = __shfl_sync(FULL, start, 0);
-                        if (count && start + count <= o.stage_cap) {
-                            if (count <= (uint32_t)QK_ID_CAP) {
-                                for (uint32_t t2 = lane; t2 < count; t2 += 32) o.stage[start + t2] = sIds[t2];
-                            } else {
-                                uint32_t at = 0;
-                                for (uint64_t i0 = 0; i0 < ix.K; i0 += 32) {
-                                    const uint64_t i = i0 + lane;
-                                    const bool ok = (i < ix.K) && qk_set_passes(ix, sM, i, -1);
-                                    const unsigned bal = __ballot_sync(FULL, ok);
-                                    if (ok) o.stage[start + at + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
-                                    at += __popc(bal);
-                                }
-                            }
-                        }
                     }
                 }
                 if (leader) {

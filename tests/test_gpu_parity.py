@@ -592,3 +592,46 @@ def test_large_answers_into_pinned_and_pageable_host_buffers(mods):
         assert np.array_equal(off.numpy().view(np.uint64), roff)
         assert np.array_equal(ids.numpy()[:n].view(np.uint32), rids)
     g.close()
+
+
+def test_id_space_beyond_the_shared_memory_bitmap(mods):
+    # K above 4096 * 32 IDs: no per-warp bitmap and no member lists, so the
+    # set stage is the staged dense scan (one warp per query even for small
+    # batches); results equal the oracle, including queries with more
+    # survivors than the staging words hold.
+    Rambo, Oracle = mods
+    from paper_1910_02611_gb300 import EINVAL, RamboError
+
+    rng = np.random.default_rng(11)
+    K, B, R, m, eta = 200_000, 16, 2, 1 << 15, 2
+    n_sets = 700  # more than the 512 staging words of a warp
+    ids = np.sort(rng.choice(K, n_sets, replace=False)).astype(np.uint64)
+    common = rng.integers(0, 1 << 62, 40, dtype=np.uint64)  # keys held by every set
+    sets = [np.concatenate([common, rng.integers(0, 1 << 62, int(rng.integers(1, 200)), dtype=np.uint64)])
+            for _ in range(n_sets)]
+    data = np.concatenate(sets)
+    off = np.zeros(n_sets + 1, np.uint64)
+    np.cumsum([s.size for s in sets], out=off[1:])
+    g = Rambo(K, B, R, m, eta, 3)
+    o = Oracle(K, B, R, m, eta, 3)
+    g.insert(ids, data, off, kind="keys")
+    o.insert_keys_batch(ids, data, off)
+    assert_partition_equal(g, o)
+    qs = [common[:1], common[:3]]  # every set survives
+    for t in range(60):
+        s = sets[int(rng.integers(0, n_sets))]
+        qs.append(s[rng.choice(s.size, int(rng.integers(1, 4)), replace=False)])
+    qs.append(rng.integers(0, 1 << 62, 2, dtype=np.uint64))
+    qd = np.concatenate(qs)
+    qo = np.zeros(len(qs) + 1, np.uint64)
+    np.cumsum([q.size for q in qs], out=qo[1:])
+    ids_g, off_g = assert_query_equal(g, o, synth.Collection("keys", qd, qo))
+    assert off_g[2] - off_g[1] >= n_sets
+    base = g.get_config()
+    for stage in (2, 3):
+        with pytest.raises(RamboError) as e:
+            g.set_config(**{**base, "set_stage": stage})
+        assert e.value.code == EINVAL
+    g.set_config(**{**base, "warps_per_query": 8})  # no bitmap: stays one warp per query
+    assert_query_equal(g, o, synth.Collection("keys", qd, qo))
+    g.close()

@@ -28,7 +28,9 @@
  *     device before anything is written), except RAMBO_ECUDA, after which the
  *     handle should be destroyed.
  *   - `on_device` = 1: every pointer argument (inputs and caller-provided
- *     outputs) is device memory; 0: host memory (pageable or pinned).
+ *     outputs) is device memory; 0: host memory (pageable or pinned; DNA
+ *     batches of 1 MiB or more in pinned memory are read in place by the
+ *     packing kernel over NVLink-C2C instead of being copied first).
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
  *     enqueue their work on it and return once it has finished (they
  *     synchronise the stream), so inputs may be freed on return.
@@ -61,7 +63,9 @@ enum {
     RAMBO_ENOMEM = -4,   /* device or pinned host allocation failed */
     RAMBO_ENOSPC = -5,   /* caller-provided output too small (see *needed) */
     RAMBO_ECUDA = -6,    /* a CUDA runtime call failed */
-    RAMBO_ETIMEOUT = -7, /* a bounded device-side wait gave up */
+    RAMBO_ETIMEOUT = -7, /* reserved for a bounded device-side wait that gives up;
+                            no kernel of this library waits on a flag, so no
+                            call returns it */
     RAMBO_EIO = -8,      /* file error in save/load */
     RAMBO_ESTATE = -9,   /* call not valid in the object's current state */
     RAMBO_E2BIG = -10    /* request larger than the fixed scratch of
@@ -293,7 +297,9 @@ int rambo_server_submit_insert(rambo_server_t *s, int kind, const uint64_t *set_
 /* Result of a ticket: RAMBO_OK with the ascending IDs (up to cap; with
  * RAMBO_ENOSPC and *n_ids set, call again with a larger buffer), 1 if still
  * pending and wait = 0, or the request's error.  A delivered result is
- * forgotten. */
+ * forgotten.  Finished batches' answers wait in host memory until collected
+ * (large ones in pooled pinned buffers shared by the batch's requests, small
+ * ones in ordinary memory), so uncollected results keep that memory. */
 int rambo_server_result(rambo_server_t *s, uint64_t ticket, int wait, uint32_t *ids, uint64_t cap,
                         uint64_t *n_ids, uint64_t *latency_ns);
 /* Waits until every submitted request has completed. */

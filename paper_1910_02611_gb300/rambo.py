@@ -174,13 +174,16 @@ class _CudaArray:
                                          "strides": None}
 
 
-def _device_copy(ptr: int, n: int, dtype: str):
+def _device_copy(ptr: int, n: int, dtype: str, copy: bool = True):
+    """A torch CUDA tensor over n elements at ptr: a copy, or (copy=False) a
+    view that is valid while the memory is (the handle's result arena: until
+    the next query call)."""
     torch = _torch()
     tdt = {"<u4": torch.int32, "<u8": torch.int64}[dtype]
     if n == 0:
         return torch.zeros(0, dtype=tdt, device="cuda")
     t = torch.as_tensor(_CudaArray(ptr, n, "<i4" if dtype == "<u4" else "<i8"), device="cuda")
-    return t.clone()
+    return t.clone() if copy else t
 
 
 def _host_arr(x, dtype) -> np.ndarray:
@@ -307,8 +310,8 @@ class Rambo:
     def query(self, data, offsets, kind: str = "keys", k: int = 31, stream=None, copy: bool = True):
         """Returns (ids, id_offsets): numpy arrays for host inputs, torch CUDA
         tensors for device inputs.  Query q's answer is ids[id_offsets[q]:id_offsets[q+1]].
-        With copy=False and host inputs the arrays are views of the handle's
-        pinned result arena, valid until the next query call."""
+        With copy=False the arrays are views of the handle's result arena
+        (pinned host or device memory), valid until the next query call."""
         L = load_library()
         dev = _is_cuda_tensor(data)
         if dev:
@@ -329,9 +332,9 @@ class Rambo:
         del keep
         self._check(rc, "query")
         if dev:
-            off_t = _device_copy(offo_p.value, n + 1, "<u8")
+            off_t = _device_copy(offo_p.value, n + 1, "<u8", copy)
             total = int(off_t[-1].item())
-            return _device_copy(ids_p.value or 0, total, "<u4"), off_t
+            return _device_copy(ids_p.value or 0, total, "<u4", copy), off_t
         offs = np.ctypeslib.as_array(C.cast(offo_p, C.POINTER(_u64)), shape=(n + 1,))
         offs = offs.copy() if copy else offs
         total = int(offs[-1])

@@ -604,7 +604,7 @@ def test_id_space_beyond_the_shared_memory_bitmap(mods):
 
     rng = np.random.default_rng(11)
     K, B, R, m, eta = 200_000, 16, 2, 1 << 15, 2
-    n_sets = 700  # more than the 512 staging words of a warp
+    n_sets = 700  # more than the 256 staging words of a warp
     ids = np.sort(rng.choice(K, n_sets, replace=False)).astype(np.uint64)
     common = rng.integers(0, 1 << 62, 40, dtype=np.uint64)  # keys held by every set
     sets = [np.concatenate([common, rng.integers(0, 1 << 62, int(rng.integers(1, 200)), dtype=np.uint64)])

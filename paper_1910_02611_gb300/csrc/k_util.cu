@@ -338,15 +338,52 @@ __global__ void k_scan_add(uint64_t* __restrict__ out, uint64_t n, const uint64_
     if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_sums[n_tiles];
 }
 
+// Small inputs: one block walks the tiles in order with a running carry (one
+// launch instead of three; the batch's launch overhead, not the scan, is the
+// cost there).
+constexpr uint64_t SCAN_ONE_BLOCK_MAX = 8 * SCAN_TILE;
+
+__global__ void k_scan_one_block(const uint32_t* __restrict__ counts, uint64_t n, uint64_t* __restrict__ out,
+                                 const uint64_t* __restrict__ n_dev) {
+    __shared__ uint64_t warp_tot[32];
+    __shared__ uint64_t tot;
+    if (n_dev) n = *n_dev;
+    uint64_t carry = 0;
+    for (uint64_t t0 = 0; t0 < n; t0 += SCAN_TILE) {
+        const uint64_t base = t0 + (uint64_t)threadIdx.x * SCAN_ITEMS;
+        uint64_t v[SCAN_ITEMS];
+        uint64_t sum = 0;
+#pragma unroll
+        for (int t = 0; t < SCAN_ITEMS; ++t) {
+            v[t] = (base + t < n) ? counts[base + t] : 0;
+            sum += v[t];
+        }
+        uint64_t pre = carry + block_exclusive_scan(sum, warp_tot, &tot);
+#pragma unroll
+        for (int t = 0; t < SCAN_ITEMS; ++t) {
+            if (base + t < n) out[base + t] = pre;
+            pre += v[t];
+        }
+        carry += tot;  // read after the scan's closing barrier, rewritten only in the next tile's scan
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
 cudaError_t launch_scan_counts(const uint32_t* counts, uint64_t n, uint64_t* offsets, uint64_t* tmp,
-                               uint64_t tmp_words, cudaStream_t s, const uint64_t* n_dev) {
+                               uint64_t tmp_words, cudaStream_t s, const uint64_t* n_dev, int* n_launched) {
     // with n_dev, n is the capacity the grids are sized for and the true count is read on the device
+    if (n <= SCAN_ONE_BLOCK_MAX) {
+        k_scan_one_block<<<1, SCAN_THREADS, 0, s>>>(counts, n, offsets, n_dev);
+        if (n_launched) *n_launched = 1;
+        return cudaGetLastError();
+    }
     uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles == 0) tiles = 1;
     if (tmp_words < tiles + 1) return cudaErrorInvalidValue;
     k_scan_tiles<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(counts, n, offsets, tmp, n_dev);
     k_scan_sums<<<1, SCAN_THREADS, 0, s>>>(tmp, tiles, n_dev);
     k_scan_add<<<(unsigned)tiles, 256, 0, s>>>(offsets, n, tmp, tiles, n_dev);
+    if (n_launched) *n_launched = 3;
     return cudaGetLastError();
 }
 

@@ -563,8 +563,9 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
         CK(launch_query(h->view(), h->hp, b, o, t, use_bitmap, h->st, s));
         CK(cudaEventRecord(h->ev[2], s));
         if (h->cfg.l2_fetch_bytes) CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, l2_prev));
-        CK(launch_scan_counts(h->qcount.p, n, d_off, h->scan_tmp.p, h->scan_tmp.cap, s));
-        h->launches += 4;
+        int n_scan = 0;
+        CK(launch_scan_counts(h->qcount.p, n, d_off, h->scan_tmp.p, h->scan_tmp.cap, s, nullptr, &n_scan));
+        h->launches += 1 + n_scan;
         CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(h->h_small, d_off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));

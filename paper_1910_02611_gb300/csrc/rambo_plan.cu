@@ -131,8 +131,11 @@ int plan_capture(rambo_plan* p) {
         e = launch_query(ix, hp, b, o, t, use_bitmap, p->st, s, &nq);
         n_launch += nq;
     }
-    if (e == cudaSuccess) e = launch_scan_counts(p->qcount, p->max_q, p->id_off, p->scan_tmp, scan_words, s, p->d_desc);
-    n_launch += 3;
+    if (e == cudaSuccess) {
+        int n_scan = 0;
+        e = launch_scan_counts(p->qcount, p->max_q, p->id_off, p->scan_tmp, scan_words, s, p->d_desc, &n_scan);
+        n_launch += n_scan;
+    }
     if (e == cudaSuccess) e = launch_gather(o, p->id_off, p->max_q, p->ids, p->st, s, p->d_desc, p->max_ids);
     ++n_launch;
     if (e == cudaSuccess) {

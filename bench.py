@@ -33,6 +33,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -687,12 +688,24 @@ def run_serving(args):
         srv.result(t_ins)
         srv.reset_stats()
         arrivals = np.cumsum(rng.exponential(1e9 / rate, len(kinds))).astype(np.uint64)
+        # a client thread collects answers as they complete (tickets are issued
+        # in submission order, right after the insert's), as a serving client
+        # would, so finished batches' buffers return to the server's pool
+        results = [None] * len(kinds)
+
+        def collect(first=int(t_ins) + 1, out=results):
+            for i in range(len(out)):
+                out[i] = srv.result(first + i)[0]
+
+        collector = threading.Thread(target=collect)
+        collector.start()
         t0 = time.perf_counter()
         tickets = srv.replay(kinds, payload, boff, arrivals)
         srv.drain()
         wall = time.perf_counter() - t0
+        collector.join()
         st = srv.stats()
-        results = [srv.result(int(t))[0] for t in tickets]
+        assert int(tickets[0]) == int(t_ins) + 1 and int(tickets[-1]) == int(t_ins) + len(kinds)
         keys = st["keys"]
         sweep.append({"rate_per_s": rate, "offered_s": float(arrivals[-1]) / 1e9, "wall_s": wall,
                       "queries": st["queries"], "batches": st["batches"],

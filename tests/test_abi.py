@@ -66,3 +66,30 @@ def test_kernels_are_compiled_for_sm103a():
 
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
     assert all("-gencode" == a or "sm_103a" in a for a in build.ARCH)
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    # The product path has no CPU fallback: without a CUDA device, creating an
+    # index fails loudly with RAMBO_ECUDA instead of answering on the host.
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1910_02611_gb300 import ECUDA, Rambo, RamboError
+
+    with pytest.raises(RamboError) as e:
+        Rambo(100, 10, 3, 1 << 20, 2, 42)
+    assert e.value.code == ECUDA
+
+
+def test_parameter_checks_precede_the_gpu():
+    # invalid parameters are rejected before any CUDA call (RAMBO_EINVAL even
+    # without a device)
+    from paper_1910_02611_gb300 import EINVAL, Rambo, RamboError
+
+    for args in ((0, 10, 3, 1 << 20, 2), (100, 0, 3, 1 << 20, 2), (100, 10, 0, 1 << 20, 2),
+                 (100, 10, 3, 1000, 2), (100, 10, 3, 1 << 20, 0), (100, 10, 9, 1 << 20, 2),
+                 (100, 5000, 3, 1 << 20, 2), (100, 10, 3, 1 << 20, 5)):
+        with pytest.raises(RamboError) as e:
+            Rambo(*args, 42)
+        assert e.value.code == EINVAL, args

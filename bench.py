@@ -29,6 +29,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -200,18 +201,26 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+def _code_only(text: str) -> str:
+    """C++ source with comments and blank lines removed (comment edits leave
+    the compiled kernel, and so its profile, unchanged)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(l.rstrip() for l in text.splitlines() if l.strip())
+
+
 def kernel_source_hash() -> str:
-    """Hash of the query kernel's device code: k_query.cuh, its instantiation
-    header, and the device helpers of rambo_impl.cuh (up to the launcher
-    declarations)."""
+    """Hash of the query kernel's device code, comments removed: k_query.cuh,
+    its instantiation header, and the device helpers of rambo_impl.cuh (up to
+    the launcher declarations)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1910_02611_gb300", "csrc")
     for name in ("k_query.cuh", "k_query_inst.cuh"):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
-    with open(os.path.join(csrc, "rambo_impl.cuh"), "rb") as f:
+        with open(os.path.join(csrc, name)) as f:
+            h.update(_code_only(f.read()).encode())
+    with open(os.path.join(csrc, "rambo_impl.cuh")) as f:
         text = f.read()
-    h.update(text.split(b"// launchers (defined in the .cu files)")[0])
+    h.update(_code_only(text.split("// launchers (defined in the .cu files)")[0]).encode())
     return h.hexdigest()[:16]
 
 

@@ -22,13 +22,15 @@
 //          query stops reading rows;
 //   A5     a surviving query keeps the registered sets i with bit phi_r(i) of
 //          M_r set in every table: per table the union of the hit cells'
-//          sets, across tables the intersection (Algorithm 2).  "dense" scans
-//          the partition table over all IDs; "sparse" enumerates the members
-//          of the hit cells of the table with the fewest hit cells, tests the
-//          other tables, and marks survivors in a per-warp bitmap;
-//   A6     survivors are written in ascending ID order to a staging arena
-//          (one atomic reservation per query); a scan + gather then lays the
-//          lists out in query order.
+//          sets, across tables the intersection (Algorithm 2).  Per query the
+//          cheapest of three exact stages fills a shared-memory bitmap of the
+//          ID space: "dense" scans the partition table over all IDs; "sparse"
+//          enumerates the registered members of the hit cells of the table
+//          with the fewest hit cells and tests the other tables; "union" ORs
+//          the hit cells' member bitmaps per table and ANDs the tables;
+//   A6     the bitmap is compacted in ascending ID order, with coalesced
+//          stores, into a staging arena (one atomic reservation per query); a
+//          scan + gather then lays the lists out in query order.
 #pragma once
 
 #include "rambo_impl.cuh"

@@ -296,8 +296,8 @@ int rambo_server_submit_insert(rambo_server_t *s, int kind, const uint64_t *set_
                                const uint64_t *offsets, uint64_t n_sets, uint64_t *ticket);
 /* Result of a ticket: RAMBO_OK with the ascending IDs (up to cap; with
  * RAMBO_ENOSPC and *n_ids set, call again with a larger buffer), 1 if still
- * pending and wait = 0, or the request's error.  A delivered result is
- * forgotten.  Finished batches' answers wait in host memory until collected
+ * pending and wait = 0, or the request's error (RAMBO_E2BIG when its answer
+ * alone exceeds max_batch_ids).  A delivered result or error is forgotten.  Finished batches' answers wait in host memory until collected
  * (large ones in pooled pinned buffers shared by the batch's requests, small
  * ones in ordinary memory), so uncollected results keep that memory. */
 int rambo_server_result(rambo_server_t *s, uint64_t ticket, int wait, uint32_t *ids, uint64_t cap,

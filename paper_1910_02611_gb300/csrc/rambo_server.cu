@@ -211,7 +211,10 @@ void finish_slot(rambo_server* S, Slot& sl) {
         for (size_t i = 0; i < sl.members.size(); ++i) {
             const Op& op = sl.members[i];
             Done d;
-            d.status = rc;
+            // a query whose own answer overflows the slot cannot be served:
+            // RAMBO_E2BIG (RAMBO_ENOSPC from rambo_server_result means only
+            // that the caller's buffer is too small)
+            d.status = rc == RAMBO_ENOSPC ? RAMBO_E2BIG : rc;
             if (rc == RAMBO_OK) {
                 d.buf = buf;
                 d.off = off[i];

@@ -619,7 +619,7 @@ class Server:
             rc = L.rambo_server_result(self._s, ticket, int(wait), buf.ctypes.data, cap, C.byref(n), C.byref(lat))
             if rc == 1:
                 return None
-            if rc == ENOSPC:
+            if rc == ENOSPC and int(n.value) > cap:
                 cap = int(n.value)
                 continue
             if rc:

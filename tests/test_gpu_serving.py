@@ -215,3 +215,34 @@ def test_server_replay_load_generator():
         assert np.array_equal(ids, want[i])
     assert srv.stats()["queries"] == len(ops)
     srv.close()
+
+
+def test_server_requeues_batches_whose_answers_overflow_the_slot():
+    # A batch whose answers exceed max_batch_ids is re-run query by query;
+    # a query whose own answer exceeds it gets RAMBO_E2BIG.  Every other
+    # answer still equals the oracle's.
+    from paper_1910_02611_gb300 import E2BIG, RamboError
+
+    Rambo, Oracle, _, Server = _mods()
+    rng, docs, gen, params, n_docs, n_gen, new_docs = _serving_setup(seed=13)
+    ops = [op for op in _request_stream(rng, docs, gen, n_docs, n_gen, new_docs, n_req=200) if op[0] != "insert"]
+    want = _oracle_answers(Oracle, params, docs, gen, n_docs, ops)
+    sizes = np.array([w.size for w in want])
+    cap = int(max(64, np.percentile(sizes, 80)))  # most single answers fit, most batches do not
+    g = _gpu_index(Rambo, params, docs, gen, n_docs)
+    srv = Server(g, slots=2, max_batch_queries=64, max_batch_bases=64 * 700, max_batch_keys=64 * 5,
+                 max_batch_ids=cap)
+    tickets = [srv.submit(op[1], kind=op[0]) for op in ops]
+    srv.drain()
+    n_big = 0
+    for i, t in enumerate(tickets):
+        if sizes[i] > cap:
+            n_big += 1
+            with pytest.raises(RamboError) as e:
+                srv.result(int(t))
+            assert e.value.code == E2BIG
+        else:
+            ids, _ = srv.result(int(t))
+            assert np.array_equal(ids, want[i]), i
+    assert 0 < n_big < len(ops)
+    srv.close()

@@ -68,7 +68,8 @@ enum {
                             call returns it */
     RAMBO_EIO = -8,      /* file error in save/load */
     RAMBO_ESTATE = -9,   /* call not valid in the object's current state */
-    RAMBO_E2BIG = -10    /* request larger than the fixed scratch of
+    RAMBO_E2BIG = -10    /* request larger than a fixed capacity: a plan's
+                            buffers, a server slot, or the scratch of
                             rambo_query_seq_batch_noalloc */
 };
 

@@ -1212,7 +1212,7 @@ const char* rambo_strerror(int code) {
         case RAMBO_ETIMEOUT: return "device wait timed out";
         case RAMBO_EIO: return "file I/O error";
         case RAMBO_ESTATE: return "invalid state";
-        case RAMBO_E2BIG: return "request exceeds the fixed scratch of the no-allocation query";
+        case RAMBO_E2BIG: return "request exceeds a fixed capacity (plan, server slot or no-allocation scratch)";
         default: return "unknown error";
     }
 }

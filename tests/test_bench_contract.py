@@ -38,3 +38,16 @@ def test_reference_arm_line_has_every_contract_key():
 
 def test_reference_arm_other_ranks_exit_without_work():
     assert _run({"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_profiling_query_count_survives_scaling():
+    # --queries asks for a number of queries per step whatever --scale does
+    sys.path.insert(0, ROOT)
+    import bench
+
+    for scale, queries in ((0.05, 123), (0.25, 2000), (0.02, 500)):
+        w = bench.make_workload("genome", scale, 16, queries)
+        assert len(w.queries) == queries, (scale, queries)
+    batches = bench.extra_batches(bench.make_workload("genome", 0.02, 16, 300), 3, 0)
+    assert len(batches) == 3 and all(len(b) == 300 for b in batches)
+    assert len({hash(b.data.tobytes()) for b in batches}) == 3  # distinct batches of one shape

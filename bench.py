@@ -2,14 +2,19 @@
 """Benchmark of the batched RAMBO query path (arXiv 1910.02611) on one or more
 GB300s.
 
-A step is one batch of the genome-like workload: 10^5 DNA query sequences of
-U[100,1000] bases (substrings of 2000 synthetic genomes with 0-2% base
-substitutions) answered against a resident index of 2000 genomes x ~10^6
-31-mers (B=64, R=6, m=2^27, eta=2): 2-bit packing, k-mer hashing, row probes,
-AND across tables' cells and across the sequence's k-mers, set-level
-intersection and compaction of the set-ID lists, all in the library's kernels.
-The index is built once per run with the construction kernel (timed and
-reported beside the query numbers).
+A step (default workload, "uneven") is one batch of 10^6 DNA query sequences
+with lognormal lengths (median 300 bases, sigma 1, clipped to [31, 10^4];
+substrings of 10^4 synthetic genomes with 0-2% base substitutions) answered
+against a resident index of 10^4 genomes x ~2*10^5 31-mers (B=128, R=8,
+m=2^26, eta=2, 8 GiB): 2-bit packing, k-mer hashing, row probes, AND across
+tables' cells and across the sequence's k-mers, set-level intersection and
+compaction of the set-ID lists, all in the library's kernels, as one replay of
+a CUDA graph captured once (the persistent query kernel with its device work
+queue inside), with the kernel tiling picked by the library's autotuner on the
+first batch before the timed region.  --config genome / document / tiny /
+serving select the other workloads, --api call the direct C-ABI call.  The
+index is built once per run with the construction kernel (timed and reported
+beside the query numbers).
 
   value   k-mers (query keys submitted) per second, inputs already in device
           memory, summed over ranks, time = max over ranks of the CUDA-event
@@ -56,7 +61,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", default="genome", choices=["genome", "uneven", "document", "tiny", "serving"])
+    ap.add_argument("--config", default="uneven", choices=["genome", "uneven", "document", "tiny", "serving"])
     ap.add_argument("--rates", default="1000,10000,100000,1000000",
                     help="serving: Poisson arrival rates (requests/s) to sweep")
     ap.add_argument("--requests-per-rate", type=int, default=20000)
@@ -72,8 +77,9 @@ def parse_args():
                     help="time the query steps only (no e2e, random-row or CPU legs): the profiling case")
     ap.add_argument("--per-query-baseline", type=int, default=2000,
                     help="queries timed through the one-query-per-launch kernel (0 = skip)")
-    ap.add_argument("--autotune", action="store_true", help="pick the kernel configuration on batch 0 first")
-    ap.add_argument("--api", choices=["call", "plan"], default="call",
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
+                    help="pick the kernel configuration with the library's autotuner on batch 0 first")
+    ap.add_argument("--api", choices=["call", "plan"], default="plan",
                     help="timed step through rambo_query_*_into (call) or a replayed CUDA-graph plan (plan)")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
@@ -415,9 +421,10 @@ def run_ours(args):
             plan.wait(to_host=False, copy=False, stream=stream)
             return nk
 
+    step = plan_step if plans else one_step
     for i in range(args.warmup):
         flush.zero_()
-        one_step(i)
+        step(i)
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local) if rank == 0 else None
@@ -431,36 +438,39 @@ def run_ours(args):
     for i in range(args.steps):
         flush.zero_()
         e0.record(stream)
-        nk = plan_step(i) if plans else one_step(i)
+        nk = step(i)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         keys += nk
-        if plans:
-            launches += plans[i % len(plans)][0].launches_per_replay
-            continue
-        st = g.last_query_stats()
+        # counters of this step's batch, and the query kernel's time from CUDA
+        # events recorded on the launching stream around it (inside the graph
+        # for a plan replay)
+        st = plans[i % len(plans)][0].last_stats() if plans else g.last_query_stats()
         probed += st["keys_probed"]
         rows_read += st["rows_read"]
         qk_ms.append(st["query_kernel_ms"])
         launches += st["kernel_launches"]
         n_ids += st["n_results"]
     torch.cuda.synchronize()
-    if plans:
-        # the kernel time and rows read of the roofline come from direct calls of
-        # the same kernel on the same batches (the graph hides per-kernel events)
-        n_roof = min(args.steps, 20)
-        for i in range(n_roof):
-            flush.zero_()
-            one_step(i)
-            st = g.last_query_stats()
-            probed += st["keys_probed"] * args.steps / n_roof
-            rows_read += st["rows_read"] * args.steps / n_roof
-            qk_ms.append(st["query_kernel_ms"] * args.steps / n_roof)
-            n_ids += st["n_results"] * args.steps / n_roof
     if dist:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
+    qk_timing = "CUDA events recorded by nodes of the replayed graph around the query kernel" if plans else \
+        "CUDA events recorded by the library on the call's stream around the query kernel"
+    if plans and not all(x > 0 for x in qk_ms):
+        # the graph was captured without its timing nodes: time the same kernel
+        # on the same batches through direct calls, after the timed region
+        qk_timing = "direct calls of the same batches after the timed region (graph without timing nodes)"
+        qk_ms, probed, rows_read, n_ids = [], 0, 0, 0
+        for i in range(args.steps):
+            flush.zero_()
+            one_step(i)
+            st = g.last_query_stats()
+            probed += st["keys_probed"]
+            rows_read += st["rows_read"]
+            qk_ms.append(st["query_kernel_ms"])
+            n_ids += st["n_results"]
     total_ms = sum(step_ms)
 
     # ---- end to end through the same call with host buffers ----
@@ -575,6 +585,7 @@ def run_ours(args):
                         f"per step (scale {args.scale})",
             "parallelism": f"replicas x{world} (one index per GPU, disjoint batches)",
             "api": "CUDA-graph plan replay" if plans else "rambo_query_*_into call",
+            "autotuned": bool(tuned),
             "l2": f"flushed before every step (256 MiB write); index {g.info().index_bytes / 2**30:.1f} GiB",
             "batches": len(batches),
         },
@@ -593,6 +604,7 @@ def run_ours(args):
             "rows_read_per_step": rows_read / args.steps,
             "rows_per_submitted_key": rows_read / max(keys, 1),
             "query_kernel_ms_per_step": qk_total / args.steps,
+            "kernel_timing": qk_timing,
         },
         "random_row_roofline": rr,
         "construction": {"keys": build_keys, "ms": build_ms, "keys_per_s": build_keys / (build_ms / 1000)},

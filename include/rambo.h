@@ -124,7 +124,9 @@ uint32_t rambo_node_of(const rambo_t *h, uint64_t set_id);
  * device required; RAMBO_EINVAL otherwise). */
 int rambo_merge(rambo_t *dst, const rambo_t *src, void *stream);
 
-/* Releases all device and host memory of the handle (NULL is ignored). */
+/* Releases all device and host memory of the handle (NULL is ignored).
+ * Destroy the handle's plans and servers first: their captured graphs point
+ * into its memory. */
 void rambo_destroy(rambo_t *h);
 
 int rambo_get_info(const rambo_t *h, rambo_info_t *out);
@@ -196,14 +198,17 @@ int rambo_query_seq_batch_into(rambo_t *h, const uint8_t *bases, const uint64_t 
  * computes exactly what rambo_query_seq_batch_into computes; every pointer
  * (bases, offsets, ids, id_offsets) is device memory owned by the caller.
  * Its working memory (2-bit packed bases, per-query counts and staged IDs)
- * is one array of 30 MiB (31,459,584 bytes) in device global memory that the
- * library reserves on every GPU it is loaded on, held until the process exits.  Limits: at most
+ * is one array of 30 MiB (31,459,072 bytes) in device global memory on every
+ * GPU the library is used on, held until the process exits.  Limits: at most
  * 2^19 queries, 2^25 bases (offsets[n] - offsets[0]) and 4,194,304 result IDs
  * staged per call; larger requests return RAMBO_E2BIG before any kernel runs
  * (results beyond the staging limit are detected after the query kernel and
- * also return RAMBO_E2BIG).  The first call on each device finds the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls share the one array: each
+ * also return RAMBO_E2BIG).  rambo_create and rambo_load, which allocate
+ * anyway, do the set-up with the handle's device current: they look up the
+ * array's device address (cudaGetSymbolAddress, which under lazy module
+ * loading is also when the array is reserved on that device) and load every
+ * kernel this call can launch, so the call itself neither allocates nor
+ * loads code.  All calls share the one array: each
  * call first clears the counters that must start at zero, so results never
  * depend on earlier calls, but calls that overlap on the GPU (several streams
  * or threads at once) race on it and must be serialised by the caller.
@@ -260,6 +265,14 @@ int rambo_plan_wait(rambo_plan_t *p, int to_host, const uint32_t **ids, const ui
                     uint64_t *n_ids, void *stream);
 /* Kernels one replay launches (inside the graph). */
 int rambo_plan_launches_per_replay(const rambo_plan_t *p);
+/* Work and time of the plan's last batch, valid after a successful
+ * rambo_plan_wait (fields as in rambo_query_stats_t, defined below; the
+ * counters come from the batch's own status block).  query_kernel_ms and
+ * device_ms come from CUDA events that nodes of the captured graph record
+ * around the query kernel and around the whole replay; both are 0 if the
+ * graph could not be captured with those nodes. */
+struct rambo_query_stats;
+int rambo_plan_last_stats(const rambo_plan_t *p, struct rambo_query_stats *out);
 
 /* ---- Continuous-batching server (no counterpart in the paper; uses Sec.
  * 3.1's streaming updates) ----
@@ -346,7 +359,9 @@ int rambo_suggest_params(uint64_t K, double n_mean, double V, double p, double d
  * would have built from the same inserts, because the partition hash mod B
  * then mod B/2 equals the hash mod B/2 (for a stacked handle every set's
  * cell becomes its cell mod B/2).  Resets the query configuration.
- * Errors: RAMBO_EINVAL when B is odd or 1, RAMBO_ENOMEM. */
+ * Errors: RAMBO_EINVAL when B is odd or 1, RAMBO_ENOMEM, RAMBO_ESTATE while
+ * a plan or server created from the handle exists (folding replaces the
+ * device buffers their captured graphs read; nothing is launched). */
 int rambo_fold(rambo_t *h, void *stream);
 
 /* Number of set bits of every Bloom filter, out[r*B + b] (host memory, R*B

@@ -43,6 +43,20 @@ int query_max_blocks_per_sm(int V, int G, uint32_t eta, bool grouped, int warps_
     return nb;
 }
 
+cudaError_t load_query_kernels(uint32_t eta) {
+    static const int vg[][2] = {{1, 1}, {2, 1}, {1, 2}, {4, 1}, {2, 2}, {4, 2}, {2, 4},
+                                {4, 4}, {2, 8}, {1, 16}, {4, 8}, {4, 16}, {4, 32}};
+    for (auto& p : vg)
+        for (int grouped = 0; grouped < 2; ++grouped) {
+            const void* f = kernel_ptr(p[0], p[1], eta, grouped != 0);
+            if (!f) continue;
+            cudaFuncAttributes a;
+            const cudaError_t e = cudaFuncGetAttributes(&a, f);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
 unsigned query_group_size(uint64_t n, int group, unsigned wpb, uint64_t group_warps, int use_bitmap) {
     return qk_group_size(n, group, wpb, group_warps, use_bitmap);
 }

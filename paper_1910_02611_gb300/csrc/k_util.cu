@@ -476,6 +476,26 @@ cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_
 }
 
 // ---------------------------------------------------------------------------
+// Loads the kernels of a sequence query other than the query kernel itself
+// (status reset, validation, packing, bad-base lookup, scans, gather):
+// cudaFuncGetAttributes makes the runtime load a kernel that lazy module
+// loading would otherwise load at its first launch.
+
+cudaError_t load_util_kernels() {
+    const void* fns[] = {reinterpret_cast<const void*>(&k_status_reset), reinterpret_cast<const void*>(&k_validate),
+                         reinterpret_cast<const void*>(&k_pack), reinterpret_cast<const void*>(&k_resolve_bad_base),
+                         reinterpret_cast<const void*>(&k_scan_one_block), reinterpret_cast<const void*>(&k_scan_tiles),
+                         reinterpret_cast<const void*>(&k_scan_sums), reinterpret_cast<const void*>(&k_scan_add),
+                         reinterpret_cast<const void*>(&k_gather)};
+    for (const void* f : fns) {
+        cudaFuncAttributes a;
+        const cudaError_t e = cudaFuncGetAttributes(&a, f);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
 // folding over (appendix): cell b of the folded index is the OR of cells b and
 // b + B/2.  Each thread rewrites whole rows from the old layout (W words,
 // stride S) into the new one (W2 words, stride S2).

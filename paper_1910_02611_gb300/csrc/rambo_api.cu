@@ -138,6 +138,8 @@ struct rambo {
     uint64_t last_err_item = 0;
     // automatic block size: last (V, G, use_bitmap) resolved and its choice
     int auto_key = -1, auto_wpb = 0, auto_per_sm = 0;
+    std::vector<rambo_plan_t*> plans;   // live plans (own or a server's) holding captured pointers
+    unsigned char* na_base = nullptr;   // device address of the no-alloc query's fixed scratch
 
     IndexView view() const {
         IndexView v;
@@ -165,6 +167,8 @@ namespace {
 
 void free_handle(rambo* h) {
     if (!h) return;
+    for (rambo_plan_t* p : h->plans) plan_orphan(p);
+    h->plans.clear();
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(h->device);
@@ -651,6 +655,21 @@ int handle_query_view(rambo_t* h, uint64_t n, IndexView* ix, HashParams* hp, Que
     *device = h->device;
     return RAMBO_OK;
 }
+
+void handle_attach_plan(rambo_t* h, rambo_plan_t* p) {
+    if (h) h->plans.push_back(p);
+}
+
+void handle_detach_plan(rambo_t* h, rambo_plan_t* p) {
+    if (!h) return;
+    for (size_t i = 0; i < h->plans.size(); ++i)
+        if (h->plans[i] == p) {
+            h->plans.erase(h->plans.begin() + (long)i);
+            return;
+        }
+}
+
+unsigned char* handle_noalloc_base(const rambo_t* h) { return h ? h->na_base : nullptr; }
 }  // namespace rgb
 
 // ===========================================================================
@@ -724,6 +743,10 @@ static int create_impl(uint64_t K, uint32_t B_local, uint32_t n_nodes, uint32_t 
     rc = build_cell_members(h, s);
     if (rc) return fail(rc);
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(RAMBO_ECUDA);
+    // the no-alloc query's scratch address and kernels, so that its calls
+    // load and reserve nothing themselves
+    rc = noalloc_setup(eta, &h->na_base);
+    if (rc) return fail(rc);
     default_config(h);
     *out = h;
     return RAMBO_OK;
@@ -1055,6 +1078,9 @@ int rambo_autotune(rambo_t* h, int kind, const void* data, const uint64_t* offse
 
 int rambo_fold(rambo_t* h, void* stream) {
     if (!h || h->B < 2 || (h->B & 1)) return RAMBO_EINVAL;
+    // folding frees and reallocates the rows and the set-stage tables that
+    // a live plan's captured graph points to
+    if (!h->plans.empty()) return RAMBO_ESTATE;
     CK(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t B2 = h->B / 2, W2 = (B2 + 31) / 32, S2 = stride_for(W2);

@@ -278,6 +278,25 @@ cudaError_t launch_query_one(const IndexView& ix, const HashParams& hp, int seq,
 // rambo_api.cu: what the fixed-scratch entry point needs from a handle
 int handle_query_view(rambo_t* h, uint64_t n, IndexView* ix, HashParams* hp, QueryTuning* t, int* use_bitmap,
                       int* device);
+// rambo_api.cu: plans hold device pointers of their handle inside a captured
+// graph; the handle keeps a list of them, refuses calls that would move those
+// buffers while any is alive, and orphans them (plan_orphan, rambo_plan.cu)
+// when it is destroyed first, so they neither launch nor touch it again
+void handle_attach_plan(rambo_t* h, rambo_plan_t* p);
+void handle_detach_plan(rambo_t* h, rambo_plan_t* p);
+void plan_orphan(rambo_plan_t* p);
+// rambo_api.cu: device address of the fixed scratch, found when the handle was created
+unsigned char* handle_noalloc_base(const rambo_t* h);
+
+// rambo_noalloc.cu: with the handle's device current, finds the device
+// address of the fixed scratch array and loads every kernel the no-alloc
+// query can launch (eta selects the query-kernel instances), so that its
+// calls need no module loading later
+int noalloc_setup(uint32_t eta, unsigned char** base);
+
+// kernel loading (lazy module loading otherwise loads a kernel at its first launch)
+cudaError_t load_util_kernels();
+cudaError_t load_query_kernels(uint32_t eta);
 
 // k_roofline.cu
 cudaError_t launch_random_rows(const uint32_t* buf, uint64_t n_rows, uint32_t row_words,

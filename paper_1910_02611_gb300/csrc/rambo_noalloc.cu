@@ -2,18 +2,24 @@
 // callers that cannot allocate device memory while they query.
 //
 // It runs the same kernels as rambo_query_seq_batch_into, but every byte of
-// working memory comes from one file-scope __device__ array reserved when the
-// library is loaded, instead of buffers the handle grows with cudaMalloc.  The
-// call itself allocates nothing (no cudaMalloc, cudaFree or allocating library
-// routine); it only launches kernels and copies a few words back to the stack.
+// working memory comes from one file-scope __device__ array instead of
+// buffers the handle grows with cudaMalloc.  The call itself allocates
+// nothing (no cudaMalloc, cudaFree or allocating library routine); it only
+// launches kernels and copies a few words back to the stack.
+//
+// Set-up happens in rambo_create / rambo_load (which allocate anyway), with
+// the handle's device current: cudaGetSymbolAddress gives the array's device
+// address (under lazy module loading this is also when the array is
+// reserved on that device), and every kernel the call can launch is loaded,
+// so the first query does not load modules either.  The address is kept in
+// the handle, so a handle created after a cudaDeviceReset holds the address
+// of that new context.
 //
 // The array is shared by every call on a device and keeps the previous call's
 // contents; the status reset at the start of each call clears everything that
 // must start at zero (error word, work-queue ticket, result cursor, counters),
 // and all other regions are fully written before they are read.  Calls that
 // overlap on the GPU race on the array.
-#include <mutex>
-
 #include "rambo_impl.cuh"
 
 using namespace rgb;
@@ -37,13 +43,9 @@ constexpr uint64_t OFF_QSTART = align256(OFF_QCOUNT + NA_MAX_QUERIES * 4);
 constexpr uint64_t OFF_SCAN = align256(OFF_QSTART + NA_MAX_QUERIES * 8);
 constexpr uint64_t OFF_STAGE = align256(OFF_SCAN + NA_SCAN_WORDS * 8);
 constexpr uint64_t NA_SCRATCH_BYTES = align256(OFF_STAGE + NA_STAGE_IDS * 4);
-static_assert(NA_SCRATCH_BYTES < (32ull << 20), "fixed scratch stays under 32 MiB");
-
-constexpr int NA_MAX_DEVICES = 64;
-
-// host-side pointers to each device's copy of the array, found once per device
-std::mutex g_mu;
-unsigned char* g_base[NA_MAX_DEVICES] = {};
+// the size the header states for the array
+static_assert(sizeof(DevStatus) <= 256, "status block fits its 256-byte slot");
+static_assert(NA_SCRATCH_BYTES == 31459072ull, "fixed scratch is the 31,459,072 bytes the header states");
 
 int map_cuda(cudaError_t e) {
     if (e == cudaSuccess) return RAMBO_OK;
@@ -56,21 +58,28 @@ int map_cuda(cudaError_t e) {
 // device address: host code must use the address cudaGetSymbolAddress gives.
 static __device__ __align__(256) unsigned char na_scratch[NA_SCRATCH_BYTES];
 
-namespace {
+namespace rgb {
 
-// Device address of na_scratch on device dev (which must be current).
-int scratch_base(int dev, unsigned char** out) {
-    if (dev < 0 || dev >= NA_MAX_DEVICES) return RAMBO_EINVAL;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_base[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, na_scratch);
-        if (e != cudaSuccess || !p) return map_cuda(e == cudaSuccess ? cudaErrorUnknown : e);
-        g_base[dev] = static_cast<unsigned char*>(p);
+int noalloc_setup(uint32_t eta, unsigned char** base) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, na_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return map_cuda(e == cudaSuccess ? cudaErrorUnknown : e);
     }
-    *out = g_base[dev];
+    e = load_util_kernels();
+    if (e == cudaSuccess) e = load_query_kernels(eta);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return map_cuda(e);
+    }
+    *base = static_cast<unsigned char*>(p);
     return RAMBO_OK;
 }
+
+}  // namespace rgb
+
+namespace {
 
 int decode(unsigned long long e) {
     if (e == NO_ERR) return RAMBO_OK;
@@ -108,9 +117,8 @@ extern "C" int rambo_query_seq_batch_noalloc(rambo_t* h, const uint8_t* bases, c
     int rc = handle_query_view(h, n ? n : 1, &ix, &hp, &t, &use_bitmap, &dev);
     if (rc) return rc;
     NA_CK(cudaSetDevice(dev));
-    unsigned char* base = nullptr;
-    rc = scratch_base(dev, &base);
-    if (rc) return rc;
+    unsigned char* base = handle_noalloc_base(h);
+    if (!base) return RAMBO_ESTATE;
     if (n == 0) {
         NA_CK(cudaMemsetAsync(id_offsets, 0, sizeof(uint64_t), s));
         NA_CK(cudaStreamSynchronize(s));

@@ -71,8 +71,14 @@ struct rambo_plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev_done = nullptr;
+    // timing events recorded by nodes of the graph itself: replay start,
+    // query kernel start and end, replay end (null when not captured)
+    cudaEvent_t ev_t[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool timed = false;
+    rambo_query_stats_t last{};
     uint64_t launched_n = 0;
     bool busy = false;
+    bool attached = false;  // counted in the handle's live plans
     int launches_per_replay = 0;
 };
 
@@ -80,10 +86,13 @@ namespace {
 
 void plan_free(rambo_plan* p) {
     if (!p) return;
+    if (p->attached && p->h) handle_detach_plan(p->h, p);
     cudaSetDevice(p->device);
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->ev_done) cudaEventDestroy(p->ev_done);
+    for (cudaEvent_t e : p->ev_t)
+        if (e) cudaEventDestroy(e);
     if (p->cap) cudaStreamDestroy(p->cap);
     void* dev[] = {p->d_data, p->d_off, p->d_packed, p->qcount, p->qstart, p->scan_tmp,
                    p->stage, p->ids, p->id_off, p->st, p->d_desc};
@@ -95,7 +104,12 @@ void plan_free(rambo_plan* p) {
     delete p;
 }
 
-int plan_capture(rambo_plan* p) {
+// Records timing event i inside the captured graph (an event-record node).
+cudaError_t mark(rambo_plan* p, int i, cudaStream_t s, bool timed) {
+    return timed ? cudaEventRecordWithFlags(p->ev_t[i], s, cudaEventRecordExternal) : cudaSuccess;
+}
+
+int plan_capture(rambo_plan* p, bool timed) {
     IndexView ix;
     HashParams hp;
     QueryTuning t;
@@ -116,7 +130,8 @@ int plan_capture(rambo_plan* p) {
     const uint64_t scan_words = scan_tmp_words(p->max_q);
     cudaStream_t s = p->cap;
     PK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemcpyAsync(p->d_desc, p->h_desc, 2 * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+    cudaError_t e = mark(p, 0, s, timed);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_desc, p->h_desc, 2 * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
     int n_launch = 0;
     if (e == cudaSuccess) e = launch_status_reset(p->st, s), ++n_launch;
     if (e == cudaSuccess) e = launch_validate_batch(b, p->kind ? p->k : 1, ix.K, p->st, s), ++n_launch;
@@ -126,11 +141,13 @@ int plan_capture(rambo_plan* p) {
         n_launch += 2;
     }
     QueryOut o{p->stage, p->max_ids, p->qstart, p->qcount};
+    if (e == cudaSuccess) e = mark(p, 1, s, timed);
     if (e == cudaSuccess) {
         int nq = 0;
         e = launch_query(ix, hp, b, o, t, use_bitmap, p->st, s, &nq);
         n_launch += nq;
     }
+    if (e == cudaSuccess) e = mark(p, 2, s, timed);
     if (e == cudaSuccess) {
         int n_scan = 0;
         e = launch_scan_counts(p->qcount, p->max_q, p->id_off, p->scan_tmp, scan_words, s, p->d_desc, &n_scan);
@@ -143,6 +160,7 @@ int plan_capture(rambo_plan* p) {
         e = cudaGetLastError();
         ++n_launch;
     }
+    if (e == cudaSuccess) e = mark(p, 3, s, timed);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->h_st, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
@@ -154,6 +172,7 @@ int plan_capture(rambo_plan* p) {
     p->graph = g;
     PK(cudaGraphInstantiate(&p->exec, g, 0));
     p->launches_per_replay = n_launch;
+    p->timed = timed;
     return RAMBO_OK;
 }
 
@@ -168,6 +187,18 @@ int decode(unsigned long long e) {
 }
 
 }  // namespace
+
+namespace rgb {
+// The plan's handle is being destroyed: its captured graph now points to freed
+// memory, so the plan forgets the handle and refuses further launches.
+void plan_orphan(rambo_plan_t* p) {
+    if (!p) return;
+    if (p->busy) cudaEventSynchronize(p->ev_done);
+    p->busy = false;
+    p->h = nullptr;
+    p->attached = false;
+}
+}  // namespace rgb
 
 extern "C" {
 
@@ -224,10 +255,20 @@ int rambo_plan_create(rambo_t* h, int kind, uint64_t max_queries, uint64_t max_i
     if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming) != cudaSuccess)
         return fail(RAMBO_ECUDA);
+    for (cudaEvent_t& ev : p->ev_t)
+        if (cudaEventCreate(&ev) != cudaSuccess) return fail(RAMBO_ECUDA);
     p->h_desc[0] = 0;
     p->h_desc[1] = 0;
-    rc = plan_capture(p);
+    // with timing nodes first; a graph without them answers the same
+    rc = plan_capture(p, true);
+    if (rc == RAMBO_ECUDA) {
+        if (p->graph) cudaGraphDestroy(p->graph);
+        p->graph = nullptr;
+        rc = plan_capture(p, false);
+    }
     if (rc) return fail(rc);
+    handle_attach_plan(h, p);
+    p->attached = true;
     *out = p;
     return RAMBO_OK;
 }
@@ -249,7 +290,7 @@ int rambo_plan_buffers(rambo_plan_t* p, void** host_data, uint64_t** host_offset
 
 int rambo_plan_launch(rambo_plan_t* p, uint64_t n_queries, uint64_t n_items, int from_host, void* stream) {
     if (!p || n_queries == 0) return RAMBO_EINVAL;
-    if (p->busy) return RAMBO_ESTATE;
+    if (p->busy || !p->h) return RAMBO_ESTATE;  // running, or its handle was destroyed
     if (n_queries > p->max_q || n_items > p->max_items) return RAMBO_E2BIG;
     cudaStream_t s = (cudaStream_t)stream;
     PK(cudaSetDevice(p->device));
@@ -285,6 +326,18 @@ int rambo_plan_wait(rambo_plan_t* p, int to_host, const uint32_t** ids, const ui
     int rc = decode(st.err);
     if (rc) return rc;
     const uint64_t total = st.spare[1];
+    p->last = rambo_query_stats_t{};
+    p->last.n_queries = p->launched_n;
+    p->last.keys_submitted = p->kind == 1 ? p->h_desc[1] - p->launched_n * (uint64_t)(p->k - 1) : p->h_desc[1];
+    p->last.keys_probed = st.keys_probed;
+    p->last.rows_read = st.rows_read;
+    p->last.n_results = total;
+    p->last.kernel_launches = (uint64_t)p->launches_per_replay;
+    for (int i = 0; i < 4; ++i) p->last.stage_queries[i] = st.stage_count[i];
+    if (p->timed) {
+        PK(cudaEventElapsedTime(&p->last.query_kernel_ms, p->ev_t[1], p->ev_t[2]));
+        PK(cudaEventElapsedTime(&p->last.device_ms, p->ev_t[0], p->ev_t[3]));
+    }
     if (n_ids) *n_ids = total;
     if (st.cursor > p->max_ids || total > p->max_ids) return RAMBO_ENOSPC;
     const uint64_t n = p->launched_n;
@@ -303,5 +356,11 @@ int rambo_plan_wait(rambo_plan_t* p, int to_host, const uint32_t** ids, const ui
 }
 
 int rambo_plan_launches_per_replay(const rambo_plan_t* p) { return p ? p->launches_per_replay : 0; }
+
+int rambo_plan_last_stats(const rambo_plan_t* p, rambo_query_stats_t* out) {
+    if (!p || !out) return RAMBO_EINVAL;
+    *out = p->last;
+    return RAMBO_OK;
+}
 
 }  // extern "C"

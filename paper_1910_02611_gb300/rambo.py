@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -87,6 +88,7 @@ SIGNATURES = {
     "rambo_plan_poll": (_i32, [_p]),
     "rambo_plan_wait": (_i32, [_p, _i32, C.POINTER(_p), C.POINTER(_p), C.POINTER(_u64), _p]),
     "rambo_plan_launches_per_replay": (_i32, [_p]),
+    "rambo_plan_last_stats": (_i32, [_p, C.POINTER(QueryStats)]),
     "rambo_server_create": (_i32, [_p, C.POINTER(ServerConfig), C.POINTER(_p)]),
     "rambo_server_submit": (_i32, [_p, _i32, _p, _u64, C.POINTER(_u64)]),
     "rambo_server_submit_insert": (_i32, [_p, _i32, _p, _p, _p, _u64, C.POINTER(_u64)]),
@@ -212,6 +214,9 @@ class Rambo:
             self._h = h
         else:
             self._h = _handle
+        # plans and servers created over this index, closed before it is
+        # (their captured graphs and worker threads use its memory)
+        self._dependents = weakref.WeakSet()
         info = self.info()
         self.K, self.B, self.R, self.m, self.eta, self.seed = info.K, info.B, info.R, info.m, info.eta, info.seed
         self.row_stride = info.row_stride
@@ -243,6 +248,8 @@ class Rambo:
         return cls(0, 0, 0, 0, 0, _handle=h)
 
     def close(self) -> None:
+        for d in list(getattr(self, "_dependents", ())):
+            d.close()
         h = getattr(self, "_h", None)
         if h is not None and h.value:
             load_library().rambo_destroy(h)
@@ -502,6 +509,7 @@ class Plan:
         if rc:
             raise RamboError(rc, "rambo_plan_create")
         self._p = h
+        index._dependents.add(self)
         hd, ho, dd, do = _p(), _p(), _p(), _p()
         L.rambo_plan_buffers(h, C.byref(hd), C.byref(ho), C.byref(dd), C.byref(do))
         self._elem = 8 if kind == "keys" else 1
@@ -574,6 +582,18 @@ class Plan:
             return ids, offs
         return _device_copy(ids_p.value or 0, total, "<u4"), _device_copy(off_p.value, n + 1, "<u8")
 
+    def last_stats(self) -> dict:
+        """Counters and CUDA-event times of the last waited batch (rambo_plan_last_stats)."""
+        st = QueryStats()
+        rc = load_library().rambo_plan_last_stats(self._p, C.byref(st))
+        if rc:
+            raise RamboError(rc, "rambo_plan_last_stats")
+        out = {}
+        for f, _ in st._fields_:
+            v = getattr(st, f)
+            out[f] = float(v) if f.endswith("_ms") else (list(v) if f == "stage_queries" else int(v))
+        return out
+
 
 class Server:
     """Continuous-batching query server over an index (rambo_server_*)."""
@@ -587,6 +607,7 @@ class Server:
             raise RamboError(rc, "rambo_server_create")
         self._s = h
         self._index = index
+        index._dependents.add(self)
         self.max_batch_ids = max_batch_ids
 
     def submit(self, data, kind: str = "seq") -> int:

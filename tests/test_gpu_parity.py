@@ -397,6 +397,38 @@ def test_folding_over_equals_an_index_built_with_half_the_cells(mods, B, folds):
     assert np.array_equal(direct.export_index(), g.export_index())
 
 
+def test_fold_is_refused_while_a_plan_holds_the_index(mods):
+    # A plan's captured graph reads the handle's rows and set-stage tables;
+    # folding replaces them, so it must be refused (RAMBO_ESTATE, index
+    # untouched) while the plan lives, and allowed once it is gone.
+    from paper_1910_02611_gb300 import ESTATE, Plan, RamboError
+
+    Rambo, Oracle = mods
+    w = synth.make("genome", 0.01, m=1 << 15, B=64, R=4)
+    g = Rambo(w.K, 64, w.R, w.m, w.eta, w.seed)
+    g.insert(w.sets.ids, w.sets.data, w.sets.offsets, kind="seq")
+    before = g.export_index()
+    q = w.queries.subset(np.arange(50))
+    plan = Plan(g, "seq", max_queries=64, max_items=int(q.offsets[-1]) + 64, max_ids=1 << 16)
+    plan.launch_host(q.data, q.offsets)
+    ids_a, off_a = plan.wait()
+    with pytest.raises(RamboError) as e:
+        g.fold()
+    assert e.value.code == ESTATE
+    assert g.B == 64 and np.array_equal(g.export_index(), before)
+    # the plan still answers as before
+    plan.launch_host(q.data, q.offsets)
+    ids_b, off_b = plan.wait()
+    assert np.array_equal(ids_a, ids_b) and np.array_equal(off_a, off_b)
+    plan.close()
+    g.fold()
+    assert g.B == 32
+    o = Oracle(w.K, 32, w.R, w.m, w.eta, w.seed)
+    o.insert_seq_batch(w.sets.ids, w.sets.data, w.sets.offsets, 31)
+    assert_index_equal(g, o)
+    g.close()
+
+
 def test_single_set_insert_host_and_device(mods):
     import torch
 

@@ -71,3 +71,61 @@ def test_noalloc_rejects_requests_beyond_its_fixed_scratch():
             g.query_seq_noalloc(qd, qo, torch.empty(n_ref - 1, dtype=torch.int32, device=dev), off)
         assert e.value.code == ENOSPC
     g.close()
+
+
+def test_noalloc_large_batch_takes_the_multi_pass_scan():
+    # more than 32768 queries: the count scan runs as three kernels over the
+    # fixed scan region instead of one block
+    import torch
+
+    from paper_1910_02611_gb300 import Rambo
+
+    dev = torch.device("cuda")
+    w = synth.make("genome", 0.02, m=1 << 18)
+    g = Rambo(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    g.insert(w.sets.ids, w.sets.data, w.sets.offsets, kind="seq", k=w.k)
+    rng = np.random.default_rng(77)
+    q = synth.substring_queries(rng, w.sets, np.full(40_000, 31), max_subst=0.0)
+    qd = torch.from_numpy(q.data).to(dev)
+    qo = torch.from_numpy(q.offsets.view(np.int64)).to(dev)
+    ref_ids = torch.empty(1 << 22, dtype=torch.int32, device=dev)
+    ref_off = torch.empty(len(q) + 1, dtype=torch.int64, device=dev)
+    n_ref = g.query_into(qd, qo, ref_ids, ref_off, kind="seq", k=w.k)
+    for _ in range(2):
+        ids = torch.full((1 << 22,), -1, dtype=torch.int32, device=dev)
+        off = torch.full((len(q) + 1,), -1, dtype=torch.int64, device=dev)
+        n = g.query_seq_noalloc(qd, qo, ids, off, k=w.k)
+        assert n == n_ref and n >= len(q)  # every query is an exact substring: at least its own set
+        assert torch.equal(off, ref_off)
+        assert torch.equal(ids[:n], ref_ids[:n_ref])
+    g.close()
+
+
+def test_noalloc_reports_e2big_when_staged_ids_exceed_its_limit():
+    # an index whose filters are all ones answers every query with every set:
+    # 1100 queries x 4096 sets = 4,505,600 IDs > the 4,194,304 staging limit
+    import torch
+
+    from paper_1910_02611_gb300 import E2BIG, Rambo, RamboError
+
+    dev = torch.device("cuda")
+    K = 4096
+    g = Rambo(K, 64, 2, 1 << 6, 1, 42)
+    rng = np.random.default_rng(5)
+    sets = synth.random_bases(rng, K * 300)
+    off = np.arange(K + 1, dtype=np.uint64) * np.uint64(300)
+    g.insert(np.arange(K, dtype=np.uint64), sets, off, kind="seq", k=31)
+    qb = synth.random_bases(rng, 1100 * 31)
+    qd = torch.from_numpy(qb).to(dev)
+    qo = torch.from_numpy((np.arange(1101, dtype=np.int64) * 31)).to(dev)
+    ids = torch.empty(1 << 23, dtype=torch.int32, device=dev)
+    out_off = torch.empty(1101, dtype=torch.int64, device=dev)
+    n_ref = g.query_into(qd, qo, ids, out_off, kind="seq", k=31)
+    assert n_ref == 1100 * K
+    with pytest.raises(RamboError) as e:
+        g.query_seq_noalloc(qd, qo, ids, out_off, k=31)
+    assert e.value.code == E2BIG
+    # a batch within the limit still answers, after the failed call
+    n = g.query_seq_noalloc(qd[: 1000 * 31], qo[:1001], ids, out_off[:1001], k=31)
+    assert n == 1000 * K
+    g.close()

@@ -45,7 +45,9 @@
  *     between tables.
  *   k-mer key: bases A/a=0, C/c=1, G/g=2, T/t=3; the window starting at p is
  *     sum_{t<k} code(seq[p+t]) * 4^(k-1-t) (first base most significant),
- *     1 <= k <= 32.  Any other byte is an error.
+ *     1 <= k <= 32.  Any other byte is an error, unless the k argument
+ *     carries ORC_SKIPN: then every window holding such a byte is skipped
+ *     and a query sequence with no other window is an error.
  *
  * Parity pins: tests/test_oracle_*.py (SplitMix64 published outputs, big-int
  * arithmetic for phi, closed forms for k-mers, brute-force exact MSMT on tiny
@@ -130,6 +132,19 @@ int orc_base_code(uint8_t ch) {
  * window and its reverse complement (the same DNA read on the other strand:
  * bases in reverse order, A<->T and C<->G, i.e. code c -> 3 - c). */
 #define ORC_CANONICAL 0x100u
+/* k may carry ORC_SKIPN: a byte outside ACGTacgt (an unresolved base such as
+ * N) no longer rejects the sequence; every window that holds one is left
+ * out, and the sequence's terms are its other windows (Sec. 3.2.1's sliding
+ * window over the resolved stretches of the read). */
+#define ORC_SKIPN 0x200u
+#define ORC_KFLAGS (0xffu | ORC_CANONICAL | ORC_SKIPN)
+
+/* 1 when the k bytes seq[p .. p+k) are all in ACGTacgt. */
+static int window_valid(const uint8_t *seq, uint64_t p, uint32_t k) {
+    for (uint32_t t = 0; t < k; ++t)
+        if (orc_base_code(seq[p + t]) < 0) return 0;
+    return 1;
+}
 
 /* Key of the window seq[p .. p+k): forward, or canonical. */
 static uint64_t window_key(const uint8_t *seq, uint64_t p, uint32_t k, int canon) {
@@ -140,19 +155,26 @@ static uint64_t window_key(const uint8_t *seq, uint64_t p, uint32_t k, int canon
     return rc < fwd ? rc : fwd;
 }
 
-/* Writes the n-k+1 window keys of seq into out (if out != NULL).  Returns the
- * number of windows (0 when n < k) or ORC_EBADSEQ on a byte outside ACGTacgt,
- * or ORC_EINVAL for k outside [1,32] (or unknown flag bits). */
+/* Writes the window keys of seq into out (if out != NULL), in window order.
+ * Returns the number of windows: n-k+1 (0 when n < k), or with ORC_SKIPN the
+ * number of windows free of bytes outside ACGTacgt.  Without ORC_SKIPN such
+ * a byte anywhere gives ORC_EBADSEQ.  ORC_EINVAL for k outside [1,32] (or
+ * unknown flag bits). */
 int64_t orc_kmers(const uint8_t *seq, uint64_t n, uint32_t kflags, uint64_t *out) {
     const uint32_t k = kflags & 0xffu;
     const int canon = (kflags & ORC_CANONICAL) != 0;
-    if (k < 1 || k > 32 || (kflags & ~(0xffu | ORC_CANONICAL))) return ORC_EINVAL;
-    for (uint64_t p = 0; p < n; ++p)
-        if (orc_base_code(seq[p]) < 0) return ORC_EBADSEQ;
+    const int skipn = (kflags & ORC_SKIPN) != 0;
+    if (k < 1 || k > 32 || (kflags & ~ORC_KFLAGS)) return ORC_EINVAL;
+    if (!skipn)
+        for (uint64_t p = 0; p < n; ++p)
+            if (orc_base_code(seq[p]) < 0) return ORC_EBADSEQ;
     if (n < k) return 0;
-    uint64_t nw = n - k + 1;
-    if (out)
-        for (uint64_t p = 0; p < nw; ++p) out[p] = window_key(seq, p, k, canon);
+    uint64_t nw = 0;
+    for (uint64_t p = 0; p + k <= n; ++p) {
+        if (skipn && !window_valid(seq, p, k)) continue;
+        if (out) out[nw] = window_key(seq, p, k, canon);
+        ++nw;
+    }
     return (int64_t)nw;
 }
 
@@ -325,7 +347,8 @@ int orc_insert_seq_batch(orc_t *o, const uint64_t *set_ids, const uint8_t *seq,
                          int nthreads) {
     const uint32_t k = kflags & 0xffu;
     const int canon = (kflags & ORC_CANONICAL) != 0;
-    if (k < 1 || k > 32 || (kflags & ~(0xffu | ORC_CANONICAL))) return ORC_EINVAL;
+    const int skipn = (kflags & ORC_SKIPN) != 0;
+    if (k < 1 || k > 32 || (kflags & ~ORC_KFLAGS)) return ORC_EINVAL;
     for (uint64_t t = 0; t < n_sets; ++t) {
         if (set_ids[t] >= o->K) return ORC_ERANGE;
         if (offsets[t + 1] < offsets[t]) return ORC_EINVAL;
@@ -341,7 +364,9 @@ int orc_insert_seq_batch(orc_t *o, const uint64_t *set_ids, const uint8_t *seq,
         me = omp_get_thread_num();
         nt = omp_get_num_threads();
 #endif
-        /* the window key, kept by dropping the oldest base and appending the next */
+        /* the window key, kept by dropping the oldest base and appending the
+         * next; `run` counts the resolved bases ending at p (with ORC_SKIPN a
+         * window is inserted only when all k of its bases are resolved) */
         uint64_t mask = k == 32 ? ~0ULL : ((1ULL << (2 * k)) - 1);
         for (uint64_t t = 0; t < n_sets; ++t) {
             const uint8_t *s = seq + offsets[t];
@@ -350,10 +375,13 @@ int orc_insert_seq_batch(orc_t *o, const uint64_t *set_ids, const uint8_t *seq,
             for (uint32_t d = 0; d < o->R; ++d) {
                 uint32_t b = orc_phi(o, d, set_ids[t]);
                 if ((int)(((uint64_t)d * o->B + b) % (uint64_t)nt) != me) continue;
-                uint64_t v = 0;
+                uint64_t v = 0, run = 0;
                 for (uint64_t p = 0; p < n; ++p) {
-                    v = ((v << 2) | (uint64_t)orc_base_code(s[p])) & mask;
-                    if (p + 1 >= k) bf_insert(o, d, b, canon ? window_key(s, p + 1 - k, k, 1) : v);
+                    const int code = orc_base_code(s[p]);
+                    run = code < 0 ? 0 : run + 1;
+                    v = ((v << 2) | (uint64_t)(code < 0 ? 0 : code)) & mask;
+                    if (p + 1 >= k && (!skipn || run >= k))
+                        bf_insert(o, d, b, canon ? window_key(s, p + 1 - k, k, 1) : v);
                 }
             }
         }
@@ -500,14 +528,14 @@ int orc_query_batch(const orc_t *o, int kind, const void *data, const uint64_t *
                 nt = offsets[q + 1] - offsets[q];
             } else {
                 uint64_t n = offsets[q + 1] - offsets[q];
-                nt = n - (k & 0xffu) + 1;
-                if (nt > qcap) {
+                uint64_t most = n - (k & 0xffu) + 1;  /* every window; fewer with ORC_SKIPN */
+                if (most > qcap) {
                     free(Q);
-                    qcap = nt;
+                    qcap = most;
                     Q = (uint64_t *)malloc(sizeof(uint64_t) * qcap);
                     if (!Q) { ok = 0; failed = 1; continue; }
                 }
-                orc_kmers((const uint8_t *)data + offsets[q], n, k, Q);
+                nt = (uint64_t)orc_kmers((const uint8_t *)data + offsets[q], n, k, Q);
                 terms = Q;
             }
             int64_t c = query_terms(o, terms, nt, &sc, buf, o->K);

@@ -481,6 +481,11 @@ def run_ours(args):
         host_batches.append((hd.view(np.uint64) if q.kind == "keys" else hd, ho, keys_in(q, w.k), len(q)))
     e2e_s, e2e_keys, h2d, d2h = 0.0, 0, 0, 0
     n_e2e = 0 if args.no_extras else max(1, min(args.e2e_steps, args.steps))
+    # untimed warm-up over every batch: the handle's pinned result arena and
+    # input buffers reach their largest size before the timed calls
+    for i in range(min(n_e2e, len(host_batches)) if n_e2e else 0):
+        hd, ho, _, _ = host_batches[i]
+        g.query(hd, ho, kind=batches[0].kind, k=w.k, copy=False)
     e2e_wall0 = time.perf_counter()
     for i in range(n_e2e):
         if i >= 2 and time.perf_counter() - e2e_wall0 > 20.0:  # bound the end-to-end leg's wall time
@@ -527,7 +532,8 @@ def run_ours(args):
     rows_per_key = w.R * w.eta
     row_bytes = g.row_stride * 4
     sectors_per_row = (row_bytes + SECTOR - 1) // SECTOR if row_bytes <= SECTOR else -(-row_bytes // SECTOR)
-    alg_bytes = rows_read * sectors_per_row * SECTOR
+    # rows read (whole sectors) plus the 4-byte write of every result ID the kernel stages
+    alg_bytes = rows_read * sectors_per_row * SECTOR + n_ids * 4
     qk_total = sum(qk_ms)
     achieved = alg_bytes / (qk_total / 1000) / 1e9
     # random-row ceiling on a buffer the size of the index
@@ -546,8 +552,10 @@ def run_ours(args):
         ms = random_row_probe(buf, n_rows, g.row_stride, reads, blocks, 256, seed=7)
         rr_reads_s = blocks * 256 * reads / (ms / 1000)
         rr_gbs = rr_reads_s * SECTOR * sectors_per_row / 1e9
+        # the kernel's row reads per second against the ceiling's (row traffic only)
+        kernel_reads_s = rows_read / (qk_total / 1000)
         rr = {"gbs": rr_gbs, "reads_per_s": rr_reads_s, "row_bytes": row_bytes, "buffer_bytes": n_rows * row_bytes,
-              "frac_of_roofline": achieved / rr_gbs}
+              "kernel_reads_per_s": kernel_reads_s, "frac_of_roofline": kernel_reads_s / rr_reads_s}
         del buf
     except Exception as ex:  # measurement helper only
         rr = {"error": str(ex)}
@@ -600,7 +608,7 @@ def run_ours(args):
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(w.name),
             "kernel": "k_query", "peak_source": peaks["source"],
-            "bytes_model": f"rows read (device counter) x {sectors_per_row} sector(s) x 32 B",
+            "bytes_model": f"rows read (device counter) x {sectors_per_row} sector(s) x 32 B + 4 B per result ID written",
             "rows_read_per_step": rows_read / args.steps,
             "rows_per_submitted_key": rows_read / max(keys, 1),
             "query_kernel_ms_per_step": qk_total / args.steps,

@@ -59,7 +59,8 @@ enum {
     RAMBO_OK = 0,
     RAMBO_EINVAL = -1,   /* bad parameter, decreasing offsets, empty key query */
     RAMBO_ERANGE = -2,   /* set ID >= K */
-    RAMBO_EBADSEQ = -3,  /* base outside ACGTacgt, or query sequence shorter than k */
+    RAMBO_EBADSEQ = -3,  /* base outside ACGTacgt (without RAMBO_KMER_SKIP_N), or a
+                            query sequence with no k-mer window */
     RAMBO_ENOMEM = -4,   /* device or pinned host allocation failed */
     RAMBO_ENOSPC = -5,   /* caller-provided output too small (see *needed) */
     RAMBO_ECUDA = -6,    /* a CUDA runtime call failed */
@@ -76,6 +77,15 @@ enum {
 /* OR-ed into a k-mer length argument: every window's key is the smaller of
  * the window and its reverse complement (both DNA strands give one key). */
 #define RAMBO_KMER_CANONICAL 0x100u
+/* OR-ed into a k-mer length argument: a byte outside ACGTacgt (an unresolved
+ * base such as N) no longer rejects the sequence; every window holding one
+ * is skipped, and the sequence's keys are its other windows (Sec. 3.2.1's
+ * sliding window over the resolved stretches of a read; the paper's
+ * whole-genome k-mers, Sec. 5.2, come from such reads).  Inserts register a
+ * set whose sequence has no valid window, with no keys; a query sequence
+ * with no valid window is RAMBO_EBADSEQ.  Combines with
+ * RAMBO_KMER_CANONICAL. */
+#define RAMBO_KMER_SKIP_N 0x200u
 
 /* Limits of this implementation. */
 #define RAMBO_MAX_R 8        /* repetitions (tables) */
@@ -213,7 +223,9 @@ int rambo_query_seq_batch_into(rambo_t *h, const uint8_t *bases, const uint64_t 
  * depend on earlier calls, but calls that overlap on the GPU (several streams
  * or threads at once) race on it and must be serialised by the caller.
  * Returns RAMBO_ENOSPC with *needed set when ids_cap is too small, and the
- * errors of rambo_query_seq_batch otherwise. */
+ * errors of rambo_query_seq_batch otherwise.  RAMBO_KMER_SKIP_N is not
+ * accepted here (RAMBO_EINVAL): its per-base mask would need working memory
+ * beyond the fixed array. */
 int rambo_query_seq_batch_noalloc(rambo_t *h, const uint8_t *bases, const uint64_t *offsets,
                                   uint64_t n_queries, uint32_t k, uint32_t *ids, uint64_t ids_cap,
                                   uint64_t *id_offsets, uint64_t *needed, void *stream);
@@ -352,6 +364,19 @@ int rambo_export_partition(const rambo_t *h, uint16_t *host_phi, uint64_t n);
  * and *eta with round(ln 2 * m / n) clamped to [1, RAMBO_MAX_ETA]. */
 int rambo_suggest_params(uint64_t K, double n_mean, double V, double p, double delta, uint32_t *B,
                          uint32_t *R, uint64_t *m, uint32_t *eta);
+
+/* The same chooser sized from a sampled prefix of the stream, as Sec. 5.1
+ * does: the mean number of distinct keys per set is measured on the first
+ * n_sample sets (host memory, CSR: kind 0 = uint64 keys, kind 1 = ASCII DNA
+ * whose keys are its k-mers under the k-mer length and flags k) and taken as
+ * n_mean; the other arguments and outputs are those of rambo_suggest_params.
+ * *n_mean (if not NULL) receives the measured mean.  Errors: RAMBO_EINVAL
+ * (no sample, decreasing offsets, bad k, a sample without keys),
+ * RAMBO_EBADSEQ (a byte outside ACGTacgt without RAMBO_KMER_SKIP_N), and
+ * RAMBO_ERANGE as rambo_suggest_params.  No GPU involved. */
+int rambo_suggest_params_from_sample(uint64_t K, int kind, const void *data, const uint64_t *offsets,
+                                     uint64_t n_sample, uint32_t k, double V, double p, double delta,
+                                     uint32_t *B, uint32_t *R, uint64_t *m, uint32_t *eta, double *n_mean);
 
 /* Folding over (appendix, Sec. 5.2): ORs cell b + B/2 onto cell b of every
  * table, halving B (and the index) while R, m, eta and the hashes stay.  The

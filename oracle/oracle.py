@@ -182,6 +182,12 @@ class Oracle:
     def phi_table(self) -> np.ndarray:
         return np.array([[self.phi(r, i) for r in range(self.R)] for i in range(self.K)], np.int64)
 
+    @staticmethod
+    def kmers_count(seq, k: int = 31) -> int:
+        """Number of terms (windows) of a sequence, or a negative error code."""
+        s = np.frombuffer(bytes(seq), np.uint8) if not isinstance(seq, np.ndarray) else np.ascontiguousarray(seq, np.uint8)
+        return int(lib().orc_kmers(_ptr(s), s.size, k, None))
+
     # -- Algorithm 1 -----------------------------------------------------------
     def insert_keys(self, set_id: int, keys) -> None:
         k = np.ascontiguousarray(keys, dtype=np.uint64)

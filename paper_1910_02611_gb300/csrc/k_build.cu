@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(256) k_insert(IndexView ix, HashParams hp, Bat
             for (int r = 0; r < RMAX; ++r) cell[r] = ph[r];
         }
         if (b.seq && p + b.k > t_end) continue;  // window runs past the end of this set's sequence
+        if (b.skipn && !window_resolved(b.nmask, p, b.k)) continue;  // skip-N: holds an unresolved base
         uint64_t key;
         if (b.seq) {
             key = kmer_at(b.packed, p, b.k);

@@ -177,7 +177,8 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                 const int rlo = (screen && ph == 1) ? 1 : 0;
                 const int rhi = (screen && ph == 0) ? 1 : R;
                 const uint64_t idx = order ? (uint64_t)grp * nsteps + s : s * KPS + grp;
-                const bool act = idx < nkeys;
+                // skip-N: a window holding an unresolved base is not a term
+                const bool act = idx < nkeys && (!b.skipn || window_resolved(b.nmask, a + idx, b.k));
                 uint64_t key = 0;
                 if (act) {
                     if (b.seq) {
@@ -656,7 +657,8 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                     const int rlo = (screen && ph == 1) ? 1 : 0;
                     const int rhi = (screen && ph == 0) ? 1 : R;
                     const uint64_t idx = order ? (uint64_t)grp * nsteps + s : s * KPS + grp;
-                    const bool act = idx < nkeys;
+                    // skip-N: a window holding an unresolved base is not a term
+                    const bool act = idx < nkeys && (!b.skipn || window_resolved(b.nmask, a + idx, b.k));
                     uint64_t key = 0;
                     if (act) {
                         if (b.seq) {

@@ -21,25 +21,31 @@ __device__ __forceinline__ int q1_code(unsigned ch) {
 
 __global__ void __launch_bounds__(Q1_THREADS)
     k_query_one(IndexView ix, HashParams hp, int seq, const uint8_t* __restrict__ bases,
-                const uint64_t* __restrict__ keys, uint64_t len, uint32_t k, int canon, uint32_t* __restrict__ out_ids,
-                uint32_t* __restrict__ out_count, int* __restrict__ bad) {
-    extern __shared__ uint32_t sM[];  // [R][W] masks, then [32] warp counts
+                const uint64_t* __restrict__ keys, uint64_t len, uint32_t k, int canon, int skipn,
+                uint32_t* __restrict__ out_ids, uint32_t* __restrict__ out_count, int* __restrict__ bad) {
+    extern __shared__ uint32_t sM[];  // [R][W] masks, then [32] warp counts, then the valid-window count
     uint32_t* warp_cnt = sM + ix.R * ix.W;
+    uint32_t* n_valid = warp_cnt + 32;
     const int tid = threadIdx.x;
     for (uint32_t w = tid; w < ix.R * ix.W; w += blockDim.x) sM[w] = ~0u;
+    if (tid == 0) *n_valid = 0;
     __syncthreads();
     const uint64_t nkeys = seq ? (len >= k ? len - k + 1 : 0) : len;
     for (uint64_t t = tid; t < nkeys; t += blockDim.x) {
         uint64_t key = 0;
         if (seq) {
+            bool resolved = true;
             for (uint32_t c = 0; c < k; ++c) {
                 int v = q1_code(bases[t + c]);
                 if (v < 0) {
-                    *bad = 1;
+                    resolved = false;
+                    if (!skipn) *bad = 1;
                     v = 0;
                 }
                 key = key * 4 + (uint64_t)v;
             }
+            if (skipn && !resolved) continue;  // skip-N: not a term
+            if (skipn) atomicAdd(n_valid, 1u);
             if (canon) {
                 uint64_t rc = 0;  // reverse complement, from the bytes again
                 for (uint32_t c = 0; c < k; ++c) {
@@ -62,6 +68,13 @@ __global__ void __launch_bounds__(Q1_THREADS)
         }
     }
     __syncthreads();
+    if (seq && skipn && *n_valid == 0) {  // no term at all: a bad sequence
+        if (tid == 0) {
+            *bad = 1;
+            *out_count = 0;
+        }
+        return;
+    }
     // set stage: every registered ID whose cell is hit in every table, in order
     const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     uint32_t count = 0;
@@ -89,10 +102,11 @@ __global__ void __launch_bounds__(Q1_THREADS)
 }
 
 cudaError_t launch_query_one(const IndexView& ix, const HashParams& hp, int seq, const uint8_t* bases,
-                             const uint64_t* keys, uint64_t len, uint32_t k, int canon, uint32_t* out_ids,
+                             const uint64_t* keys, uint64_t len, uint32_t k, int canon, int skipn, uint32_t* out_ids,
                              uint32_t* out_count, int* bad, cudaStream_t s) {
-    const size_t smem = (size_t)(ix.R * ix.W + 32) * 4;
-    k_query_one<<<1, Q1_THREADS, smem, s>>>(ix, hp, seq, bases, keys, len, k, canon, out_ids, out_count, bad);
+    const size_t smem = (size_t)(ix.R * ix.W + 33) * 4;
+    k_query_one<<<1, Q1_THREADS, smem, s>>>(ix, hp, seq, bases, keys, len, k, canon, skipn, out_ids, out_count,
+                                            bad);
     return cudaGetLastError();
 }
 

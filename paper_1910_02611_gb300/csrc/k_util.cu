@@ -151,8 +151,23 @@ __device__ __forceinline__ uint32_t codes4(uint32_t w, int* bad) {
     return c;
 }
 
+// bits t (0..3) set for the bytes of a little-endian word outside ACGTacgt
+__device__ __forceinline__ uint32_t unresolved4(uint32_t w) {
+    const uint32_t u = w | 0x20202020u;
+    uint32_t m = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const uint32_t ch = (u >> (8 * t)) & 0xffu;
+        if (!((ch == 'a') | (ch == 'c') | (ch == 'g') | (ch == 't'))) m |= 1u << t;
+    }
+    return m;
+}
+
+// With nmask (skip-N), bit t of nmask[w] marks base 32w + t as unresolved
+// (packed as 0) and nothing is reported; bits past the end are 0.
 __global__ void k_pack(const uint8_t* __restrict__ bases, uint64_t total, uint64_t* __restrict__ packed,
-                       uint64_t n_words, DevStatus* st, const uint64_t* __restrict__ desc) {
+                       uint64_t n_words, DevStatus* st, const uint64_t* __restrict__ desc,
+                       uint32_t* __restrict__ nmask) {
     if (desc) {
         total = desc[1];
         n_words = total / 32 + 2;
@@ -163,6 +178,7 @@ __global__ void k_pack(const uint8_t* __restrict__ bases, uint64_t total, uint64
         uint64_t v = 0;
         uint64_t p0 = w * 32;
         unsigned long long bad = NO_ERR;
+        uint32_t um = 0;  // unresolved bases of this word
         if (aligned && p0 + 32 <= total) {
             // two 16-byte loads, four bases per 32-bit word
             const uint4* q = reinterpret_cast<const uint4*>(bases + p0);
@@ -172,10 +188,16 @@ __global__ void k_pack(const uint8_t* __restrict__ bases, uint64_t total, uint64
             for (int i = 0; i < 8; ++i) {
                 int b4;
                 const uint32_t c = codes4(wd[i], &b4);
-                if (b4 < 4 && bad == NO_ERR) bad = p0 + 4 * i + b4;
+                if (b4 < 4) {
+                    if (nmask) um |= unresolved4(wd[i]) << (4 * i);
+                    else if (bad == NO_ERR) bad = p0 + 4 * i + b4;
+                }
 #pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    v |= (uint64_t)((c >> (8 * t)) & 3u) << (62 - 2 * (4 * i + t));
+                for (int t = 0; t < 4; ++t) {
+                    // an unresolved byte packs as 0 (its code bits are masked out)
+                    const uint32_t code = ((um >> (4 * i + t)) & 1u) ? 0u : ((c >> (8 * t)) & 3u);
+                    v |= (uint64_t)code << (62 - 2 * (4 * i + t));
+                }
             }
         } else {
             for (int t = 0; t < 32; ++t) {
@@ -183,22 +205,59 @@ __global__ void k_pack(const uint8_t* __restrict__ bases, uint64_t total, uint64
                 if (p >= total) break;
                 int c = base_code(__ldg(bases + p));
                 if (c < 0) {
-                    if (bad == NO_ERR) bad = p;
+                    if (nmask) um |= 1u << t;
+                    else if (bad == NO_ERR) bad = p;
                     c = 0;
                 }
                 v |= (uint64_t)c << (62 - 2 * t);
             }
         }
         packed[w] = v;
+        if (nmask) nmask[w] = um;
         if (bad != NO_ERR) atomicMin(&st->bad_pos, bad);
     }
 }
 
 cudaError_t launch_pack(const uint8_t* bases, uint64_t total, uint64_t* packed, uint64_t n_words,
-                        DevStatus* st, cudaStream_t s, const uint64_t* desc) {
+                        DevStatus* st, cudaStream_t s, const uint64_t* desc, uint32_t* nmask) {
     if (n_words == 0) return cudaSuccess;
     // with a descriptor, n_words is the capacity the grid is sized for
-    k_pack<<<grid_for(n_words, 256, 1 << 16), 256, 0, s>>>(bases, total, packed, n_words, st, desc);
+    k_pack<<<grid_for(n_words, 256, 1 << 16), 256, 0, s>>>(bases, total, packed, n_words, st, desc, nmask);
+    return cudaGetLastError();
+}
+
+// Skip-N queries: query t needs k consecutive resolved bases somewhere in
+// [a, e), i.e. a gap of at least k between consecutive unresolved bases (the
+// range ends counting as unresolved).  Visits only the unresolved bits.
+__global__ void k_check_windows(BatchView b, DevStatus* st) {
+    bv_resolve(b);
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < b.n;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t a = b.offsets[t] - b.off0, e = b.offsets[t + 1] - b.off0;
+        if (e < a + b.k) continue;  // decreasing or too short: reported by the validation
+        uint64_t next = a;          // first base after the last unresolved one seen
+        bool found = false;
+        for (uint64_t w = a >> 5; w <= (e - 1) >> 5 && !found; ++w) {
+            uint32_t x = b.nmask[w];
+            if (w == (a >> 5)) x &= ~0u << (a & 31);
+            if (w == ((e - 1) >> 5) && ((e - 1) & 31) != 31) x &= (2u << ((e - 1) & 31)) - 1u;
+            while (x) {
+                const uint64_t pos = w * 32 + (uint64_t)(__ffs(x) - 1);
+                if (pos - next >= b.k) {
+                    found = true;
+                    break;
+                }
+                next = pos + 1;
+                x &= x - 1;
+            }
+        }
+        if (!found && e - next < b.k) record_error(st, t, PRIO_EBADSEQ);
+    }
+}
+
+cudaError_t launch_check_windows(const BatchView& b, DevStatus* st, cudaStream_t s) {
+    if (b.n == 0 && !b.desc) return cudaSuccess;
+    k_check_windows<<<grid_for(b.n, 256, 8192), 256, 0, s>>>(b, st);
     return cudaGetLastError();
 }
 
@@ -487,6 +546,7 @@ cudaError_t load_util_kernels() {
                          reinterpret_cast<const void*>(&k_scan_one_block), reinterpret_cast<const void*>(&k_scan_tiles),
                          reinterpret_cast<const void*>(&k_scan_sums), reinterpret_cast<const void*>(&k_scan_add),
                          reinterpret_cast<const void*>(&k_gather)};
+    // (k_check_windows serves skip-N queries, which the no-alloc call does not take)
     for (const void* f : fns) {
         cudaFuncAttributes a;
         const cudaError_t e = cudaFuncGetAttributes(&a, f);

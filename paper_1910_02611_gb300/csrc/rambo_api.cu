@@ -2,6 +2,7 @@
 // life cycle, parameter derivation, input staging, kernel sequencing, status
 // decoding and result hand-out.  Every step of insertion and query runs in the
 // kernels of this library; the host only moves buffers and orders launches.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -36,7 +37,8 @@ int map_cuda(cudaError_t e) {
         if (r_ != RAMBO_OK) return r_; \
     } while (0)
 
-// growable device buffer
+// growable device buffer (grown with 1/8 headroom, so batches of slightly
+// varying size do not reallocate every call)
 template <class T>
 struct DBuf {
     T* p = nullptr;
@@ -46,7 +48,7 @@ struct DBuf {
         if (p) cudaFree(p);
         p = nullptr;
         cap = 0;
-        size_t want = n < 64 ? 64 : n;
+        size_t want = n < 64 ? 64 : n + n / 8;
         if (cudaMalloc(&p, want * sizeof(T)) != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
@@ -62,7 +64,7 @@ struct DBuf {
     }
 };
 
-// growable pinned host buffer
+// growable pinned host buffer (1/8 headroom, as DBuf: pinning is slow)
 template <class T>
 struct HBuf {
     T* p = nullptr;
@@ -72,7 +74,7 @@ struct HBuf {
         if (p) cudaFreeHost(p);
         p = nullptr;
         cap = 0;
-        size_t want = n < 64 ? 64 : n;
+        size_t want = n < 64 ? 64 : n + n / 8;
         if (cudaMallocHost(&p, want * sizeof(T)) != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
@@ -125,7 +127,7 @@ struct rambo {
     // scratch
     DBuf<uint8_t> in_data;
     DBuf<uint64_t> in_off, in_ids, packed, qstart, scan_tmp, id_off;
-    DBuf<uint32_t> stage, qcount, ids, fill, perm, chist;
+    DBuf<uint32_t> stage, qcount, ids, fill, perm, chist, nmask;
     DBuf<uint64_t> ckeys, coff;
     HBuf<uint32_t> h_ids;
     HBuf<uint64_t> h_id_off;
@@ -197,6 +199,7 @@ void free_handle(rambo* h) {
     h->fill.release();
     h->perm.release();
     h->chist.release();
+    h->nmask.release();
     h->ckeys.release();
     h->coff.release();
     h->h_ids.release();
@@ -344,9 +347,15 @@ int stage_batch(rambo* h, const void* data, size_t elem, const uint64_t* offsets
 int pack_bases(rambo* h, BatchView& b, const void* d_bases, cudaStream_t s) {
     const uint64_t n_words = b.total / 32 + 2;  // one spare word for windows crossing the last word
     RK(h->packed.ensure(n_words));
-    CK(launch_pack(static_cast<const uint8_t*>(d_bases), b.total, h->packed.p, n_words, h->st, s));
+    uint32_t* nmask = nullptr;
+    if (b.skipn) {
+        RK(h->nmask.ensure(n_words));
+        nmask = h->nmask.p;
+    }
+    CK(launch_pack(static_cast<const uint8_t*>(d_bases), b.total, h->packed.p, n_words, h->st, s, nullptr, nmask));
     CK(launch_resolve_bad_base(b, h->st, s));
     b.packed = h->packed.p;
+    b.nmask = nmask;
     return RAMBO_OK;
 }
 
@@ -354,14 +363,15 @@ int run_insert(rambo* h, int seq, const uint64_t* set_ids, const void* data, con
                uint64_t n, uint32_t k, int on_device, cudaStream_t s) {
     if (!h || !offsets || !set_ids || (!data && n)) return RAMBO_EINVAL;
     uint32_t kk = 0;
-    int canon = 0;
-    if (seq && !split_k(k, &kk, &canon)) return RAMBO_EINVAL;
+    int canon = 0, skipn = 0;
+    if (seq && !split_k(k, &kk, &canon, &skipn)) return RAMBO_EINVAL;
     if (n == 0) return RAMBO_OK;
     CK(cudaSetDevice(h->device));
     BatchView b{};
     b.seq = seq;
     b.k = kk;
     b.canon = canon;
+    b.skipn = skipn;
     const void* d_data = nullptr;
     RK(stage_batch(h, data, seq ? 1 : 8, offsets, set_ids, n, on_device, s, b, &d_data));
     CK(launch_status_reset(h->st, s));
@@ -484,8 +494,8 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
               int on_device, cudaStream_t s, QueryDest& d) {
     if (!h || !offsets || (!data && n)) return RAMBO_EINVAL;
     uint32_t kk = 0;
-    int canon = 0;
-    if (seq && !split_k(k, &kk, &canon)) return RAMBO_EINVAL;
+    int canon = 0, skipn = 0;
+    if (seq && !split_k(k, &kk, &canon, &skipn)) return RAMBO_EINVAL;
     k = kk;
     CK(cudaSetDevice(h->device));
     h->last = rambo_query_stats_t{};
@@ -517,6 +527,7 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
     b.seq = seq;
     b.k = k;
     b.canon = canon;
+    b.skipn = skipn;
     const void* d_data = nullptr;
     RK(stage_batch(h, data, seq ? 1 : 8, offsets, nullptr, n, on_device, s, b, &d_data));
     int use_bitmap = 0;
@@ -542,6 +553,10 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
         if (seq) {
             RK(pack_bases(h, b, d_data, s));
             h->launches += 2;
+            if (b.skipn) {
+                CK(launch_check_windows(b, h->st, s));
+                h->launches += 1;
+            }
         } else {
             b.keys = static_cast<const uint64_t*>(d_data);
         }
@@ -871,6 +886,70 @@ int rambo_suggest_params(uint64_t K, double n_mean, double V, double p, double d
     return Rv ? RAMBO_OK : RAMBO_ERANGE;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Host k-mer keys of one sequence under the library's encoding (first base
+// most significant; canonical = min with the reverse complement; skip-N =
+// windows holding a byte outside ACGTacgt left out).  Returns RAMBO_EBADSEQ
+// for such a byte without skip-N.
+int host_kmers(const uint8_t* s, uint64_t n, uint32_t k, int canon, int skipn, std::vector<uint64_t>& out) {
+    const uint64_t mask = k == 32 ? ~0ull : ((1ull << (2 * k)) - 1);
+    uint64_t fwd = 0, rc = 0, run = 0;
+    for (uint64_t p = 0; p < n; ++p) {
+        const unsigned u = s[p] | 0x20u;
+        int c = u == 'a' ? 0 : u == 'c' ? 1 : u == 'g' ? 2 : u == 't' ? 3 : -1;
+        if (c < 0) {
+            if (!skipn) return RAMBO_EBADSEQ;
+            run = 0;
+            c = 0;
+        } else {
+            ++run;
+        }
+        fwd = ((fwd << 2) | (uint64_t)c) & mask;
+        rc = (rc >> 2) | ((uint64_t)(3 - c) << (2 * (k - 1)));
+        if (p + 1 >= k && run >= k) out.push_back(canon && rc < fwd ? rc : fwd);
+    }
+    return RAMBO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rambo_suggest_params_from_sample(uint64_t K, int kind, const void* data, const uint64_t* offsets,
+                                     uint64_t n_sample, uint32_t k, double V, double p, double delta, uint32_t* B,
+                                     uint32_t* R, uint64_t* m, uint32_t* eta, double* n_mean) {
+    if (!offsets || !n_sample || (kind != 0 && kind != 1) || (!data && offsets[n_sample] > offsets[0]))
+        return RAMBO_EINVAL;
+    uint32_t kk = 0;
+    int canon = 0, skipn = 0;
+    if (kind == 1 && !split_k(k, &kk, &canon, &skipn)) return RAMBO_EINVAL;
+    // Sec. 5.1: the mean set cardinality, measured on the first sets of the
+    // stream, sizes every BFU
+    uint64_t distinct = 0;
+    std::vector<uint64_t> keys;
+    for (uint64_t t = 0; t < n_sample; ++t) {
+        if (offsets[t + 1] < offsets[t]) return RAMBO_EINVAL;
+        keys.clear();
+        if (kind == 0) {
+            const uint64_t* kp = static_cast<const uint64_t*>(data);
+            keys.assign(kp + offsets[t], kp + offsets[t + 1]);
+        } else {
+            const int rc = host_kmers(static_cast<const uint8_t*>(data) + offsets[t], offsets[t + 1] - offsets[t], kk,
+                                      canon, skipn, keys);
+            if (rc) return rc;
+        }
+        std::sort(keys.begin(), keys.end());
+        distinct += (uint64_t)(std::unique(keys.begin(), keys.end()) - keys.begin());
+    }
+    if (distinct == 0) return RAMBO_EINVAL;  // nothing to size the filters from
+    const double mean = (double)distinct / (double)n_sample;
+    if (n_mean) *n_mean = mean;
+    return rambo_suggest_params(K, mean, V, p, delta, B, R, m, eta);
+}
+
 int rambo_insert_seq_batch(rambo_t* h, const uint64_t* set_ids, const uint8_t* bases, const uint64_t* offsets,
                            uint64_t n_sets, uint32_t k, int on_device, void* stream) {
     return run_insert(h, 1, set_ids, bases, offsets, n_sets, k, on_device, (cudaStream_t)stream);
@@ -1007,8 +1086,8 @@ int rambo_query_one_per_launch(rambo_t* h, int kind, const void* data, const uin
                                uint64_t n_queries, uint32_t k, uint32_t* ids, uint32_t* counts, void* stream) {
     if (!h || !host_offsets || (!data && n_queries) || (n_queries && (!ids || !counts))) return RAMBO_EINVAL;
     uint32_t kk = 0;
-    int canon = 0;
-    if (kind == 1 && !split_k(k, &kk, &canon)) return RAMBO_EINVAL;
+    int canon = 0, skipn = 0;
+    if (kind == 1 && !split_k(k, &kk, &canon, &skipn)) return RAMBO_EINVAL;
     k = kk;
     if (kind != 0 && kind != 1) return RAMBO_EINVAL;
     CK(cudaSetDevice(h->device));
@@ -1026,7 +1105,7 @@ int rambo_query_one_per_launch(rambo_t* h, int kind, const void* data, const uin
         const uint64_t a = host_offsets[q], len = host_offsets[q + 1] - a;
         const uint8_t* bp = kind == 1 ? static_cast<const uint8_t*>(data) + a : nullptr;
         const uint64_t* kp = kind == 0 ? static_cast<const uint64_t*>(data) + a : nullptr;
-        CK(launch_query_one(ix, h->hp, kind, bp, kp, len, k, canon, ids + q * h->K, counts + q, d_bad, s));
+        CK(launch_query_one(ix, h->hp, kind, bp, kp, len, k, canon, skipn, ids + q * h->K, counts + q, d_bad, s));
     }
     int bad = 0;
     CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -147,11 +147,22 @@ __device__ __forceinline__ uint64_t canonical_kmer(uint64_t fwd, uint32_t k) {
     return rc < fwd ? rc : fwd;
 }
 
-// k and the canonical flag from a k-mer length argument; false when invalid
-__host__ __device__ inline bool split_k(uint32_t kflags, uint32_t* k, int* canon) {
+// 1 when none of the k bases starting at base p is unresolved (skip-N
+// windows): nmask holds one bit per base, bit t of word w for base 32w + t.
+// Reads word p/32 and the next one (k <= 32, so o + k <= 63).
+__device__ __forceinline__ bool window_resolved(const uint32_t* __restrict__ nmask, uint64_t p, uint32_t k) {
+    const uint64_t wi = p >> 5;
+    const uint32_t o = (uint32_t)(p & 31);
+    const uint64_t two = (uint64_t)__ldg(nmask + wi) | ((uint64_t)__ldg(nmask + wi + 1) << 32);
+    return ((two >> o) & ((1ull << k) - 1)) == 0;
+}
+
+// k and the canonical / skip-N flags from a k-mer length argument; false when invalid
+__host__ __device__ inline bool split_k(uint32_t kflags, uint32_t* k, int* canon, int* skipn = nullptr) {
     *k = kflags & 0xffu;
     *canon = (kflags & RAMBO_KMER_CANONICAL) ? 1 : 0;
-    return *k >= 1 && *k <= 32 && !(kflags & ~(0xffu | RAMBO_KMER_CANONICAL));
+    if (skipn) *skipn = (kflags & RAMBO_KMER_SKIP_N) ? 1 : 0;
+    return *k >= 1 && *k <= 32 && !(kflags & ~(0xffu | RAMBO_KMER_CANONICAL | RAMBO_KMER_SKIP_N));
 }
 
 __device__ __forceinline__ void record_error(DevStatus* st, uint64_t index, unsigned prio) {
@@ -187,6 +198,8 @@ struct BatchView {
     uint64_t n;                    // items
     uint32_t k;
     int canon;                     // keys are canonical k-mers (min of both strands)
+    int skipn;                     // windows holding an unresolved base are skipped
+    const uint32_t* nmask;         // skip-N: one bit per packed base, set = unresolved
     const uint64_t* set_ids;       // insert batches only
     const uint32_t* perm;          // queries only: processing order (NULL = 0..n-1)
     const uint64_t* desc;          // device descriptor {n, total} (offsets[0] = 0) read at
@@ -234,8 +247,12 @@ cudaError_t launch_phi_init(uint16_t* phi, uint64_t K, uint32_t R, uint32_t B, c
 cudaError_t launch_or_words(uint32_t* dst, const uint32_t* src, uint64_t n, cudaStream_t s);
 cudaError_t launch_validate_batch(const BatchView& b, uint64_t min_len, uint64_t K, DevStatus* st,
                                   cudaStream_t s);
+// nmask (skip-N): one bit per base, total/32 + 2 words; unresolved bases are
+// marked there instead of being reported as errors
 cudaError_t launch_pack(const uint8_t* bases, uint64_t total, uint64_t* packed, uint64_t n_words,
-                        DevStatus* st, cudaStream_t s, const uint64_t* desc = nullptr);
+                        DevStatus* st, cudaStream_t s, const uint64_t* desc = nullptr, uint32_t* nmask = nullptr);
+// skip-N queries: a query with no window free of unresolved bases is EBADSEQ
+cudaError_t launch_check_windows(const BatchView& b, DevStatus* st, cudaStream_t s);
 cudaError_t launch_resolve_bad_base(const BatchView& b, DevStatus* st, cudaStream_t s);
 cudaError_t launch_register(const BatchView& b, uint32_t* reg, DevStatus* st, cudaStream_t s);
 cudaError_t launch_scan_counts(const uint32_t* counts, uint64_t n, uint64_t* offsets,
@@ -272,7 +289,7 @@ cudaError_t launch_query(const IndexView& ix, const HashParams& hp, const BatchV
 
 // k_query_one.cu: the plain one-query-per-launch kernel
 cudaError_t launch_query_one(const IndexView& ix, const HashParams& hp, int seq, const uint8_t* bases,
-                             const uint64_t* keys, uint64_t len, uint32_t k, int canon, uint32_t* out_ids,
+                             const uint64_t* keys, uint64_t len, uint32_t k, int canon, int skipn, uint32_t* out_ids,
                              uint32_t* out_count, int* bad, cudaStream_t s);
 
 // rambo_api.cu: what the fixed-scratch entry point needs from a handle

@@ -104,8 +104,9 @@ extern "C" int rambo_query_seq_batch_noalloc(rambo_t* h, const uint8_t* bases, c
                                              uint64_t* id_offsets, uint64_t* needed, void* stream) {
     if (!h || !offsets || !id_offsets || (!bases && n_queries) || (!ids && ids_cap)) return RAMBO_EINVAL;
     uint32_t kk = 0;
-    int canon = 0;
-    if (!split_k(k, &kk, &canon)) return RAMBO_EINVAL;
+    int canon = 0, skipn = 0;
+    // skip-N windows need a per-base mask beyond the fixed array: not taken here
+    if (!split_k(k, &kk, &canon, &skipn) || skipn) return RAMBO_EINVAL;
     k = kk;
     if (n_queries > NA_MAX_QUERIES) return RAMBO_E2BIG;
     const uint64_t n = n_queries;

@@ -43,7 +43,7 @@ struct rambo_plan {
     rambo_t* h = nullptr;
     int kind = 1;
     uint32_t k = 31;
-    int canon = 0;
+    int canon = 0, skipn = 0;
     uint64_t max_q = 0, max_items = 0, max_ids = 0;
     int device = 0;
     size_t elem = 1;
@@ -51,6 +51,7 @@ struct rambo_plan {
     uint8_t* d_data = nullptr;
     uint64_t* d_off = nullptr;
     uint64_t* d_packed = nullptr;
+    uint32_t* d_nmask = nullptr;  // skip-N: unresolved-base bits
     uint32_t* qcount = nullptr;
     uint64_t* qstart = nullptr;
     uint64_t* scan_tmp = nullptr;
@@ -94,7 +95,7 @@ void plan_free(rambo_plan* p) {
     for (cudaEvent_t e : p->ev_t)
         if (e) cudaEventDestroy(e);
     if (p->cap) cudaStreamDestroy(p->cap);
-    void* dev[] = {p->d_data, p->d_off, p->d_packed, p->qcount, p->qstart, p->scan_tmp,
+    void* dev[] = {p->d_data, p->d_off, p->d_packed, p->d_nmask, p->qcount, p->qstart, p->scan_tmp,
                    p->stage, p->ids, p->id_off, p->st, p->d_desc};
     for (void* d : dev)
         if (d) cudaFree(d);
@@ -126,6 +127,8 @@ int plan_capture(rambo_plan* p, bool timed) {
     b.off0 = 0;
     b.k = p->k;
     b.canon = p->canon;
+    b.skipn = p->skipn;
+    b.nmask = p->d_nmask;
     b.desc = p->d_desc;
     const uint64_t scan_words = scan_tmp_words(p->max_q);
     cudaStream_t s = p->cap;
@@ -136,9 +139,11 @@ int plan_capture(rambo_plan* p, bool timed) {
     if (e == cudaSuccess) e = launch_status_reset(p->st, s), ++n_launch;
     if (e == cudaSuccess) e = launch_validate_batch(b, p->kind ? p->k : 1, ix.K, p->st, s), ++n_launch;
     if (e == cudaSuccess && p->kind == 1) {
-        e = launch_pack(p->d_data, p->max_items, p->d_packed, p->max_items / 32 + 2, p->st, s, p->d_desc);
+        e = launch_pack(p->d_data, p->max_items, p->d_packed, p->max_items / 32 + 2, p->st, s, p->d_desc,
+                        p->d_nmask);
         if (e == cudaSuccess) e = launch_resolve_bad_base(b, p->st, s);
         n_launch += 2;
+        if (e == cudaSuccess && p->skipn) e = launch_check_windows(b, p->st, s), ++n_launch;
     }
     QueryOut o{p->stage, p->max_ids, p->qstart, p->qcount};
     if (e == cudaSuccess) e = mark(p, 1, s, timed);
@@ -206,8 +211,8 @@ int rambo_plan_create(rambo_t* h, int kind, uint64_t max_queries, uint64_t max_i
                       rambo_plan_t** out) {
     if (!h || !out || (kind != 0 && kind != 1) || !max_queries || !max_items || !max_ids) return RAMBO_EINVAL;
     uint32_t kk = 0;
-    int canon = 0;
-    if (kind == 1 && !split_k(k, &kk, &canon)) return RAMBO_EINVAL;
+    int canon = 0, skipn = 0;
+    if (kind == 1 && !split_k(k, &kk, &canon, &skipn)) return RAMBO_EINVAL;
     if (max_queries > 0xffffffffull) return RAMBO_EINVAL;
     *out = nullptr;
     rambo_plan* p = new (std::nothrow) rambo_plan();
@@ -225,6 +230,7 @@ int rambo_plan_create(rambo_t* h, int kind, uint64_t max_queries, uint64_t max_i
     p->kind = kind;
     p->k = kind == 1 ? kk : 0;
     p->canon = kind == 1 ? canon : 0;
+    p->skipn = kind == 1 ? skipn : 0;
     p->max_q = max_queries;
     p->max_items = max_items;
     p->max_ids = max_ids;
@@ -237,6 +243,7 @@ int rambo_plan_create(rambo_t* h, int kind, uint64_t max_queries, uint64_t max_i
     bool ok = cudaMalloc(&p->d_data, max_items * p->elem + 16) == cudaSuccess &&
               cudaMalloc(&p->d_off, (max_queries + 1) * 8) == cudaSuccess &&
               (kind == 0 || cudaMalloc(&p->d_packed, (max_items / 32 + 2) * 8) == cudaSuccess) &&
+              (!p->skipn || cudaMalloc(&p->d_nmask, (max_items / 32 + 2) * 4) == cudaSuccess) &&
               cudaMalloc(&p->qcount, max_queries * 4) == cudaSuccess &&
               cudaMalloc(&p->qstart, max_queries * 8) == cudaSuccess &&
               cudaMalloc(&p->scan_tmp, scan_tmp_words(max_queries) * 8) == cudaSuccess &&

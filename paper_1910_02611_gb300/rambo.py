@@ -64,6 +64,9 @@ SIGNATURES = {
     "rambo_insert": (_i32, [_p, _u64, _p, _u64, _i32, _p]),
     "rambo_suggest_params": (_i32, [_u64, C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(_u32),
                                     C.POINTER(_u32), C.POINTER(_u64), C.POINTER(_u32)]),
+    "rambo_suggest_params_from_sample": (_i32, [_u64, _i32, _p, _p, _u64, _u32, C.c_double, C.c_double, C.c_double,
+                                                C.POINTER(_u32), C.POINTER(_u32), C.POINTER(_u64), C.POINTER(_u32),
+                                                C.POINTER(C.c_double)]),
     "rambo_insert_seq_batch": (_i32, [_p, _p, _p, _p, _u64, _u32, _i32, _p]),
     "rambo_query_batch": (_i32, [_p, _p, _p, _u64, _i32, C.POINTER(_p), C.POINTER(_p), _p]),
     "rambo_query_seq_batch": (_i32, [_p, _p, _p, _u64, _u32, _i32, C.POINTER(_p), C.POINTER(_p), _p]),
@@ -693,6 +696,26 @@ def suggest_params(K: int, n_mean: float, V: float = 1.0, p: float = 0.01, delta
     out = dict(B=B.value, R=R.value, m=m.value, eta=eta.value)
     if rc:
         err = RamboError(rc, "suggest_params")
+        err.params = out
+        raise err
+    return out
+
+
+def suggest_params_from_sample(K: int, data, offsets, kind: str = "keys", k: int = 31, V: float = 1.0,
+                               p: float = 0.01, delta: float = 0.01) -> dict:
+    """Parameter chooser sized from a sampled prefix (Sec. 5.1): the mean
+    distinct-key count of the sample's sets (CSR, host arrays) is the n_mean
+    of suggest_params.  Returns the parameters and the measured n_mean."""
+    d = _host_arr(data, np.uint64 if kind == "keys" else np.uint8)
+    off = _host_arr(offsets, np.uint64)
+    _check_csr(d, off, "suggest_params_from_sample")
+    B, R, m, eta, nm = _u32(), _u32(), _u64(), _u32(), C.c_double(0.0)
+    rc = load_library().rambo_suggest_params_from_sample(K, 0 if kind == "keys" else 1, d.ctypes.data,
+                                                         off.ctypes.data, off.size - 1, k, V, p, delta, C.byref(B),
+                                                         C.byref(R), C.byref(m), C.byref(eta), C.byref(nm))
+    out = dict(B=B.value, R=R.value, m=m.value, eta=eta.value, n_mean=nm.value)
+    if rc:
+        err = RamboError(rc, "suggest_params_from_sample")
         err.params = out
         raise err
     return out

@@ -479,6 +479,80 @@ def test_canonical_kmers_index_and_queries(mods, k):
     assert np.array_equal(ids1, a_ids) and np.array_equal(off1, a_off)
 
 
+def _sprinkle_unresolved(rng, data: np.ndarray, rate: float, runs: int) -> np.ndarray:
+    """A copy of ASCII DNA with single unresolved bytes at the given rate
+    plus a few runs of N (as assembly gaps and low-quality stretches give)."""
+    out = data.copy()
+    junk = np.frombuffer(b"NnRY-.", np.uint8)
+    hit = np.flatnonzero(rng.random(out.size) < rate)
+    out[hit] = junk[rng.integers(0, junk.size, hit.size)]
+    for _ in range(runs):
+        a = int(rng.integers(0, max(1, out.size - 200)))
+        out[a: a + int(rng.integers(1, 200))] = ord("N")
+    return out
+
+
+@pytest.mark.parametrize("k", [31, 31 | 0x100, 12])
+def test_skip_n_windows_index_and_queries(mods, k):
+    # skip-N (Sec. 3.2.1 over reads with unresolved bases): windows holding a
+    # byte outside ACGTacgt are left out on both sides
+    from paper_1910_02611_gb300 import EBADSEQ, Plan, RamboError
+
+    Rambo, Oracle = mods
+    SKIPN = 0x200
+    rng = np.random.default_rng(k)
+    w = synth.make("genome", 0.01, m=1 << 16)
+    sets = synth.Collection("seq", _sprinkle_unresolved(rng, w.sets.data, 0.002, 40), w.sets.offsets, w.sets.ids)
+    g = Rambo(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    g.insert(sets.ids, sets.data, sets.offsets, kind="seq", k=k | SKIPN)
+    o = Oracle(w.K, w.B, w.R, w.m, w.eta, w.seed)
+    o.insert_seq_batch(sets.ids, sets.data, sets.offsets, k | SKIPN, nthreads=4)
+    assert_index_equal(g, o)
+    gt = Rambo(w.K, w.B, w.R, w.m, w.eta, w.seed)  # window-by-window build
+    gt.set_build_tiling(1 << 17, mode=1)
+    gt.insert(sets.ids, sets.data, sets.offsets, kind="seq", k=k | SKIPN)
+    assert np.array_equal(gt.export_index(), g.export_index())
+    gt.close()
+    # queries with unresolved bytes, some at the window edges; keep those with a valid window
+    q = w.queries.subset(np.arange(600))
+    qd = _sprinkle_unresolved(rng, q.data, 0.004, 3)
+    for t in range(0, 600, 7):
+        qd[int(q.offsets[t])] = ord("N")
+        qd[int(q.offsets[t + 1]) - 1] = ord("n")
+    keep = [t for t in range(600) if o.kmers_count(qd[int(q.offsets[t]):int(q.offsets[t + 1])], k | SKIPN) > 0]
+    qq = synth.Collection("seq", qd, q.offsets).subset(np.array(keep))
+    for cfg in ({}, {"set_stage": 1}, {"set_stage": 2}, {"set_stage": 3}, {"visit_order": 0}):
+        if cfg:
+            g.set_config(**cfg)
+        assert_query_equal(g, o, qq, k=k | SKIPN)
+    rids, roff = o.query_batch("seq", qq.data, qq.offsets, k=k | SKIPN)
+    # through a captured plan
+    plan = Plan(g, "seq", max_queries=len(qq), max_items=int(qq.offsets[-1]), max_ids=1 << 20, k=k | SKIPN)
+    plan.launch_host(qq.data, qq.offsets)
+    pids, poff = plan.wait()
+    assert np.array_equal(poff, roff) and np.array_equal(pids, rids)
+    plan.close()
+    # the one-query-per-launch kernel
+    import torch
+
+    sub = qq.subset(np.arange(50))
+    bids, boff = g.query_one_per_launch(torch.from_numpy(sub.data).cuda(), sub.offsets, kind="seq", k=k | SKIPN)
+    s_ids, s_off = o.query_batch("seq", sub.data, sub.offsets, k=k | SKIPN)
+    assert np.array_equal(boff, s_off) and np.array_equal(bids, s_ids)
+    # a query with no valid window is a bad sequence, reported at its index
+    bad = qq.subset(np.arange(10))
+    bd = bad.data.copy()
+    bd[int(bad.offsets[6]): int(bad.offsets[7])] = ord("N")
+    with pytest.raises(RamboError) as e:
+        g.query(bd, bad.offsets, kind="seq", k=k | SKIPN)
+    assert e.value.code == EBADSEQ and e.value.item == 6
+    # without the flag the same bytes reject the sequence
+    with pytest.raises(RamboError) as e:
+        g.query(qq.data, qq.offsets, kind="seq", k=k)
+    assert e.value.code == EBADSEQ
+    g.close()
+
+
 def test_two_level_hash_node_indexes_merge_into_the_stacked_index(mods, tmp_path):
     # Sec. 5.2 / appendix: node-local builds (each inserting only the sets tau
     # routes to it) OR into the stacked index; it equals the oracle's stacked

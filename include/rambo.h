@@ -87,10 +87,15 @@ enum {
  * RAMBO_KMER_CANONICAL. */
 #define RAMBO_KMER_SKIP_N 0x200u
 
-/* Limits of this implementation. */
-#define RAMBO_MAX_R 8        /* repetitions (tables) */
+/* Limits of this implementation.  Indexes with R <= 8 and rows of at most
+ * 4096 cells are queried by the register-tiled kernel (one warp, or a few,
+ * per query); wider rows (the paper's stacked B = 50000 index, Sec. 5.2, or
+ * ClueWeb09's B = 2e4, Sec. 5.3) and more tables by a kernel that gives each
+ * query a thread block, its masks in shared memory, and reads every row
+ * coalesced across the block. */
+#define RAMBO_MAX_R 16       /* repetitions (tables) */
 #define RAMBO_MAX_ETA 4      /* hashes per Bloom filter */
-#define RAMBO_MAX_B 4096     /* cells per table */
+#define RAMBO_MAX_B 65535    /* cells per table */
 #define RAMBO_MAX_L 32       /* m = 2^L bits per Bloom filter */
 
 typedef struct rambo_info {

@@ -48,11 +48,12 @@ __global__ void __launch_bounds__(256) k_insert(IndexView ix, HashParams hp, Bat
     if (lane == 0) t = find_item(b.offsets, b.n, w_begin + b.off0);
     t = __shfl_sync(FULL, t, 0);
     uint64_t t_end = __ldg(b.offsets + t + 1) - b.off0;
+    const int R = (int)ix.R;
     uint32_t cell[RMAX];
     {
-        const uint16_t* ph = ix.phi + __ldg(b.set_ids + t) * PHI_STRIDE;
+        const uint16_t* ph = ix.phi + __ldg(b.set_ids + t) * ix.ps;
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r) cell[r] = ph[r];
+        for (int r = 0; r < RMAX; ++r) cell[r] = r < R ? ph[r] : 0u;
     }
     for (uint64_t p = w_begin + lane; p < w_end; p += 32) {
         if (p >= t_end) {
@@ -61,9 +62,9 @@ __global__ void __launch_bounds__(256) k_insert(IndexView ix, HashParams hp, Bat
                 ++t;
                 t_end = __ldg(b.offsets + t + 1) - b.off0;
             } while (p >= t_end);
-            const uint16_t* ph = ix.phi + __ldg(b.set_ids + t) * PHI_STRIDE;
+            const uint16_t* ph = ix.phi + __ldg(b.set_ids + t) * ix.ps;
 #pragma unroll
-            for (int r = 0; r < RMAX; ++r) cell[r] = ph[r];
+            for (int r = 0; r < RMAX; ++r) cell[r] = r < R ? ph[r] : 0u;
         }
         if (b.seq && p + b.k > t_end) continue;  // window runs past the end of this set's sequence
         if (b.skipn && !window_resolved(b.nmask, p, b.k)) continue;  // skip-N: holds an unresolved base

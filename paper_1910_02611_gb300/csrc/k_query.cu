@@ -65,6 +65,11 @@ cudaError_t launch_query(const IndexView& ix, const HashParams& hp, const BatchV
                          const QueryTuning& t, int use_bitmap, DevStatus* st, cudaStream_t s, int* n_launched) {
     if (n_launched) *n_launched = 0;
     if (b.n == 0 && !b.desc) return cudaSuccess;
+    if (t.wide) {
+        const cudaError_t e = launch_query_wide(ix, hp, b, o, t.blocks, st, s);
+        if (e == cudaSuccess && n_launched) *n_launched = 1;
+        return e;
+    }
     const uint32_t spw = query_smem_words_per_warp(ix.R, ix.S, ix.K, use_bitmap);
     const size_t smem = (size_t)spw * 4 * t.warps_per_block;
     // Which instance serves the batch: known here for host-sized batches;

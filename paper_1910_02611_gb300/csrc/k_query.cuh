@@ -83,7 +83,7 @@ __device__ __forceinline__ bool qk_set_passes(const IndexView& ix, const uint32_
                         ph.z & 0xffffu, ph.z >> 16, ph.w & 0xffffu, ph.w >> 16};
     bool ok = true;
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
+    for (int r = 0; r < RF; ++r) {
         if (r < (int)ix.R && r != skip_r) {
             uint32_t b = cell[r];
             ok &= (sM[r * ix.S + (b >> 5)] >> (b & 31)) & 1u;
@@ -156,9 +156,9 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
             const uint64_t e = __ldg(b.offsets + q + 1) - b.off0;
             const uint64_t nkeys = b.seq ? (e - a - b.k + 1) : (e - a);  // >= 1 (validated)
 
-            uint32_t M[RMAX][V];
+            uint32_t M[RF][V];
 #pragma unroll
-            for (int r = 0; r < RMAX; ++r)
+            for (int r = 0; r < RF; ++r)
 #pragma unroll
                 for (int v = 0; v < V; ++v) M[r][v] = has_words ? ~0u : 0u;
 
@@ -190,10 +190,10 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                 }
                 const uint64_t y = mix64(key);
                 // A3: issue every row read of this step, then combine
-                uint32_t val[RMAX][ETA][V];
+                uint32_t val[RF][ETA][V];
                 const bool ld = act && has_words;
 #pragma unroll
-                for (int r = 0; r < RMAX; ++r) {
+                for (int r = 0; r < RF; ++r) {
                     if (r >= rlo && r < rhi && ld) {
                         const uint32_t* rb = rows + (uint64_t)r * ix.m * ix.S + w0;
 #pragma unroll
@@ -207,7 +207,7 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                 }
                 uint32_t nz = 0;
 #pragma unroll
-                for (int r = 0; r < RMAX; ++r) {
+                for (int r = 0; r < RF; ++r) {
                     if (r < R) {
                         uint32_t any = 0;
                         const bool probed_r = r >= rlo && r < rhi;
@@ -246,7 +246,7 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                 // stage the masks: row words [w0, w0+V) of table r
                 if (grp == 0 && has_words) {
 #pragma unroll
-                    for (int r = 0; r < RMAX; ++r)
+                    for (int r = 0; r < RF; ++r)
                         if (r < R)
 #pragma unroll
                             for (int v = 0; v < V; ++v) sM[r * ix.S + w0 + v] = M[r][v];
@@ -254,11 +254,11 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                 __syncwarp();
                 // per-table hit-cell counts; the table with the fewest hit cells
                 // gives the sparse stage its candidates
-                uint32_t pc[RMAX];
+                uint32_t pc[RF];
                 int rstar = 0;
                 uint32_t pmin = 0xffffffffu;
 #pragma unroll
-                for (int r = 0; r < RMAX; ++r) {
+                for (int r = 0; r < RF; ++r) {
                     uint32_t c = 0;
                     if (r < R && grp == 0 && has_words)
 #pragma unroll
@@ -278,7 +278,7 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                 if (!use_bitmap) stage = 1;
                 uint32_t list_total = 0;
 #pragma unroll
-                for (int r = 0; r < RMAX; ++r)
+                for (int r = 0; r < RF; ++r)
                     if (r < R) list_total += pc[r] * 2 > ix.B ? ix.B - pc[r] : pc[r];
                 const bool union_ok = ix.mem_bits && list_total <= 2u * QK_ID_CAP;
                 if (stage == 3 && !union_ok) stage = 1;
@@ -290,7 +290,7 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                     if (union_ok) {
                         uni = kw / 32 + 1;
 #pragma unroll
-                        for (int r = 0; r < RMAX; ++r) {
+                        for (int r = 0; r < RF; ++r) {
                             if (r >= R) continue;
                             const uint32_t cr = pc[r] < ix.B - pc[r] ? pc[r] : ix.B - pc[r];
                             uni += (uint64_t)cr * (kw / 32 + 1);
@@ -321,7 +321,7 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                                                           ph[u].y >> 16,     ph[u].z & 0xffffu, ph[u].z >> 16,
                                                           ph[u].w & 0xffffu, ph[u].w >> 16};
 #pragma unroll
-                                for (int r = 0; r < RMAX; ++r)
+                                for (int r = 0; r < RF; ++r)
                                     if (r < R) ok &= (sM[r * ix.S + (cell[r] >> 5)] >> (cell[r] & 31)) & 1u;
                                 const unsigned bal = __ballot_sync(FULL, ok);
                                 if (lane == 0 && i0 + 32 * u < ix.K) sBits[(i0 >> 5) + u] = bal;
@@ -380,7 +380,7 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                                                             ph[c].w & 0xffffu, ph[c].w >> 16};
                                     bool ok = true;
 #pragma unroll
-                                    for (int r = 0; r < RMAX; ++r)
+                                    for (int r = 0; r < RF; ++r)
                                         if (r < R && r != rstar) ok &= (sM[r * ix.S + (cl[r] >> 5)] >> (cl[r] & 31)) & 1u;
                                     if (ok) atomicOr(sBits + (id[c] >> 5), 1u << (id[c] & 31));
                                 }
@@ -393,10 +393,10 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                         // shared memory first (warp prefix sums), then each lane ORs
                         // UW words per cell for UC cells at a time.
                         uint16_t* list = reinterpret_cast<uint16_t*>(sIds);
-                        uint32_t list_off[RMAX + 1];
+                        uint32_t list_off[RF + 1];
                         list_off[0] = 0;
 #pragma unroll
-                        for (int r = 0; r < RMAX; ++r) {
+                        for (int r = 0; r < RF; ++r) {
                             uint32_t n_r = 0;
                             if (r < R) {
                                 const bool comp = pc[r] * 2 > ix.B;
@@ -434,7 +434,7 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                                 g[u] = w < bw ? __ldg(ix.reg + w) : 0u;
                             }
 #pragma unroll
-                            for (int r = 0; r < RMAX; ++r) {
+                            for (int r = 0; r < RF; ++r) {
                                 if (r >= R) continue;
                                 const bool comp = pc[r] * 2 > ix.B;
                                 const uint32_t* mb = ix.mem_bits + (uint64_t)r * ix.B * bw;
@@ -557,13 +557,13 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
 // query more than one warp.  A launch whose instance does not match the
 // batch's group size returns at once, so a captured graph holds both and the
 // batch size, read on the device, picks.  Tilings whose row words in flight
-// (RMAX * ETA * V) fit in 64 registers are held to 128 registers a thread, so
+// (RF * ETA * V) fit in 64 registers are held to 128 registers a thread, so
 // two full blocks share an SM; wider ones keep every register they need, and
 // so does the one-warp V = 4, ETA = 2 tiling, measured 11% faster that way on
 // the uneven workload (16-byte rows, 8 tables).
 template <int V, int G, int ETA, bool GROUP>
 __global__ void __launch_bounds__(QK_THREADS_MAX,
-                                  (RMAX * ETA * V <= 64 && !(V == 4 && ETA == 2 && !GROUP)) ? 2 : 1)
+                                  (RF * ETA * V <= 64 && !(V == 4 && ETA == 2 && !GROUP)) ? 2 : 1)
     k_query(IndexView ix, HashParams hp, BatchView b, QueryOut o, int set_stage, int batch,
             uint32_t smem_per_warp, int use_bitmap, int order, int load_kind, int group,
             unsigned long long group_warps, DevStatus* st) {
@@ -633,9 +633,9 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                 if (leader) *ctl_dead = 0;
                 qk_group_sync(P, gi);
 
-                uint32_t M[RMAX][V];
+                uint32_t M[RF][V];
 #pragma unroll
-                for (int r = 0; r < RMAX; ++r)
+                for (int r = 0; r < RF; ++r)
 #pragma unroll
                     for (int v = 0; v < V; ++v) M[r][v] = has_words ? ~0u : 0u;
 
@@ -670,10 +670,10 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                     }
                     const uint64_t y = mix64(key);
                     // A3: issue every row read of this step, then combine
-                    uint32_t val[RMAX][ETA][V];
+                    uint32_t val[RF][ETA][V];
                     const bool ld = act && has_words;
 #pragma unroll
-                    for (int r = 0; r < RMAX; ++r) {
+                    for (int r = 0; r < RF; ++r) {
                         if (r >= rlo && r < rhi && ld) {
                             const uint32_t* rb = rows + (uint64_t)r * ix.m * ix.S + w0;
 #pragma unroll
@@ -687,7 +687,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                     }
                     uint32_t nz = 0;
 #pragma unroll
-                    for (int r = 0; r < RMAX; ++r) {
+                    for (int r = 0; r < RF; ++r) {
                         if (r < R) {
                             uint32_t any = 0;
                             const bool probed_r = r >= rlo && r < rhi;
@@ -726,7 +726,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                 // holds a superset, which the AND leaves correct)
                 if (alive && mine && grp == 0 && has_words) {
 #pragma unroll
-                    for (int r = 0; r < RMAX; ++r)
+                    for (int r = 0; r < RF; ++r)
                         if (r < R)
 #pragma unroll
                             for (int v = 0; v < V; ++v) atomicAnd(sM + r * ix.S + w0 + v, M[r][v]);
@@ -738,12 +738,12 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                 unsigned long long start = 0;
                 // per-table hit-cell counts; the table with the fewest hit cells
                 // gives the sparse stage its candidates
-                uint32_t pc[RMAX];
+                uint32_t pc[RF];
                 int rstar = 0;
                 uint32_t pmin = 0xffffffffu;
                 if (alive) {
 #pragma unroll
-                    for (int r = 0; r < RMAX; ++r) {
+                    for (int r = 0; r < RF; ++r) {
                         uint32_t c = 0;
                         if (r < R)
                             for (uint32_t w = lane; w < ix.S; w += 32) c += __popc(sM[r * ix.S + w]);
@@ -764,7 +764,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                     int stage = set_stage;
                     uint32_t list_total = 0;
 #pragma unroll
-                    for (int r = 0; r < RMAX; ++r)
+                    for (int r = 0; r < RF; ++r)
                         if (r < R) list_total += pc[r] * 2 > ix.B ? ix.B - pc[r] : pc[r];
                     const bool union_ok = ix.mem_bits && list_total <= 2u * QK_ID_CAP;
                     if (stage == 3 && !union_ok) stage = 1;
@@ -776,7 +776,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                         if (union_ok) {
                             uni = kw / 32 + 1;
 #pragma unroll
-                            for (int r = 0; r < RMAX; ++r) {
+                            for (int r = 0; r < RF; ++r) {
                                 if (r >= R) continue;
                                 const uint32_t cr = pc[r] < ix.B - pc[r] ? pc[r] : ix.B - pc[r];
                                 uni += (uint64_t)cr * (kw / 32 + 1);
@@ -807,7 +807,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                                                               ph[u].y >> 16,     ph[u].z & 0xffffu, ph[u].z >> 16,
                                                               ph[u].w & 0xffffu, ph[u].w >> 16};
 #pragma unroll
-                                    for (int r = 0; r < RMAX; ++r)
+                                    for (int r = 0; r < RF; ++r)
                                         if (r < R) ok &= (sM[r * ix.S + (cell[r] >> 5)] >> (cell[r] & 31)) & 1u;
                                     const unsigned bal = __ballot_sync(FULL, ok);
                                     if (lane == 0 && i0 + 32 * u < ix.K) sBits[(i0 >> 5) + u] = bal;
@@ -867,7 +867,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                                                                 ph[c].w & 0xffffu, ph[c].w >> 16};
                                         bool ok = true;
 #pragma unroll
-                                        for (int r = 0; r < RMAX; ++r)
+                                        for (int r = 0; r < RF; ++r)
                                             if (r < R && r != rstar) ok &= (sM[r * ix.S + (cl[r] >> 5)] >> (cl[r] & 31)) & 1u;
                                         if (ok) atomicOr(sBits + (id[c] >> 5), 1u << (id[c] & 31));
                                     }
@@ -881,10 +881,10 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                             // each lane ORs UW words per cell for UC cells at a time;
                             // the group's warps take interleaved word ranges.
                             uint16_t* list = reinterpret_cast<uint16_t*>(sIds);
-                            uint32_t list_off[RMAX + 1];
+                            uint32_t list_off[RF + 1];
                             list_off[0] = 0;
 #pragma unroll
-                            for (int r = 0; r < RMAX; ++r) {
+                            for (int r = 0; r < RF; ++r) {
                                 uint32_t n_r = 0;
                                 if (r < R) {
                                     const bool comp = pc[r] * 2 > ix.B;
@@ -922,7 +922,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                                     g[u] = w < bw ? __ldg(ix.reg + w) : 0u;
                                 }
 #pragma unroll
-                                for (int r = 0; r < RMAX; ++r) {
+                                for (int r = 0; r < RF; ++r) {
                                     if (r >= R) continue;
                                     const bool comp = pc[r] * 2 > ix.B;
                                     const uint32_t* mb = ix.mem_bits + (uint64_t)r * ix.B * bw;

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(Q1_THREADS)
         bool ok = i < ix.K && ((ix.reg[i >> 5] >> (i & 31)) & 1u);
         if (ok)
             for (uint32_t r = 0; r < ix.R; ++r) {
-                const uint32_t b = ix.phi[i * PHI_STRIDE + r];
+                const uint32_t b = ix.phi[i * ix.ps + r];
                 ok &= (sM[r * ix.W + (b >> 5)] >> (b & 31)) & 1u;
             }
         const unsigned bal = __ballot_sync(FULL, ok);
@@ -105,6 +105,12 @@ cudaError_t launch_query_one(const IndexView& ix, const HashParams& hp, int seq,
                              const uint64_t* keys, uint64_t len, uint32_t k, int canon, int skipn, uint32_t* out_ids,
                              uint32_t* out_count, int* bad, cudaStream_t s) {
     const size_t smem = (size_t)(ix.R * ix.W + 33) * 4;
+    if (smem > 48 * 1024) {  // wide rows: masks of R * W words
+        const cudaError_t e =
+            cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_query_one), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     k_query_one<<<1, Q1_THREADS, smem, s>>>(ix, hp, seq, bases, keys, len, k, canon, skipn, out_ids, out_count,
                                             bad);
     return cudaGetLastError();

@@ -32,7 +32,7 @@ cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// partition table: phi[i*PHI_STRIDE + r] = phi_r(i)
+// partition table: phi[i*ps + r] = phi_r(i), ps = phi_stride_for(R) (8 or 16)
 
 struct PhiParams {
     uint64_t a[RMAX], c[RMAX];
@@ -45,22 +45,27 @@ struct PhiParams {
 // node-parallel construction; one node gives the plain partition).  B is the
 // current cell count, smaller than B_local * n_nodes after folding over.
 __global__ void k_phi_init(uint16_t* phi, uint64_t K, uint32_t R, uint32_t B, PhiParams pp) {
+    const uint32_t ps = phi_stride_for(R);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < K;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t node = pp.n_nodes > 1 ? partition_hash(pp.a_tau, pp.c_tau, i, pp.n_nodes) : 0;
-        uint16_t row[PHI_STRIDE];
+        uint16_t row[RMAX];
 #pragma unroll
-        for (int r = 0; r < PHI_STRIDE; ++r) {
+        for (int r = 0; r < RMAX; ++r) {
             uint64_t cell = 0;
             if (r < (int)R) cell = ((uint64_t)pp.B_local * node + partition_hash(pp.a[r], pp.c[r], i, pp.B_local)) % B;
             row[r] = (uint16_t)cell;
         }
-        uint4 v;
-        v.x = row[0] | ((uint32_t)row[1] << 16);
-        v.y = row[2] | ((uint32_t)row[3] << 16);
-        v.z = row[4] | ((uint32_t)row[5] << 16);
-        v.w = row[6] | ((uint32_t)row[7] << 16);
-        reinterpret_cast<uint4*>(phi)[i] = v;
+#pragma unroll
+        for (int h = 0; h < RMAX / 8; ++h) {
+            if (h * 8u >= ps) break;
+            uint4 v;
+            v.x = row[8 * h + 0] | ((uint32_t)row[8 * h + 1] << 16);
+            v.y = row[8 * h + 2] | ((uint32_t)row[8 * h + 3] << 16);
+            v.z = row[8 * h + 4] | ((uint32_t)row[8 * h + 5] << 16);
+            v.w = row[8 * h + 6] | ((uint32_t)row[8 * h + 7] << 16);
+            reinterpret_cast<uint4*>(phi + i * ps)[h] = v;
+        }
     }
 }
 
@@ -596,33 +601,39 @@ cudaError_t launch_fold(const uint32_t* old_rows, uint64_t n_rows, uint32_t W, u
 // ---------------------------------------------------------------------------
 // statistics: set bits of every Bloom filter (bit b of the rows of table r)
 
+// Block (x, r, z) counts cells [z*CP_CELLS, (z+1)*CP_CELLS) of table r over
+// its share of the rows, in shared-memory counters.
+constexpr uint32_t CP_CELLS = 8192;
+
 __global__ void k_cell_popcount(IndexView ix, unsigned long long* out) {
-    extern __shared__ unsigned int cnt[];  // B counters
+    __shared__ unsigned int cnt[CP_CELLS];
     const uint32_t r = blockIdx.y;
-    for (uint32_t b = threadIdx.x; b < ix.B; b += blockDim.x) cnt[b] = 0;
+    const uint32_t c0 = blockIdx.z * CP_CELLS;
+    const uint32_t nc = min(CP_CELLS, ix.B - c0);
+    for (uint32_t b = threadIdx.x; b < nc; b += blockDim.x) cnt[b] = 0;
     __syncthreads();
     const uint32_t* rows = ix.rows + (uint64_t)r * ix.m * ix.S;
+    const uint32_t w_lo = c0 / 32, w_hi = (c0 + nc + 31) / 32;
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < ix.m;
          p += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t* row = rows + p * ix.S;
-        for (uint32_t w = 0; w < ix.W; ++w) {
+        for (uint32_t w = w_lo; w < w_hi; ++w) {
             uint32_t x = row[w];
             while (x) {
-                int bit = __ffs(x) - 1;
-                atomicAdd(&cnt[w * 32 + bit], 1u);
+                const uint32_t b = w * 32 + (uint32_t)(__ffs(x) - 1);
+                atomicAdd(&cnt[b - c0], 1u);
                 x &= x - 1;
             }
         }
     }
     __syncthreads();
-    for (uint32_t b = threadIdx.x; b < ix.B; b += blockDim.x)
-        if (cnt[b]) atomicAdd(out + (uint64_t)r * ix.B + b, (unsigned long long)cnt[b]);
+    for (uint32_t b = threadIdx.x; b < nc; b += blockDim.x)
+        if (cnt[b]) atomicAdd(out + (uint64_t)r * ix.B + c0 + b, (unsigned long long)cnt[b]);
 }
 
 cudaError_t launch_cell_popcount(const IndexView& ix, unsigned long long* out, cudaStream_t s) {
-    dim3 grid((unsigned)grid_for(ix.m, 256, 512), ix.R);
-    size_t smem = sizeof(unsigned int) * ix.B;
-    k_cell_popcount<<<grid, 256, smem, s>>>(ix, out);
+    dim3 grid((unsigned)grid_for(ix.m, 256, ix.B > CP_CELLS ? 128 : 512), ix.R, (ix.B + CP_CELLS - 1) / CP_CELLS);
+    k_cell_popcount<<<grid, 256, 0, s>>>(ix, out);
     return cudaGetLastError();
 }
 
@@ -635,7 +646,7 @@ __global__ void k_member_count(const uint16_t* __restrict__ phi, const uint32_t*
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < K;
          i += (uint64_t)gridDim.x * blockDim.x) {
         if (!((reg[i >> 5] >> (i & 31)) & 1u)) continue;
-        for (uint32_t r = 0; r < R; ++r) atomicAdd(cnt + r * B + phi[i * PHI_STRIDE + r], 1u);
+        for (uint32_t r = 0; r < R; ++r) atomicAdd(cnt + r * B + phi[i * phi_stride_for(R) + r], 1u);
     }
 }
 
@@ -645,9 +656,10 @@ __global__ void k_member_place(const uint16_t* __restrict__ phi, const uint32_t*
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < K;
          i += (uint64_t)gridDim.x * blockDim.x) {
         if (!((reg[i >> 5] >> (i & 31)) & 1u)) continue;
-        const uint4 row = reinterpret_cast<const uint4*>(phi)[i];
+        // (the sparse stage's partition-row copy: the first 8 tables, all it reads)
+        const uint4 row = reinterpret_cast<const uint4*>(phi + i * phi_stride_for(R))[0];
         for (uint32_t r = 0; r < R; ++r) {
-            uint32_t cell = r * B + phi[i * PHI_STRIDE + r];
+            uint32_t cell = r * B + phi[i * phi_stride_for(R) + r];
             uint32_t at = atomicAdd(fill + cell, 1u);
             ids[off[cell] + at] = (uint32_t)i;
             rows[off[cell] + at] = row;
@@ -661,7 +673,7 @@ __global__ void k_member_bits(const uint16_t* __restrict__ phi, uint64_t K, uint
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < K;
          i += (uint64_t)gridDim.x * blockDim.x)
         for (uint32_t r = 0; r < R; ++r) {
-            const uint64_t cell = (uint64_t)r * B + phi[i * PHI_STRIDE + r];
+            const uint64_t cell = (uint64_t)r * B + phi[i * phi_stride_for(R) + r];
             atomicOr(bits + cell * bw + (i >> 5), 1u << (i & 31));
         }
 }

@@ -155,6 +155,7 @@ struct rambo {
         v.K = K;
         v.B = B;
         v.phi = phi;
+        v.ps = phi_stride_for(R);
         v.reg = reg;
         v.mem_off = mem_off;
         v.mem_ids = mem_ids;
@@ -423,6 +424,22 @@ struct QueryDest {
 };
 
 int resolve_tuning(rambo* h, uint64_t n, int& use_bitmap, QueryTuning& t) {
+    t = QueryTuning{};
+    if (query_is_wide(h->R, h->S)) {
+        // rows wider than the register tiling or more than RF tables: one
+        // thread block per query, as many resident as fit
+        use_bitmap = 0;
+        t.wide = 1;
+        t.set_stage = 1;
+        const int per_sm = query_wide_blocks_per_sm(h->R, h->S);
+        if (per_sm < 1) return RAMBO_EINVAL;
+        uint64_t blocks = (uint64_t)per_sm * h->num_sms;
+        if (blocks > n) blocks = n;
+        t.blocks = (int)(blocks < 1 ? 1 : blocks);
+        t.warps_per_block = QW_THREADS / 32;
+        t.batch = 1;
+        return RAMBO_OK;
+    }
     t.V = (int)h->cfg.words_per_lane;
     t.G = (int)h->cfg.lanes_per_key;
     t.warps_per_block = (int)h->cfg.warps_per_block;
@@ -742,7 +759,7 @@ static int create_impl(uint64_t K, uint32_t B_local, uint32_t n_nodes, uint32_t 
         return code;
     };
     if (cudaMalloc(&h->rows, h->index_words() * 4) != cudaSuccess) return fail(RAMBO_ENOMEM);
-    if (cudaMalloc(&h->phi, K * PHI_STRIDE * sizeof(uint16_t)) != cudaSuccess) return fail(RAMBO_ENOMEM);
+    if (cudaMalloc(&h->phi, K * phi_stride_for(R) * sizeof(uint16_t)) != cudaSuccess) return fail(RAMBO_ENOMEM);
     if (cudaMalloc(&h->reg, ((K + 31) / 32) * 4) != cudaSuccess) return fail(RAMBO_ENOMEM);
     if (cudaMalloc(&h->st, sizeof(DevStatus)) != cudaSuccess) return fail(RAMBO_ENOMEM);
     if (cudaMallocHost(&h->h_st, sizeof(DevStatus)) != cudaSuccess) return fail(RAMBO_ENOMEM);
@@ -1002,10 +1019,11 @@ int rambo_export_registered(const rambo_t* h, uint32_t* host_words, uint64_t n_w
 int rambo_export_partition(const rambo_t* h, uint16_t* host_phi, uint64_t n) {
     if (!h || !host_phi || n != h->K * h->R) return RAMBO_EINVAL;
     CK(cudaSetDevice(h->device));
-    std::vector<uint16_t> tmp(h->K * PHI_STRIDE);
+    const uint32_t ps = phi_stride_for(h->R);
+    std::vector<uint16_t> tmp(h->K * ps);
     CK(cudaMemcpy(tmp.data(), h->phi, tmp.size() * 2, cudaMemcpyDeviceToHost));
     for (uint64_t i = 0; i < h->K; ++i)
-        for (uint32_t r = 0; r < h->R; ++r) host_phi[i * h->R + r] = tmp[i * PHI_STRIDE + r];
+        for (uint32_t r = 0; r < h->R; ++r) host_phi[i * h->R + r] = tmp[i * ps + r];
     return RAMBO_OK;
 }
 

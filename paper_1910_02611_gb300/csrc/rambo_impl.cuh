@@ -14,7 +14,14 @@ namespace rgb {
 
 constexpr int RMAX = RAMBO_MAX_R;
 constexpr int EMAX = RAMBO_MAX_ETA;
-constexpr int PHI_STRIDE = 8;  // partition table row: 8 uint16 per set ID (16 B)
+// the register-tiled query kernel: at most RF tables, rows of at most
+// FAST_MAX_S words (32 lanes x 4 words)
+constexpr int RF = 8;
+constexpr uint32_t FAST_MAX_S = 128;
+// partition table row: 8 uint16 per set ID (16 B) for R <= 8, else 16 (32 B)
+__host__ __device__ inline uint32_t phi_stride_for(uint32_t R) { return R <= 8 ? 8u : 16u; }
+// true when an index needs the block-per-query kernel
+__host__ __device__ inline bool query_is_wide(uint32_t R, uint32_t S) { return R > (uint32_t)RF || S > FAST_MAX_S; }
 constexpr unsigned FULL = 0xffffffffu;
 constexpr unsigned long long NO_ERR = ~0ull;
 
@@ -180,7 +187,8 @@ struct IndexView {
     uint32_t S, W;         // row stride / words holding bits
     uint64_t K;
     uint32_t B;
-    const uint16_t* phi;   // [K][PHI_STRIDE]
+    const uint16_t* phi;   // [K][ps]
+    uint32_t ps;           // partition-table row stride (phi_stride_for(R))
     uint32_t* reg;         // ceil(K/32) words
     const uint64_t* mem_off;  // [R*B + 1] offsets of each cell's registered members (sparse stage)
     const uint32_t* mem_ids;  // registered members of each cell (unordered)
@@ -234,6 +242,7 @@ struct QueryTuning {
     int group;             // warps per query: 0 = from the batch size on the device, else at most this
     int blocks_group;      // grid of the grouped instance (0: not used)
     unsigned long long group_warps;  // its warps, the budget the group size is chosen against
+    int wide;              // 1: the block-per-query kernel (R > RF or rows wider than FAST_MAX_S words)
 };
 
 // ---------------------------------------------------------------------------
@@ -286,6 +295,14 @@ unsigned query_group_size(uint64_t n, int group, unsigned wpb, uint64_t group_wa
 cudaError_t launch_query(const IndexView& ix, const HashParams& hp, const BatchView& b, const QueryOut& o,
                          const QueryTuning& t, int use_bitmap, DevStatus* st, cudaStream_t s,
                          int* n_launched = nullptr);
+
+// k_query_wide.cu: block-per-query kernel for wide rows or many tables
+constexpr int QW_THREADS = 256;
+size_t query_wide_smem_bytes(uint32_t R, uint32_t S);
+int query_wide_blocks_per_sm(uint32_t R, uint32_t S);
+cudaError_t launch_query_wide(const IndexView& ix, const HashParams& hp, const BatchView& b, const QueryOut& o,
+                              int blocks, DevStatus* st, cudaStream_t s);
+cudaError_t load_query_wide_kernel();
 
 // k_query_one.cu: the plain one-query-per-launch kernel
 cudaError_t launch_query_one(const IndexView& ix, const HashParams& hp, int seq, const uint8_t* bases,

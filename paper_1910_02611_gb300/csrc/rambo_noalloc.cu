@@ -69,6 +69,7 @@ int noalloc_setup(uint32_t eta, unsigned char** base) {
     }
     e = load_util_kernels();
     if (e == cudaSuccess) e = load_query_kernels(eta);
+    if (e == cudaSuccess) e = load_query_wide_kernel();
     if (e != cudaSuccess) {
         cudaGetLastError();
         return map_cuda(e);

@@ -62,3 +62,19 @@ def assert_query_equal(g, o, queries, k: int = 31, nthreads: int = NTHREADS, **g
         raise AssertionError(f"result sizes differ first at query {q}: gpu {off[q+1]-off[q]} oracle {roff[q+1]-roff[q]}")
     assert np.array_equal(ids, rids)
     return ids, off
+
+
+def assert_index_equal_by_rows(g, o):
+    """Index bits through the oracle's row view (bit p of every cell of a
+    table): cheaper than per-cell filters when B is large."""
+    rows = g.export_index()  # [R, m, S]
+    R, m, S = rows.shape
+    assert (R, m) == (o.R, o.m)
+    W = (o.B + 31) // 32
+    assert np.all(rows[:, :, W:] == 0), "padding words must stay zero"
+    for r in range(R):
+        ref = np.stack([o.get_row(r, p) for p in range(m)]).view(np.uint32)[:, :W]  # [m, W]
+        if not np.array_equal(rows[r, :, :W], ref):
+            bad = np.argwhere(rows[r, :, :W] != ref)
+            raise AssertionError(f"table {r}: {len(bad)} words differ, first (pos, word) {bad[:3].tolist()}")
+    assert np.array_equal(g.export_registered(), o.registered())

@@ -55,8 +55,8 @@ def test_create_rejects_bad_parameters_before_touching_the_gpu(lib):
     lib.rambo_create.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
                                  ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]
     h = ctypes.c_void_p()
-    for args in [(10, 4, 2, 1000, 2), (10, 0, 2, 1024, 2), (10, 4, 9, 1024, 2), (10, 4, 2, 1024, 5),
-                 (0, 4, 2, 1024, 2), (10, 4097, 2, 1024, 2), (10, 4, 2, 1 << 33, 2)]:
+    for args in [(10, 4, 2, 1000, 2), (10, 0, 2, 1024, 2), (10, 4, 17, 1024, 2), (10, 4, 2, 1024, 5),
+                 (0, 4, 2, 1024, 2), (10, 65536, 2, 1024, 2), (10, 4, 2, 1 << 33, 2)]:
         assert lib.rambo_create(*args, 1, ctypes.byref(h)) == -1
         assert not h.value
 
@@ -88,8 +88,8 @@ def test_parameter_checks_precede_the_gpu():
     from paper_1910_02611_gb300 import EINVAL, Rambo, RamboError
 
     for args in ((0, 10, 3, 1 << 20, 2), (100, 0, 3, 1 << 20, 2), (100, 10, 0, 1 << 20, 2),
-                 (100, 10, 3, 1000, 2), (100, 10, 3, 1 << 20, 0), (100, 10, 9, 1 << 20, 2),
-                 (100, 5000, 3, 1 << 20, 2), (100, 10, 3, 1 << 20, 5)):
+                 (100, 10, 3, 1000, 2), (100, 10, 3, 1 << 20, 0), (100, 10, 17, 1 << 20, 2),
+                 (100, 65536, 3, 1 << 20, 2), (100, 10, 3, 1 << 20, 5)):
         with pytest.raises(RamboError) as e:
             Rambo(*args, 42)
         assert e.value.code == EINVAL, args

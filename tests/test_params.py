@@ -155,7 +155,7 @@ def test_unreachable_failure_rate_reports_erange():
 
     with pytest.raises(RamboError) as e:
         suggest_params(10**6, 1000, V=500.0, p=0.2, delta=1e-9)
-    assert e.value.code == ERANGE and e.value.params["R"] == 8
+    assert e.value.code == ERANGE and e.value.params["R"] == 16  # RAMBO_MAX_R
 
 
 def test_sample_errors():

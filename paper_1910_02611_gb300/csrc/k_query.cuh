@@ -581,8 +581,8 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
     const uint32_t bw = qk_bitmap_words(ix.K);
     const uint32_t* __restrict__ rows = ix.rows;
 
-    if (*(volatile unsigned long long*)&st->err != NO_ERR) return;
     bv_resolve(b);
+    if (query_batch_rejected(b, st)) return;
     // Query group: P warps answer one query together (P = 1 for large
     // batches; up to 8 when the batch is too small to fill the grid, so a
     // lone query's steps and set stage spread over more warps).  group = 0

@@ -45,8 +45,8 @@ __global__ void __launch_bounds__(QW_THREADS) k_query_wide(IndexView ix, HashPar
     uint32_t* ctl_act = ctl + 5;                                                     // [5..8] term valid flags
     uint32_t* warp_cnt = ctl + 16;                                                   // [16..23] per-warp counts
 
-    if (*(volatile unsigned long long*)&st->err != NO_ERR) return;
     bv_resolve(b);
+    if (query_batch_rejected(b, st)) return;
     const unsigned tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned nthreads = blockDim.x, nwarps = nthreads >> 5;
     const uint32_t rmask = R >= 32 ? ~0u : ((1u << R) - 1u);

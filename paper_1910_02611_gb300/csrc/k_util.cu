@@ -99,14 +99,13 @@ cudaError_t launch_or_words(uint32_t* dst, const uint32_t* src, uint64_t n, cuda
 // ---------------------------------------------------------------------------
 // batch validation: set IDs < K, non-decreasing offsets, minimum item length
 
-__global__ void k_validate(BatchView b, uint64_t min_len, unsigned short_prio, uint64_t K,
-                           DevStatus* st) {
-    bv_resolve(b);
-    // a descriptor-driven batch must start at 0 and end exactly at the staged data's end
-    if (b.desc && blockIdx.x == 0 && threadIdx.x == 0 && (b.offsets[0] != 0 || b.offsets[b.n] != b.total))
-        record_error(st, 0, PRIO_EINVAL);
-    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < b.n;
-         t += (uint64_t)gridDim.x * blockDim.x) {
+// Validation of items [t0, n) with stride: set IDs < K, non-decreasing
+// offsets, minimum length; a descriptor-driven batch must also start at 0
+// and end exactly at the staged data's end.
+__device__ __forceinline__ void validate_items(const BatchView& b, uint64_t min_len, unsigned short_prio, uint64_t K,
+                                               DevStatus* st, uint64_t t0, uint64_t stride) {
+    if (b.desc && t0 == 0 && (b.offsets[0] != 0 || b.offsets[b.n] != b.total)) record_error(st, 0, PRIO_EINVAL);
+    for (uint64_t t = t0; t < b.n; t += stride) {
         if (b.set_ids && b.set_ids[t] >= K) {
             record_error(st, t, PRIO_ERANGE);
             continue;
@@ -118,6 +117,13 @@ __global__ void k_validate(BatchView b, uint64_t min_len, unsigned short_prio, u
         }
         if (hi - lo < min_len) record_error(st, t, short_prio);
     }
+}
+
+__global__ void k_validate(BatchView b, uint64_t min_len, unsigned short_prio, uint64_t K,
+                           DevStatus* st) {
+    bv_resolve(b);
+    validate_items(b, min_len, short_prio, K, st, blockIdx.x * (uint64_t)blockDim.x + threadIdx.x,
+                   (uint64_t)gridDim.x * blockDim.x);
 }
 
 cudaError_t launch_validate_batch(const BatchView& b, uint64_t min_len, uint64_t K, DevStatus* st,
@@ -168,18 +174,14 @@ __device__ __forceinline__ uint32_t unresolved4(uint32_t w) {
     return m;
 }
 
-// With nmask (skip-N), bit t of nmask[w] marks base 32w + t as unresolved
-// (packed as 0) and nothing is reported; bits past the end are 0.
-__global__ void k_pack(const uint8_t* __restrict__ bases, uint64_t total, uint64_t* __restrict__ packed,
-                       uint64_t n_words, DevStatus* st, const uint64_t* __restrict__ desc,
-                       uint32_t* __restrict__ nmask) {
-    if (desc) {
-        total = desc[1];
-        n_words = total / 32 + 2;
-    }
+// Packs words [w0, n_words) with stride.  With nmask (skip-N), bit t of
+// nmask[w] marks base 32w + t as unresolved (packed as 0) and nothing is
+// reported; bits past the end are 0.
+__device__ __forceinline__ void pack_words(const uint8_t* __restrict__ bases, uint64_t total,
+                                           uint64_t* __restrict__ packed, uint64_t n_words, DevStatus* st,
+                                           uint32_t* __restrict__ nmask, uint64_t w0, uint64_t stride) {
     const bool aligned = (reinterpret_cast<uintptr_t>(bases) & 15) == 0;
-    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < n_words;
-         w += (uint64_t)gridDim.x * blockDim.x) {
+    for (uint64_t w = w0; w < n_words; w += stride) {
         uint64_t v = 0;
         uint64_t p0 = w * 32;
         unsigned long long bad = NO_ERR;
@@ -221,6 +223,39 @@ __global__ void k_pack(const uint8_t* __restrict__ bases, uint64_t total, uint64
         if (nmask) nmask[w] = um;
         if (bad != NO_ERR) atomicMin(&st->bad_pos, bad);
     }
+}
+
+__global__ void k_pack(const uint8_t* __restrict__ bases, uint64_t total, uint64_t* __restrict__ packed,
+                       uint64_t n_words, DevStatus* st, const uint64_t* __restrict__ desc,
+                       uint32_t* __restrict__ nmask) {
+    if (desc) {
+        total = desc[1];
+        n_words = total / 32 + 2;
+    }
+    pack_words(bases, total, packed, n_words, st, nmask, blockIdx.x * (uint64_t)blockDim.x + threadIdx.x,
+               (uint64_t)gridDim.x * blockDim.x);
+}
+
+// Query intake in one launch: validation of every query and, for DNA, the
+// 2-bit packing of the batch (the two write only the error words and the
+// packed buffers, so they need no ordering).  The item holding the lowest
+// unresolved base is looked up by the query kernel (resolve_bad_base).
+__global__ void k_intake(BatchView b, uint64_t min_len, unsigned short_prio, uint64_t K,
+                         const uint8_t* __restrict__ bases, uint64_t* __restrict__ packed, uint64_t n_words,
+                         uint32_t* __restrict__ nmask, DevStatus* st) {
+    bv_resolve(b);
+    const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+    validate_items(b, min_len, short_prio, K, st, t0, stride);
+    if (bases) pack_words(bases, b.total, packed, b.desc ? b.total / 32 + 2 : n_words, st, nmask, t0, stride);
+}
+
+cudaError_t launch_intake(const BatchView& b, uint64_t min_len, uint64_t K, const uint8_t* bases, uint64_t* packed,
+                          uint64_t n_words, uint32_t* nmask, DevStatus* st, cudaStream_t s) {
+    if (b.n == 0 && !b.desc) return cudaSuccess;
+    const unsigned prio = b.seq ? PRIO_EBADSEQ : PRIO_EINVAL;
+    const uint64_t work = b.n > n_words ? b.n : n_words;  // capacities for a descriptor batch
+    k_intake<<<grid_for(work, 256, 1 << 16), 256, 0, s>>>(b, min_len, prio, K, bases, packed, n_words, nmask, st);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pack(const uint8_t* bases, uint64_t total, uint64_t* packed, uint64_t n_words,
@@ -269,17 +304,7 @@ cudaError_t launch_check_windows(const BatchView& b, DevStatus* st, cudaStream_t
 // The item holding the lowest bad byte gets an EBADSEQ error.
 __global__ void k_resolve_bad_base(BatchView b, DevStatus* st) {
     bv_resolve(b);
-    unsigned long long p = st->bad_pos;
-    if (p == NO_ERR || b.n == 0) return;
-    uint64_t abs_p = p + b.off0;
-    // largest t in [0, n) with offsets[t] <= abs_p
-    uint64_t lo = 0, hi = b.n;  // invariant: answer in [lo, hi)
-    while (hi - lo > 1) {
-        uint64_t mid = lo + (hi - lo) / 2;
-        if (b.offsets[mid] <= abs_p) lo = mid;
-        else hi = mid;
-    }
-    record_error(st, lo, PRIO_EBADSEQ);
+    resolve_bad_base(b, st);
 }
 
 cudaError_t launch_resolve_bad_base(const BatchView& b, DevStatus* st, cudaStream_t s) {
@@ -515,9 +540,11 @@ cudaError_t launch_cluster_order(const BatchView& b, uint64_t* keys, uint32_t* h
 
 __global__ void k_gather(QueryOut o, const uint64_t* __restrict__ id_offsets, uint64_t n,
                          uint32_t* __restrict__ ids, const DevStatus* st, const uint64_t* __restrict__ n_dev,
-                         uint64_t ids_cap) {
-    if (st->err != NO_ERR || st->cursor > o.stage_cap) return;
+                         uint64_t ids_cap, unsigned long long* total_out) {
     if (n_dev) n = *n_dev;
+    // the number of result IDs, for a caller that reads the status block only
+    if (total_out && blockIdx.x == 0 && threadIdx.x == 0) *total_out = id_offsets[n];
+    if (st->err != NO_ERR || st->cursor > o.stage_cap) return;
     if (id_offsets[n] > ids_cap) return;  // the caller sees the total and reports the shortfall
     const int lane = threadIdx.x & 31;
     uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -532,10 +559,11 @@ __global__ void k_gather(QueryOut o, const uint64_t* __restrict__ id_offsets, ui
 }
 
 cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_t n, uint32_t* ids,
-                          const DevStatus* st, cudaStream_t s, const uint64_t* n_dev, uint64_t ids_cap) {
+                          const DevStatus* st, cudaStream_t s, const uint64_t* n_dev, uint64_t ids_cap,
+                          unsigned long long* total_out) {
     if (n == 0) return cudaSuccess;
     int blocks = grid_for(n * 32, 256, 152 * 16);
-    k_gather<<<blocks, 256, 0, s>>>(o, id_offsets, n, ids, st, n_dev, ids_cap);
+    k_gather<<<blocks, 256, 0, s>>>(o, id_offsets, n, ids, st, n_dev, ids_cap, total_out);
     return cudaGetLastError();
 }
 
@@ -550,7 +578,7 @@ cudaError_t load_util_kernels() {
                          reinterpret_cast<const void*>(&k_pack), reinterpret_cast<const void*>(&k_resolve_bad_base),
                          reinterpret_cast<const void*>(&k_scan_one_block), reinterpret_cast<const void*>(&k_scan_tiles),
                          reinterpret_cast<const void*>(&k_scan_sums), reinterpret_cast<const void*>(&k_scan_add),
-                         reinterpret_cast<const void*>(&k_gather)};
+                         reinterpret_cast<const void*>(&k_gather), reinterpret_cast<const void*>(&k_intake)};
     // (k_check_windows serves skip-N queries, which the no-alloc call does not take)
     for (const void* f : fns) {
         cudaFuncAttributes a;

@@ -123,6 +123,7 @@ struct rambo {
     uint32_t* mem_bits = nullptr;
     DevStatus* st = nullptr;
     DevStatus* h_st = nullptr;  // pinned
+    DevStatus* h_reset = nullptr;  // pinned: a clean status block, copied in before each query
     uint64_t* h_small = nullptr;  // pinned, 8 words
     // scratch
     DBuf<uint8_t> in_data;
@@ -184,6 +185,7 @@ void free_handle(rambo* h) {
     if (h->mem_bits) cudaFree(h->mem_bits);
     if (h->st) cudaFree(h->st);
     if (h->h_st) cudaFreeHost(h->h_st);
+    if (h->h_reset) cudaFreeHost(h->h_reset);
     if (h->h_small) cudaFreeHost(h->h_small);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
@@ -564,18 +566,31 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
     }
     for (int attempt = 0; attempt < 2; ++attempt) {
         CK(cudaEventRecord(h->ev[0], s));
-        CK(launch_status_reset(h->st, s));
-        CK(launch_validate_batch(b, seq ? k : 1, h->K, h->st, s));
-        h->launches += 2;
+        // a clean status block (error words, work-queue ticket, cursor,
+        // counters) from the pinned template: a copy, not a kernel
+        CK(cudaMemcpyAsync(h->st, h->h_reset, sizeof(DevStatus), cudaMemcpyHostToDevice, s));
+        // intake: validation and 2-bit packing in one launch; the query
+        // kernel looks up the item of an unresolved base, if packing met one
+        const uint8_t* bases = nullptr;
+        uint64_t n_words = 0;
         if (seq) {
-            RK(pack_bases(h, b, d_data, s));
-            h->launches += 2;
+            n_words = b.total / 32 + 2;  // one spare word for windows crossing the last word
+            RK(h->packed.ensure(n_words));
+            b.packed = h->packed.p;
+            b.nmask = nullptr;
             if (b.skipn) {
-                CK(launch_check_windows(b, h->st, s));
-                h->launches += 1;
+                RK(h->nmask.ensure(n_words));
+                b.nmask = h->nmask.p;
             }
+            bases = static_cast<const uint8_t*>(d_data);
         } else {
             b.keys = static_cast<const uint64_t*>(d_data);
+        }
+        CK(launch_intake(b, seq ? k : 1, h->K, bases, h->packed.p, n_words, const_cast<uint32_t*>(b.nmask), h->st, s));
+        h->launches += 1;
+        if (seq && b.skipn) {
+            CK(launch_check_windows(b, h->st, s));
+            h->launches += 1;
         }
         b.perm = nullptr;
         if (h->cfg.cluster) {
@@ -763,6 +778,10 @@ static int create_impl(uint64_t K, uint32_t B_local, uint32_t n_nodes, uint32_t 
     if (cudaMalloc(&h->reg, ((K + 31) / 32) * 4) != cudaSuccess) return fail(RAMBO_ENOMEM);
     if (cudaMalloc(&h->st, sizeof(DevStatus)) != cudaSuccess) return fail(RAMBO_ENOMEM);
     if (cudaMallocHost(&h->h_st, sizeof(DevStatus)) != cudaSuccess) return fail(RAMBO_ENOMEM);
+    if (cudaMallocHost(&h->h_reset, sizeof(DevStatus)) != cudaSuccess) return fail(RAMBO_ENOMEM);
+    *h->h_reset = DevStatus{};
+    h->h_reset->err = NO_ERR;
+    h->h_reset->bad_pos = NO_ERR;
     if (cudaMallocHost(&h->h_small, 8 * sizeof(uint64_t)) != cudaSuccess) return fail(RAMBO_ENOMEM);
     for (auto& ev : h->ev)
         if (cudaEventCreate(&ev) != cudaSuccess) return fail(RAMBO_ECUDA);

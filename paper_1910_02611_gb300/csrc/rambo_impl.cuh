@@ -224,6 +224,31 @@ __device__ __forceinline__ void bv_resolve(BatchView& b) {
     }
 }
 
+// When packing met a byte outside ACGTacgt, the item holding the lowest one
+// gets an EBADSEQ error (binary search for the largest t with offsets[t] <=
+// position).  One thread; b must be resolved (bv_resolve).
+__device__ __forceinline__ void resolve_bad_base(const BatchView& b, DevStatus* st) {
+    const unsigned long long p = *(volatile unsigned long long*)&st->bad_pos;
+    if (p == NO_ERR || b.n == 0) return;
+    const uint64_t abs_p = p + b.off0;
+    uint64_t lo = 0, hi = b.n;  // invariant: answer in [lo, hi)
+    while (hi - lo > 1) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (b.offsets[mid] <= abs_p) lo = mid;
+        else hi = mid;
+    }
+    record_error(st, lo, PRIO_EBADSEQ);
+}
+
+// First thing of every query kernel: the item holding an unresolved base
+// (if packing met one) is recorded by one thread, and every block leaves
+// once any validation error is known.  Returns true when the batch is bad.
+__device__ __forceinline__ bool query_batch_rejected(const BatchView& b, DevStatus* st) {
+    const bool bad_base = b.seq && *(volatile unsigned long long*)&st->bad_pos != NO_ERR;
+    if (bad_base && blockIdx.x == 0 && threadIdx.x == 0) resolve_bad_base(b, st);
+    return bad_base || *(volatile unsigned long long*)&st->err != NO_ERR;
+}
+
 struct QueryOut {
     uint32_t* stage;       // staged IDs (arena)
     uint64_t stage_cap;
@@ -270,7 +295,11 @@ cudaError_t launch_scan_counts(const uint32_t* counts, uint64_t n, uint64_t* off
 uint64_t scan_tmp_words(uint64_t n);
 cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_t n, uint32_t* ids,
                           const DevStatus* st, cudaStream_t s, const uint64_t* n_dev = nullptr,
-                          uint64_t ids_cap = ~0ull);
+                          uint64_t ids_cap = ~0ull, unsigned long long* total_out = nullptr);
+// queries: validation and (bases != NULL) packing in one launch; n_words is
+// the packed capacity (a descriptor batch packs total/32 + 2 words of it)
+cudaError_t launch_intake(const BatchView& b, uint64_t min_len, uint64_t K, const uint8_t* bases, uint64_t* packed,
+                          uint64_t n_words, uint32_t* nmask, DevStatus* st, cudaStream_t s);
 cudaError_t launch_cell_popcount(const IndexView& ix, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_members(const IndexView& ix, uint64_t* mem_off, uint32_t* mem_ids, uint4* mem_phi,
                            uint32_t* fill, cudaStream_t s);

@@ -153,10 +153,9 @@ extern "C" int rambo_query_seq_batch_noalloc(rambo_t* h, const uint8_t* bases, c
     b.set_ids = nullptr;
     b.perm = nullptr;
     NA_CK(launch_status_reset(st, s));  // clears error word, ticket, cursor, counters
-    NA_CK(launch_validate_batch(b, k, ix.K, st, s));
-    NA_CK(launch_pack(bases + ends[0], total, packed, total / 32 + 2, st, s));
     b.packed = packed;
-    NA_CK(launch_resolve_bad_base(b, st, s));
+    // validation and packing in one launch (the query kernel reports an unresolved base)
+    NA_CK(launch_intake(b, k, ix.K, bases + ends[0], packed, total / 32 + 2, nullptr, st, s));
     QueryOut o{stage, NA_STAGE_IDS, qstart, qcount};
     NA_CK(launch_query(ix, hp, b, o, t, use_bitmap, st, s));
     NA_CK(launch_scan_counts(qcount, n, id_offsets, scan_tmp, NA_SCAN_WORDS, s));

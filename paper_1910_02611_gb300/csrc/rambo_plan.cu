@@ -31,11 +31,14 @@ int map_cuda(cudaError_t e) {
         if (e_ != cudaSuccess) return map_cuda(e_); \
     } while (0)
 
-// total number of staged result IDs, read where the descriptor says the batch ends
-__global__ void k_store_total(const uint64_t* __restrict__ id_off, const uint64_t* __restrict__ desc,
-                              DevStatus* st) {
-    st->spare[1] = id_off[desc[0]];
-}
+// What one host-to-device copy node writes before every replay: the batch
+// descriptor {n, total} and a clean status block (error words, work-queue
+// ticket, cursor, counters), so no reset kernel is needed.
+struct PlanHead {
+    uint64_t desc[2];
+    uint64_t pad[2];
+    DevStatus st;
+};
 
 }  // namespace
 
@@ -58,12 +61,14 @@ struct rambo_plan {
     uint32_t* stage = nullptr;
     uint32_t* ids = nullptr;
     uint64_t* id_off = nullptr;
-    DevStatus* st = nullptr;
-    uint64_t* d_desc = nullptr;
+    PlanHead* d_head = nullptr;
+    DevStatus* st = nullptr;   // &d_head->st
+    uint64_t* d_desc = nullptr;  // d_head->desc
     // pinned host
     uint8_t* h_data = nullptr;
     uint64_t* h_off = nullptr;
-    uint64_t* h_desc = nullptr;
+    PlanHead* h_head = nullptr;  // descriptor + clean status template
+    uint64_t* h_desc = nullptr;  // h_head->desc
     DevStatus* h_st = nullptr;
     uint32_t* h_ids = nullptr;
     uint64_t* h_id_off = nullptr;
@@ -96,10 +101,10 @@ void plan_free(rambo_plan* p) {
         if (e) cudaEventDestroy(e);
     if (p->cap) cudaStreamDestroy(p->cap);
     void* dev[] = {p->d_data, p->d_off, p->d_packed, p->d_nmask, p->qcount, p->qstart, p->scan_tmp,
-                   p->stage, p->ids, p->id_off, p->st, p->d_desc};
+                   p->stage, p->ids, p->id_off, p->d_head};
     for (void* d : dev)
         if (d) cudaFree(d);
-    void* host[] = {p->h_data, p->h_off, p->h_desc, p->h_st, p->h_ids, p->h_id_off};
+    void* host[] = {p->h_data, p->h_off, p->h_head, p->h_st, p->h_ids, p->h_id_off};
     for (void* x : host)
         if (x) cudaFreeHost(x);
     delete p;
@@ -134,17 +139,15 @@ int plan_capture(rambo_plan* p, bool timed) {
     cudaStream_t s = p->cap;
     PK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = mark(p, 0, s, timed);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_desc, p->h_desc, 2 * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+    // descriptor and clean status block in one copy node
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_head, p->h_head, sizeof(PlanHead), cudaMemcpyHostToDevice, s);
     int n_launch = 0;
-    if (e == cudaSuccess) e = launch_status_reset(p->st, s), ++n_launch;
-    if (e == cudaSuccess) e = launch_validate_batch(b, p->kind ? p->k : 1, ix.K, p->st, s), ++n_launch;
-    if (e == cudaSuccess && p->kind == 1) {
-        e = launch_pack(p->d_data, p->max_items, p->d_packed, p->max_items / 32 + 2, p->st, s, p->d_desc,
-                        p->d_nmask);
-        if (e == cudaSuccess) e = launch_resolve_bad_base(b, p->st, s);
-        n_launch += 2;
-        if (e == cudaSuccess && p->skipn) e = launch_check_windows(b, p->st, s), ++n_launch;
-    }
+    // intake: validation and (DNA) packing in one kernel
+    if (e == cudaSuccess)
+        e = launch_intake(b, p->kind ? p->k : 1, ix.K, p->kind == 1 ? p->d_data : nullptr, p->d_packed,
+                          p->kind == 1 ? p->max_items / 32 + 2 : 0, p->d_nmask, p->st, s),
+        ++n_launch;
+    if (e == cudaSuccess && p->kind == 1 && p->skipn) e = launch_check_windows(b, p->st, s), ++n_launch;
     QueryOut o{p->stage, p->max_ids, p->qstart, p->qcount};
     if (e == cudaSuccess) e = mark(p, 1, s, timed);
     if (e == cudaSuccess) {
@@ -158,13 +161,10 @@ int plan_capture(rambo_plan* p, bool timed) {
         e = launch_scan_counts(p->qcount, p->max_q, p->id_off, p->scan_tmp, scan_words, s, p->d_desc, &n_scan);
         n_launch += n_scan;
     }
-    if (e == cudaSuccess) e = launch_gather(o, p->id_off, p->max_q, p->ids, p->st, s, p->d_desc, p->max_ids);
+    // the gather also stores the number of result IDs in the status block
+    if (e == cudaSuccess)
+        e = launch_gather(o, p->id_off, p->max_q, p->ids, p->st, s, p->d_desc, p->max_ids, &p->st->spare[1]);
     ++n_launch;
-    if (e == cudaSuccess) {
-        k_store_total<<<1, 1, 0, s>>>(p->id_off, p->d_desc, p->st);
-        e = cudaGetLastError();
-        ++n_launch;
-    }
     if (e == cudaSuccess) e = mark(p, 3, s, timed);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->h_st, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
     cudaGraph_t g = nullptr;
@@ -249,16 +249,23 @@ int rambo_plan_create(rambo_t* h, int kind, uint64_t max_queries, uint64_t max_i
               cudaMalloc(&p->scan_tmp, scan_tmp_words(max_queries) * 8) == cudaSuccess &&
               cudaMalloc(&p->stage, max_ids * 4) == cudaSuccess && cudaMalloc(&p->ids, max_ids * 4) == cudaSuccess &&
               cudaMalloc(&p->id_off, (max_queries + 1) * 8) == cudaSuccess &&
-              cudaMalloc(&p->st, sizeof(DevStatus)) == cudaSuccess && cudaMalloc(&p->d_desc, 16) == cudaSuccess &&
+              cudaMalloc(&p->d_head, sizeof(PlanHead)) == cudaSuccess &&
               cudaMallocHost(&p->h_data, max_items * p->elem + 16) == cudaSuccess &&
               cudaMallocHost(&p->h_off, (max_queries + 1) * 8) == cudaSuccess &&
-              cudaMallocHost(&p->h_desc, 16) == cudaSuccess && cudaMallocHost(&p->h_st, sizeof(DevStatus)) == cudaSuccess &&
+              cudaMallocHost(&p->h_head, sizeof(PlanHead)) == cudaSuccess &&
+              cudaMallocHost(&p->h_st, sizeof(DevStatus)) == cudaSuccess &&
               cudaMallocHost(&p->h_ids, max_ids * 4) == cudaSuccess &&
               cudaMallocHost(&p->h_id_off, (max_queries + 1) * 8) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         return fail(RAMBO_ENOMEM);
     }
+    p->st = &p->d_head->st;
+    p->d_desc = p->d_head->desc;
+    p->h_desc = p->h_head->desc;
+    *p->h_head = PlanHead{};
+    p->h_head->st.err = NO_ERR;
+    p->h_head->st.bad_pos = NO_ERR;
     if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming) != cudaSuccess)
         return fail(RAMBO_ECUDA);

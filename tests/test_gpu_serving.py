@@ -35,7 +35,10 @@ def test_plan_replays_match_query_calls():
     o = Oracle(w.K, w.B, w.R, w.m, w.eta, w.seed)
     o.insert_seq_batch(w.sets.ids, w.sets.data, w.sets.offsets, 31)
     plan = Plan(g, "seq", max_queries=600, max_items=600 * 1000, max_ids=1 << 20)
-    assert plan.launches_per_replay >= 8
+    # intake (validation + packing), the two query-kernel instances, one-block
+    # scan, gather: five kernels per replay (the status reset rides on the
+    # descriptor copy)
+    assert plan.launches_per_replay == 5
     rng = np.random.default_rng(3)
     for n in (1, 37, 600, 250):
         idx = rng.choice(len(w.queries), n, replace=False)
@@ -72,6 +75,21 @@ def test_plan_replays_match_query_calls():
     with pytest.raises(RamboError) as e:
         plan.wait()
     assert e.value.code == EINVAL
+    # an unresolved base: EBADSEQ (found by the query kernel from the packing
+    # kernel's lowest bad position); the next batch starts from a clean status
+    from paper_1910_02611_gb300 import EBADSEQ
+
+    q = w.queries.subset(np.arange(20))
+    bad = q.data.copy()
+    bad[int(q.offsets[13]) + 5] = ord("N")
+    plan.launch_host(bad, q.offsets)
+    with pytest.raises(RamboError) as e:
+        plan.wait()
+    assert e.value.code == EBADSEQ
+    plan.launch_host(q.data, q.offsets)
+    ids, off = plan.wait()
+    rids, roff = o.query_batch("seq", q.data, q.offsets, k=31)
+    assert np.array_equal(off, roff) and np.array_equal(ids, rids)
     plan.close()
     # the plain call still agrees afterwards
     assert_query_equal(g, o, w.queries.subset(np.arange(200)))

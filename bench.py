@@ -79,6 +79,9 @@ def parse_args():
                     help="queries timed through the one-query-per-launch kernel (0 = skip)")
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="pick the kernel configuration with the library's autotuner on batch 0 first")
+    ap.add_argument("--query-config", default=None,
+                    help="set the query kernel configuration, e.g. lanes_per_key=1,words_per_lane=4,warps_per_block=8 "
+                         "(profiling runs: the autotuner's timings under a profiler are not the run's)")
     ap.add_argument("--api", choices=["call", "plan"], default="plan",
                     help="timed step through rambo_query_*_into (call) or a replayed CUDA-graph plan (plan)")
     ap.add_argument("--json-out", default=None)
@@ -369,9 +372,11 @@ def run_ours(args):
         qo = torch.from_numpy(q.offsets.view(np.int64)).to(dev)
         dev_batches.append((qd, qo, keys_in(q, w.k), len(q)))
     tuned = None
-    if args.autotune:
+    if args.autotune and not args.query_config:
         qd0, qo0, _, _ = dev_batches[0]
         tuned = g.autotune(qd0, qo0, kind=batches[0].kind, k=w.k, reps=2)
+    if args.query_config:
+        g.set_config(**{kv.split("=")[0]: int(kv.split("=")[1]) for kv in args.query_config.split(",")})
     # size the caller-owned result buffer: a call with no room reports the IDs needed
     from paper_1910_02611_gb300 import ENOSPC, RamboError
 

@@ -371,22 +371,24 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* w
 }
 
 __global__ void k_scan_tiles(const uint32_t* __restrict__ counts, uint64_t n, uint64_t* __restrict__ out,
-                             uint64_t* __restrict__ tile_sums, const uint64_t* __restrict__ n_dev) {
+                             uint64_t* __restrict__ tile_sums, const uint64_t* __restrict__ n_dev,
+                             const uint64_t* __restrict__ base_dev) {
     __shared__ uint64_t warp_tot[32];
     __shared__ uint64_t tot;
     if (n_dev) n = *n_dev;
-    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+    const uint64_t base = base_dev ? *base_dev : 0;
+    const uint64_t i0 = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
     uint64_t v[SCAN_ITEMS];
     uint64_t sum = 0;
 #pragma unroll
     for (int t = 0; t < SCAN_ITEMS; ++t) {
-        v[t] = (base + t < n) ? counts[base + t] : 0;
+        v[t] = (i0 + t < n) ? counts[i0 + t] : 0;
         sum += v[t];
     }
-    uint64_t pre = block_exclusive_scan(sum, warp_tot, &tot);
+    uint64_t pre = base + block_exclusive_scan(sum, warp_tot, &tot);
 #pragma unroll
     for (int t = 0; t < SCAN_ITEMS; ++t) {
-        if (base + t < n) out[base + t] = pre;
+        if (i0 + t < n) out[i0 + t] = pre;
         pre += v[t];
     }
     if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
@@ -413,7 +415,7 @@ __global__ void k_scan_sums(uint64_t* tile_sums, uint64_t n_tiles, const uint64_
 }
 
 __global__ void k_scan_add(uint64_t* __restrict__ out, uint64_t n, const uint64_t* __restrict__ tile_sums,
-                           uint64_t n_tiles, const uint64_t* __restrict__ n_dev) {
+                           uint64_t n_tiles, const uint64_t* __restrict__ n_dev, const uint64_t* __restrict__ base_dev) {
     if (n_dev) {
         n = *n_dev;
         n_tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
@@ -424,7 +426,7 @@ __global__ void k_scan_add(uint64_t* __restrict__ out, uint64_t n, const uint64_
     uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
     for (int t = threadIdx.x; t < SCAN_TILE; t += blockDim.x)
         if (base + t < n) out[base + t] += add;
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_sums[n_tiles];
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_sums[n_tiles] + (base_dev ? *base_dev : 0);
 }
 
 // Small inputs: one block walks the tiles in order with a running carry (one
@@ -433,11 +435,11 @@ __global__ void k_scan_add(uint64_t* __restrict__ out, uint64_t n, const uint64_
 constexpr uint64_t SCAN_ONE_BLOCK_MAX = 8 * SCAN_TILE;
 
 __global__ void k_scan_one_block(const uint32_t* __restrict__ counts, uint64_t n, uint64_t* __restrict__ out,
-                                 const uint64_t* __restrict__ n_dev) {
+                                 const uint64_t* __restrict__ n_dev, const uint64_t* __restrict__ base_dev) {
     __shared__ uint64_t warp_tot[32];
     __shared__ uint64_t tot;
     if (n_dev) n = *n_dev;
-    uint64_t carry = 0;
+    uint64_t carry = base_dev ? *base_dev : 0;
     for (uint64_t t0 = 0; t0 < n; t0 += SCAN_TILE) {
         const uint64_t base = t0 + (uint64_t)threadIdx.x * SCAN_ITEMS;
         uint64_t v[SCAN_ITEMS];
@@ -459,19 +461,21 @@ __global__ void k_scan_one_block(const uint32_t* __restrict__ counts, uint64_t n
 }
 
 cudaError_t launch_scan_counts(const uint32_t* counts, uint64_t n, uint64_t* offsets, uint64_t* tmp,
-                               uint64_t tmp_words, cudaStream_t s, const uint64_t* n_dev, int* n_launched) {
-    // with n_dev, n is the capacity the grids are sized for and the true count is read on the device
+                               uint64_t tmp_words, cudaStream_t s, const uint64_t* n_dev, int* n_launched,
+                               const uint64_t* base_dev) {
+    // with n_dev, n is the capacity the grids are sized for and the true count is read on the device;
+    // with base_dev, every offset is shifted by the value it points to
     if (n <= SCAN_ONE_BLOCK_MAX) {
-        k_scan_one_block<<<1, SCAN_THREADS, 0, s>>>(counts, n, offsets, n_dev);
+        k_scan_one_block<<<1, SCAN_THREADS, 0, s>>>(counts, n, offsets, n_dev, base_dev);
         if (n_launched) *n_launched = 1;
         return cudaGetLastError();
     }
     uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles == 0) tiles = 1;
     if (tmp_words < tiles + 1) return cudaErrorInvalidValue;
-    k_scan_tiles<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(counts, n, offsets, tmp, n_dev);
+    k_scan_tiles<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(counts, n, offsets, tmp, n_dev, base_dev);
     k_scan_sums<<<1, SCAN_THREADS, 0, s>>>(tmp, tiles, n_dev);
-    k_scan_add<<<(unsigned)tiles, 256, 0, s>>>(offsets, n, tmp, tiles, n_dev);
+    k_scan_add<<<(unsigned)tiles, 256, 0, s>>>(offsets, n, tmp, tiles, n_dev, base_dev);
     if (n_launched) *n_launched = 3;
     return cudaGetLastError();
 }

@@ -132,6 +132,12 @@ struct rambo {
     DBuf<uint64_t> ckeys, coff;
     HBuf<uint32_t> h_ids;
     HBuf<uint64_t> h_id_off;
+    // host-output pipeline: copy stream, per-chunk events, chunk bases and totals, status copies
+    cudaStream_t cs = nullptr;
+    cudaEvent_t pev[9] = {};
+    DBuf<uint64_t> pslot;
+    HBuf<uint64_t> ptot;
+    HBuf<DevStatus> pst;
     rambo_query_config_t cfg{};
     uint64_t build_tile_bytes = BUILD_TILE_BYTES;
     int build_mode = 0;
@@ -207,6 +213,12 @@ void free_handle(rambo* h) {
     h->coff.release();
     h->h_ids.release();
     h->h_id_off.release();
+    h->pslot.release();
+    h->ptot.release();
+    h->pst.release();
+    for (auto& e : h->pev)
+        if (e) cudaEventDestroy(e);
+    if (h->cs) cudaStreamDestroy(h->cs);
     cudaSetDevice(cur);
     delete h;
 }
@@ -509,6 +521,151 @@ int resolve_tuning(rambo* h, uint64_t n, int& use_bitmap, QueryTuning& t) {
     return RAMBO_OK;
 }
 
+// A clean status block (error words, work-queue ticket, cursor, counters)
+// from the pinned template -- a copy, not a kernel -- then the intake:
+// validation and 2-bit packing in one launch (the query kernel looks up the
+// item of an unresolved base, if packing met one).  Sets the batch's packed,
+// mask or key pointers.
+int enqueue_intake(rambo* h, BatchView& b, const void* d_data, int seq, uint32_t k, cudaStream_t s) {
+    CK(cudaMemcpyAsync(h->st, h->h_reset, sizeof(DevStatus), cudaMemcpyHostToDevice, s));
+    const uint8_t* bases = nullptr;
+    uint64_t n_words = 0;
+    b.nmask = nullptr;
+    if (seq) {
+        n_words = b.total / 32 + 2;  // one spare word for windows crossing the last word
+        RK(h->packed.ensure(n_words));
+        b.packed = h->packed.p;
+        if (b.skipn) {
+            RK(h->nmask.ensure(n_words));
+            b.nmask = h->nmask.p;
+        }
+        bases = static_cast<const uint8_t*>(d_data);
+    } else {
+        b.keys = static_cast<const uint64_t*>(d_data);
+    }
+    CK(launch_intake(b, seq ? k : 1, h->K, bases, h->packed.p, n_words, const_cast<uint32_t*>(b.nmask), h->st, s));
+    h->launches += 1;
+    if (seq && b.skipn) {
+        CK(launch_check_windows(b, h->st, s));
+        h->launches += 1;
+    }
+    return RAMBO_OK;
+}
+
+// Host-output pipeline for large batches answered into the handle's pinned
+// arena: the batch is cut into chunks of queries that run back to back on
+// the call's stream (query kernel, count scan continuing from the previous
+// chunk's total, gather), and each chunk's IDs and offsets go to pinned host
+// memory on a second stream while the later chunks compute, so the
+// device-to-host copy of the answers overlaps the query kernel instead of
+// following it.  The device and pinned ID buffers and the staging arena
+// must already be large enough (they are after a first call of that size);
+// when the answers do not fit, it returns PIPE_FALLBACK with the staging
+// arena grown, and the caller answers the batch the unpipelined way.
+constexpr int PIPE_MAX_CHUNKS = 8;
+constexpr uint64_t PIPE_MIN_QUERIES = 1u << 16;
+constexpr int PIPE_FALLBACK = 1;
+
+int run_query_pipelined(rambo* h, BatchView b, const void* d_data, int seq, uint32_t k, uint64_t n, cudaStream_t s,
+                        QueryDest& d) {
+    if (!h->ids.p || !h->h_ids.p || !h->stage.p) return PIPE_FALLBACK;
+    if (!h->cs) CK(cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking));
+    for (auto& e : h->pev)
+        if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    RK(h->pslot.ensure(PIPE_MAX_CHUNKS));
+    RK(h->ptot.ensure(PIPE_MAX_CHUNKS));
+    RK(h->pst.ensure(2));
+    RK(h->id_off.ensure(n + 1));
+    RK(h->h_id_off.ensure(n + 1));
+    uint64_t* d_off = h->id_off.p;
+    const uint64_t cap = h->ids.cap < h->h_ids.cap ? h->ids.cap : h->h_ids.cap;
+    const int C = n >= (1u << 19) ? PIPE_MAX_CHUNKS : PIPE_MAX_CHUNKS / 2;
+    uint64_t q_lo[PIPE_MAX_CHUNKS + 1];
+    for (int c = 0; c <= C; ++c) q_lo[c] = n * (uint64_t)c / (uint64_t)C;
+
+    CK(cudaEventRecord(h->ev[0], s));
+    RK(enqueue_intake(h, b, d_data, seq, k, s));
+    // the item holding an unresolved base, looked up over the whole batch
+    // (the chunks' query kernels see only their slice)
+    if (seq) {
+        CK(launch_resolve_bad_base(b, h->st, s));
+        h->launches += 1;
+    }
+    CK(cudaMemcpyAsync(h->pst.p, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(h->pev[PIPE_MAX_CHUNKS], s));
+    CK(cudaMemsetAsync(h->pslot.p, 0, sizeof(uint64_t), s));
+    CK(cudaEventRecord(h->ev[1], s));
+    for (int c = 0; c < C; ++c) {
+        const uint64_t nc = q_lo[c + 1] - q_lo[c];
+        BatchView bc = b;
+        bc.offsets = b.offsets + q_lo[c];
+        bc.n = nc;
+        bc.perm = nullptr;
+        bc.no_resolve = 1;
+        int ub = 0;
+        QueryTuning t{};
+        RK(resolve_tuning(h, nc, ub, t));
+        QueryOut oc{h->stage.p, h->stage.cap, h->qstart.p + q_lo[c], h->qcount.p + q_lo[c]};
+        if (c) CK(cudaMemsetAsync(&h->st->ticket, 0, sizeof(unsigned long long), s));  // a fresh work queue
+        int nl = 0, n_scan = 0;
+        CK(launch_query(h->view(), h->hp, bc, oc, t, ub, h->st, s, &nl));
+        // chunk c's offsets continue from the total written by chunk c - 1's scan
+        if (c) CK(cudaMemcpyAsync(h->pslot.p + c, d_off + q_lo[c], sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        CK(launch_scan_counts(oc.qcount, nc, d_off + q_lo[c], h->scan_tmp.p, h->scan_tmp.cap, s, nullptr, &n_scan,
+                              h->pslot.p + c));
+        CK(launch_gather(oc, d_off + q_lo[c], nc, h->ids.p, h->st, s, nullptr, cap));
+        CK(cudaMemcpyAsync(h->ptot.p + c, d_off + q_lo[c + 1], sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(h->pev[c], s));
+        h->launches += (uint64_t)(nl + n_scan + 1);
+    }
+    CK(cudaEventRecord(h->ev[2], s));
+    CK(cudaMemcpyAsync(h->pst.p + 1, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(h->ev[3], s));
+    // copies of each finished chunk, on the second stream
+    CK(cudaEventSynchronize(h->pev[PIPE_MAX_CHUNKS]));
+    const DevStatus in = h->pst.p[0];
+    bool fits = in.err == NO_ERR && in.bad_pos == NO_ERR;
+    uint64_t prev = 0;
+    for (int c = 0; c < C && fits; ++c) {
+        CK(cudaEventSynchronize(h->pev[c]));
+        const uint64_t tot = h->ptot.p[c];
+        if (tot < prev || tot > cap) {
+            fits = false;
+            break;
+        }
+        CK(cudaStreamWaitEvent(h->cs, h->pev[c], 0));
+        if (tot > prev)
+            CK(cudaMemcpyAsync(h->h_ids.p + prev, h->ids.p + prev, (tot - prev) * sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, h->cs));
+        const uint64_t o0 = c ? q_lo[c] + 1 : 0;
+        CK(cudaMemcpyAsync(h->h_id_off.p + o0, d_off + o0, (q_lo[c + 1] + 1 - o0) * sizeof(uint64_t),
+                           cudaMemcpyDeviceToHost, h->cs));
+        prev = tot;
+    }
+    CK(cudaStreamSynchronize(s));
+    CK(cudaStreamSynchronize(h->cs));
+    const DevStatus fin = h->pst.p[1];
+    RK(decode_err(h, fin.err));
+    if (!fits || fin.cursor > h->stage.cap) {
+        RK(h->stage.ensure(fin.cursor));
+        return PIPE_FALLBACK;
+    }
+    h->last.n_queries = n;
+    h->last.keys_submitted = seq ? (b.total - n * (uint64_t)(k - 1)) : b.total;
+    h->last.keys_probed = fin.keys_probed;
+    h->last.rows_read = fin.rows_read;
+    h->last.n_results = prev;
+    for (int i = 0; i < 4; ++i) h->last.stage_queries[i] = fin.stage_count[i];
+    // (the chunks' query kernels, interleaved with their scans and gathers)
+    CK(cudaEventElapsedTime(&h->last.query_kernel_ms, h->ev[1], h->ev[2]));
+    CK(cudaEventElapsedTime(&h->last.device_ms, h->ev[0], h->ev[3]));
+    h->last.kernel_launches = h->launches;
+    if (d.needed) *d.needed = prev;
+    *d.out_ids = h->h_ids.p;
+    *d.out_off = h->h_id_off.p;
+    return RAMBO_OK;
+}
+
 int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint64_t n, uint32_t k,
               int on_device, cudaStream_t s, QueryDest& d) {
     if (!h || !offsets || (!data && n)) return RAMBO_EINVAL;
@@ -556,6 +713,11 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
     RK(h->qstart.ensure(n));
     RK(h->scan_tmp.ensure(scan_tmp_words(n)));
     if (h->stage.cap < (1u << 20)) RK(h->stage.ensure(1u << 20));
+    if (!on_device && d.arena && n >= PIPE_MIN_QUERIES && !h->cfg.cluster && !h->cfg.l2_fetch_bytes) {
+        const int rc = run_query_pipelined(h, b, d_data, seq, k, n, s, d);
+        if (rc != PIPE_FALLBACK) return rc;
+        h->launches = 0;
+    }
     // device-side destination of the CSR offsets
     uint64_t* d_off;
     if (!d.arena && on_device) {
@@ -566,32 +728,7 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
     }
     for (int attempt = 0; attempt < 2; ++attempt) {
         CK(cudaEventRecord(h->ev[0], s));
-        // a clean status block (error words, work-queue ticket, cursor,
-        // counters) from the pinned template: a copy, not a kernel
-        CK(cudaMemcpyAsync(h->st, h->h_reset, sizeof(DevStatus), cudaMemcpyHostToDevice, s));
-        // intake: validation and 2-bit packing in one launch; the query
-        // kernel looks up the item of an unresolved base, if packing met one
-        const uint8_t* bases = nullptr;
-        uint64_t n_words = 0;
-        if (seq) {
-            n_words = b.total / 32 + 2;  // one spare word for windows crossing the last word
-            RK(h->packed.ensure(n_words));
-            b.packed = h->packed.p;
-            b.nmask = nullptr;
-            if (b.skipn) {
-                RK(h->nmask.ensure(n_words));
-                b.nmask = h->nmask.p;
-            }
-            bases = static_cast<const uint8_t*>(d_data);
-        } else {
-            b.keys = static_cast<const uint64_t*>(d_data);
-        }
-        CK(launch_intake(b, seq ? k : 1, h->K, bases, h->packed.p, n_words, const_cast<uint32_t*>(b.nmask), h->st, s));
-        h->launches += 1;
-        if (seq && b.skipn) {
-            CK(launch_check_windows(b, h->st, s));
-            h->launches += 1;
-        }
+        RK(enqueue_intake(h, b, d_data, seq, k, s));
         b.perm = nullptr;
         if (h->cfg.cluster) {
             RK(h->ckeys.ensure(n));

@@ -210,6 +210,8 @@ struct BatchView {
     const uint32_t* nmask;         // skip-N: one bit per packed base, set = unresolved
     const uint64_t* set_ids;       // insert batches only
     const uint32_t* perm;          // queries only: processing order (NULL = 0..n-1)
+    int no_resolve;                // 1: the query kernel leaves the unresolved-base lookup to a
+                                   // separate launch over the whole batch (this view is a slice)
     const uint64_t* desc;          // device descriptor {n, total} (offsets[0] = 0) read at
                                    // kernel start instead of n/total/off0; lets one captured
                                    // CUDA graph serve batches of any size up to its capacity
@@ -245,7 +247,7 @@ __device__ __forceinline__ void resolve_bad_base(const BatchView& b, DevStatus* 
 // once any validation error is known.  Returns true when the batch is bad.
 __device__ __forceinline__ bool query_batch_rejected(const BatchView& b, DevStatus* st) {
     const bool bad_base = b.seq && *(volatile unsigned long long*)&st->bad_pos != NO_ERR;
-    if (bad_base && blockIdx.x == 0 && threadIdx.x == 0) resolve_bad_base(b, st);
+    if (bad_base && !b.no_resolve && blockIdx.x == 0 && threadIdx.x == 0) resolve_bad_base(b, st);
     return bad_base || *(volatile unsigned long long*)&st->err != NO_ERR;
 }
 
@@ -291,7 +293,7 @@ cudaError_t launch_resolve_bad_base(const BatchView& b, DevStatus* st, cudaStrea
 cudaError_t launch_register(const BatchView& b, uint32_t* reg, DevStatus* st, cudaStream_t s);
 cudaError_t launch_scan_counts(const uint32_t* counts, uint64_t n, uint64_t* offsets,
                                uint64_t* tmp, uint64_t tmp_words, cudaStream_t s, const uint64_t* n_dev = nullptr,
-                               int* n_launched = nullptr);
+                               int* n_launched = nullptr, const uint64_t* base_dev = nullptr);
 uint64_t scan_tmp_words(uint64_t n);
 cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_t n, uint32_t* ids,
                           const DevStatus* st, cudaStream_t s, const uint64_t* n_dev = nullptr,

@@ -397,6 +397,53 @@ def test_folding_over_equals_an_index_built_with_half_the_cells(mods, B, folds):
     assert np.array_equal(direct.export_index(), g.export_index())
 
 
+def test_large_host_batches_take_the_copy_pipeline(mods):
+    # batches of 65536+ queries answered into host memory run in chunks whose
+    # answers are copied while later chunks compute; the first call of a size
+    # sizes the buffers the unpipelined way, the next ones pipeline.  Answers,
+    # and the item an error is reported at, must not depend on the path.
+    from paper_1910_02611_gb300 import EBADSEQ, EINVAL, RamboError
+
+    Rambo, Oracle = mods
+    w = synth.make("genome", 0.02, m=1 << 18)
+    g, o = build_pair(w, Rambo, Oracle)
+    rng = np.random.default_rng(64)
+    for n in (70_000, 70_000, 600_000):
+        q = synth.substring_queries(rng, w.sets, rng.integers(31, 60, n))
+        ids, off = g.query(q.data, q.offsets, kind="seq")
+        if n == 600_000:  # the oracle checks a sample; the rest against the device-output path
+            import torch
+
+            dids, doff = g.query(torch.from_numpy(q.data).cuda(), torch.from_numpy(q.offsets.view(np.int64)).cuda(),
+                                 kind="seq")
+            assert np.array_equal(off, doff.cpu().numpy().view(np.uint64))
+            assert np.array_equal(ids, dids.cpu().numpy().view(np.uint32))
+            sel = np.sort(rng.choice(n, 3000, replace=False))
+            sub = q.subset(sel)
+            rids, roff = o.query_batch("seq", sub.data, sub.offsets, k=31)
+            for j, t in enumerate(sel):
+                assert np.array_equal(ids[int(off[t]):int(off[t + 1])], rids[int(roff[j]):int(roff[j + 1])])
+        else:
+            rids, roff = o.query_batch("seq", q.data, q.offsets, k=31)
+            assert np.array_equal(off, roff) and np.array_equal(ids, rids)
+    # errors in a late chunk: the item index is the batch's, not the chunk's
+    q = synth.substring_queries(rng, w.sets, rng.integers(31, 60, 70_000))
+    bad = q.data.copy()
+    bad[int(q.offsets[65_000]) + 3] = ord("N")
+    with pytest.raises(RamboError) as e:
+        g.query(bad, q.offsets, kind="seq")
+    assert e.value.code == EBADSEQ and e.value.item == 65_000
+    off = q.offsets.copy()
+    off[50_001] = off[50_000] - 1  # query 50000 ends before it starts
+    with pytest.raises(RamboError) as e:
+        g.query(q.data, off, kind="seq")
+    assert e.value.code == EINVAL and e.value.item == 50_000
+    ids, off2 = g.query(q.data, q.offsets, kind="seq")  # and the handle still answers
+    rids, roff = o.query_batch("seq", q.data, q.offsets, k=31)
+    assert np.array_equal(off2, roff) and np.array_equal(ids, rids)
+    g.close()
+
+
 def test_fold_is_refused_while_a_plan_holds_the_index(mods):
     # A plan's captured graph reads the handle's rows and set-stage tables;
     # folding replaces them, so it must be refused (RAMBO_ESTATE, index

@@ -468,7 +468,11 @@ int rambo_set_query_config(rambo_t *h, const rambo_query_config_t *cfg);
  * call from the input and index sizes, 1 = always run the build window by
  * window (each window of tile_bytes of the index stays resident in L2 while
  * the input streams past), 2 = one pass with every update going to device
- * memory.  tile_bytes = 0 keeps the current window size (128 MiB initially). */
+ * memory, 3 = hash every key once per input chunk, file its updates by
+ * 48 MiB window of the index and apply them window by window (needs
+ * R * eta <= 32; a chunk whose updates are far from uniform over the rows
+ * falls back to mode 1).  Mode 0 takes 3 for large builds.  tile_bytes = 0
+ * keeps the current window size of mode 1 (128 MiB initially). */
 int rambo_set_build_tiling(rambo_t *h, uint64_t tile_bytes, int mode);
 
 /* Lists the query-kernel configurations valid for this handle (at most cap),

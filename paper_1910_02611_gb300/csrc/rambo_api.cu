@@ -130,6 +130,8 @@ struct rambo {
     DBuf<uint64_t> in_off, in_ids, packed, qstart, scan_tmp, id_off;
     DBuf<uint32_t> stage, qcount, ids, fill, perm, chist, nmask;
     DBuf<uint64_t> ckeys, coff;
+    DBuf<uint32_t> brec;               // bucketed build: update records
+    DBuf<unsigned long long> bfill;    // bucketed build: per-window fill counters + overflow flag
     HBuf<uint32_t> h_ids;
     HBuf<uint64_t> h_id_off;
     // host-output pipeline: copy stream, per-chunk events, chunk bases and totals, status copies
@@ -210,6 +212,8 @@ void free_handle(rambo* h) {
     h->chist.release();
     h->nmask.release();
     h->ckeys.release();
+    h->brec.release();
+    h->bfill.release();
     h->coff.release();
     h->h_ids.release();
     h->h_id_off.release();
@@ -374,6 +378,62 @@ int pack_bases(rambo* h, BatchView& b, const void* d_bases, cudaStream_t s) {
     return RAMBO_OK;
 }
 
+// Bucketed build of a validated, packed, registered batch: the input is cut
+// into chunks whose update records (R*eta per key, 4 bytes each) fit a
+// budget of device memory; per chunk one scatter launch files every record
+// into its window's bucket (a chunk whose records overflow a bucket is filed
+// again into larger ones) and one apply launch per window ORs the bucket
+// into the rows.  Returns BUCKET_FALLBACK when memory or the bucket count
+// does not allow it; the caller then builds window by window.
+constexpr int BUCKET_FALLBACK = 1;
+constexpr uint64_t BUCKET_WIN_BYTES = 48ull << 20;  // a window: well inside one die's share of L2
+
+int insert_bucketed(rambo* h, const BatchView& b, cudaStream_t s) {
+    const uint64_t rows_total = (uint64_t)h->R * h->m;
+    uint64_t rows_per_win = BUCKET_WIN_BYTES / ((uint64_t)h->S * 4);
+    if (rows_per_win < 1) rows_per_win = 1;
+    if (rows_per_win > rows_total) rows_per_win = rows_total;
+    const uint64_t n_win64 = (rows_total + rows_per_win - 1) / rows_per_win;
+    if (n_win64 > 4096) return BUCKET_FALLBACK;
+    const uint32_t n_win = (uint32_t)n_win64;
+    const uint64_t per_key = (uint64_t)h->R * h->eta;
+    // records per chunk: up to 3e9 (12 GB), or a third of the free memory
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    uint64_t budget = (uint64_t)free_b / 3 / 4;
+    if (budget > 3000000000ull) budget = 3000000000ull;
+    if (budget < (1ull << 24)) return BUCKET_FALLBACK;
+    uint64_t chunk_keys = (uint64_t)((double)budget / 1.6 / (double)per_key);
+    if (chunk_keys > b.total) chunk_keys = b.total;
+    if (chunk_keys < 1) chunk_keys = 1;
+    // a window's share of a chunk's records (each distinct key's positions are
+    // uniform over the rows; keys repeated across sets make the shares lumpier)
+    const double expect = (double)chunk_keys * (double)per_key * (double)rows_per_win / (double)rows_total;
+    uint64_t cap = (uint64_t)(expect * 1.5) + 65536;
+    RK(h->bfill.ensure(n_win + 1));  // [n_win] fill counters, then the overflow flag
+    const IndexView ix = h->view();
+    for (uint64_t p_lo = 0; p_lo < b.total; p_lo += chunk_keys) {
+        const uint64_t p_hi = p_lo + chunk_keys < b.total ? p_lo + chunk_keys : b.total;
+        for (int attempt = 0;; ++attempt) {
+            if (h->brec.ensure(n_win * cap) != RAMBO_OK) return BUCKET_FALLBACK;
+            CK(cudaMemsetAsync(h->bfill.p, 0, (n_win + 1) * sizeof(unsigned long long), s));
+            CK(launch_bucket_scatter(ix, h->hp, b, p_lo, p_hi, rows_per_win, n_win, cap, h->brec.p, h->bfill.p,
+                                     h->bfill.p + n_win, h->st, h->num_sms, s));
+            CK(cudaMemcpyAsync(h->h_small, h->bfill.p + n_win, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               s));
+            CK(cudaStreamSynchronize(s));
+            if (!h->h_small[0]) break;
+            // a bucket overflowed: file the chunk again into larger buckets
+            if (attempt == 3) return BUCKET_FALLBACK;
+            cap *= 2;
+        }
+        for (uint32_t w = 0; w < n_win; ++w)
+            CK(launch_bucket_apply(h->rows, (uint64_t)w * rows_per_win * h->S, h->brec.p, h->bfill.p, w, cap,
+                                   h->num_sms, s));
+    }
+    return RAMBO_OK;
+}
+
 int run_insert(rambo* h, int seq, const uint64_t* set_ids, const void* data, const uint64_t* offsets,
                uint64_t n, uint32_t k, int on_device, cudaStream_t s) {
     if (!h || !offsets || !set_ids || (!data && n)) return RAMBO_EINVAL;
@@ -408,7 +468,20 @@ int run_insert(rambo* h, int seq, const uint64_t* set_ids, const void* data, con
     const double tiled_ps = (double)n_keys * ((double)n_tiles * 5.0 + atomics * 5.0) + (double)n_tiles * 4e6;
     const double untiled_ps = (double)n_keys * atomics * 40.0 + 4e6;
     const bool use_tiles = h->build_mode == 1 || (h->build_mode == 0 && n_tiles > 1 && tiled_ps < untiled_ps);
-    if (use_tiles) {
+    // large builds: every key hashed once per input chunk, its updates filed
+    // by window and applied window by window (k_build_bucket.cu)
+    const bool bucket_ok = (uint64_t)h->R * h->eta <= 32;
+    const bool use_buckets =
+        bucket_ok && (h->build_mode == 3 ||
+                      (h->build_mode == 0 && n_tiles > 1 && (double)n_keys * atomics >= (double)(1ull << 26)));
+    if (use_buckets) {
+        const int brc = insert_bucketed(h, b, s);
+        if (brc != RAMBO_OK && brc != BUCKET_FALLBACK) return brc;
+        if (brc == RAMBO_OK) goto built;
+        // a bucket overflowed (keys far from uniform over the rows): build the
+        // same bits window by window; the updates already applied are idempotent
+    }
+    if (use_tiles || use_buckets) {
         for (uint64_t lo = 0; lo < rows_total; lo += tile_rows) {
             uint64_t hi = lo + tile_rows < rows_total ? lo + tile_rows : rows_total;
             CK(launch_insert(h->view(), h->hp, b, lo, hi, h->st, h->num_sms, s));
@@ -416,6 +489,7 @@ int run_insert(rambo* h, int seq, const uint64_t* set_ids, const void* data, con
     } else {
         CK(launch_insert(h->view(), h->hp, b, 0, rows_total, h->st, h->num_sms, s));
     }
+built:
     CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const int rc = decode_err(h, h->h_st->err);
@@ -1363,7 +1437,7 @@ int rambo_fold(rambo_t* h, void* stream) {
 }
 
 int rambo_set_build_tiling(rambo_t* h, uint64_t tile_bytes, int mode) {
-    if (!h || mode < 0 || mode > 2) return RAMBO_EINVAL;
+    if (!h || mode < 0 || mode > 3) return RAMBO_EINVAL;
     if (tile_bytes) {
         if (tile_bytes < (uint64_t)h->S * 4) return RAMBO_EINVAL;
         h->build_tile_bytes = tile_bytes;

@@ -452,7 +452,8 @@ class Rambo:
 
     def set_build_tiling(self, tile_bytes: int = 0, mode: int = 0) -> None:
         """mode 0 auto, 1 always window by window (L2-resident slices of
-        tile_bytes), 2 single pass."""
+        tile_bytes), 2 single pass, 3 keys hashed once per input chunk with
+        their updates filed and applied by window."""
         self._check(load_library().rambo_set_build_tiling(self._h, tile_bytes, mode), "set_build_tiling")
 
     def list_configs(self) -> list[dict]:

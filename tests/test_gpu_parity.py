@@ -319,6 +319,56 @@ def test_tiled_construction_matches_oracle(mods, tile_bytes):
         assert_index_equal(g2, o2)
 
 
+@pytest.mark.parametrize("name,k", [("genome_small", 31), ("genome_small", 31 | 0x100), ("document_small", 31),
+                                    ("uneven_small", 31 | 0x200)])
+def test_bucketed_construction_matches_oracle(mods, name, k):
+    # construction mode 3: every key hashed once per input chunk, its updates
+    # filed by window of the index and applied window by window -- the same
+    # bits as the oracle's Algorithm 1 and as the window-by-window build
+    Rambo, Oracle = mods
+    w = WORKLOADS[name]()
+    kind = w.sets.kind
+    g = Rambo(w.K, w.B, w.R, 1 << 22, w.eta, w.seed)  # an index of several 48 MiB windows
+    g.set_build_tiling(mode=3)
+    g.insert(w.sets.ids, w.sets.data, w.sets.offsets, kind=kind, k=k)
+    o = Oracle(w.K, w.B, w.R, 1 << 22, w.eta, w.seed)
+    if kind == "keys":
+        o.insert_keys_batch(w.sets.ids, w.sets.data, w.sets.offsets, nthreads=8)
+    else:
+        o.insert_seq_batch(w.sets.ids, w.sets.data, w.sets.offsets, k, nthreads=8)
+    assert np.array_equal(g.cell_popcount(), o.cell_popcount())
+    gt = Rambo(w.K, w.B, w.R, 1 << 22, w.eta, w.seed)
+    gt.set_build_tiling(1 << 24, mode=1)
+    gt.insert(w.sets.ids, w.sets.data, w.sets.offsets, kind=kind, k=k)
+    assert np.array_equal(gt.export_index(), g.export_index())
+    rows = g.export_index()
+    for r in range(w.R):  # sampled rows against the oracle's row view
+        for p in np.random.default_rng(r).integers(0, 1 << 22, 300):
+            want = o.get_row(r, int(p)).view(np.uint32)[: g.row_words]
+            assert np.array_equal(rows[r, int(p), : g.row_words], want)
+    gt.close()
+    g.close()
+
+
+def test_bucketed_construction_recovers_from_skewed_keys(mods):
+    # one key repeated 300000 times lands every update of the batch in the few
+    # rows it hashes to: a bucket overflows and the chunk is filed again
+    Rambo, Oracle = mods
+    K, B, R, m, eta = 40, 64, 6, 1 << 22, 2
+    keys = np.full(300_000, 0x1234567, np.uint64)
+    keys[::1000] = np.arange(300, dtype=np.uint64) * 7919  # and a few others
+    off = np.array([0, 150_000, 300_000], np.uint64)
+    ids = np.array([3, 17], np.uint64)
+    g = Rambo(K, B, R, m, eta, 42)
+    g.set_build_tiling(mode=3)
+    g.insert(ids, keys, off, kind="keys")
+    o = Oracle(K, B, R, m, eta, 42)
+    o.insert_keys_batch(ids, keys, off)
+    assert np.array_equal(g.cell_popcount(), o.cell_popcount())
+    assert_index_equal(g, o)
+    g.close()
+
+
 def test_pack_aligned_and_unaligned_inputs(mods):
     # sequences starting at every alignment of the base array (16-byte vector
     # path and byte path of the packer), with and without a bad byte

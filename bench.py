@@ -440,6 +440,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     step_ms, keys, probed, rows_read, qk_ms, launches, n_ids = [], 0, 0, 0, [], 0, 0
+    stages = [0, 0, 0, 0]  # surviving queries by set stage: staged dense, dense, sparse, union
     for i in range(args.steps):
         flush.zero_()
         e0.record(stream)
@@ -457,6 +458,7 @@ def run_ours(args):
         qk_ms.append(st["query_kernel_ms"])
         launches += st["kernel_launches"]
         n_ids += st["n_results"]
+        stages = [a + b for a, b in zip(stages, st["stage_queries"])]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -618,6 +620,8 @@ def run_ours(args):
             "rows_per_submitted_key": rows_read / max(keys, 1),
             "query_kernel_ms_per_step": qk_total / args.steps,
             "kernel_timing": qk_timing,
+            "set_stage_queries_per_step": {name: v / args.steps for name, v in
+                                           zip(("staged_dense", "dense", "sparse", "union"), stages)},
         },
         "random_row_roofline": rr,
         "construction": {"keys": build_keys, "ms": build_ms, "keys_per_s": build_keys / (build_ms / 1000)},

@@ -458,6 +458,13 @@ typedef struct rambo_query_config {
                                * small batch spreads each query over a block).
                                * Needs a set stage with a shared-memory bitmap
                                * (K <= 131072); otherwise one warp per query. */
+    uint32_t host_chunks;     /* answers returned in host memory (the arena
+                               * query calls with on_device = 0, batches of
+                               * 65536 queries or more): the batch runs as this
+                               * many chunks whose answers are copied while the
+                               * next ones compute; 0 = automatic (4, or 8 from
+                               * 2^19 queries), 1 = one piece, copied at the end;
+                               * at most 8 */
 } rambo_query_config_t;
 
 int rambo_get_query_config(const rambo_t *h, rambo_query_config_t *out);

@@ -415,7 +415,8 @@ __global__ void k_scan_sums(uint64_t* tile_sums, uint64_t n_tiles, const uint64_
 }
 
 __global__ void k_scan_add(uint64_t* __restrict__ out, uint64_t n, const uint64_t* __restrict__ tile_sums,
-                           uint64_t n_tiles, const uint64_t* __restrict__ n_dev, const uint64_t* __restrict__ base_dev) {
+                           uint64_t n_tiles, const uint64_t* __restrict__ n_dev, const uint64_t* __restrict__ base_dev,
+                           unsigned long long* __restrict__ total_out) {
     if (n_dev) {
         n = *n_dev;
         n_tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
@@ -426,7 +427,10 @@ __global__ void k_scan_add(uint64_t* __restrict__ out, uint64_t n, const uint64_
     uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
     for (int t = threadIdx.x; t < SCAN_TILE; t += blockDim.x)
         if (base + t < n) out[base + t] += add;
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_sums[n_tiles] + (base_dev ? *base_dev : 0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out[n] = tile_sums[n_tiles] + (base_dev ? *base_dev : 0);
+        if (total_out) *total_out = out[n];
+    }
 }
 
 // Small inputs: one block walks the tiles in order with a running carry (one
@@ -435,7 +439,8 @@ __global__ void k_scan_add(uint64_t* __restrict__ out, uint64_t n, const uint64_
 constexpr uint64_t SCAN_ONE_BLOCK_MAX = 8 * SCAN_TILE;
 
 __global__ void k_scan_one_block(const uint32_t* __restrict__ counts, uint64_t n, uint64_t* __restrict__ out,
-                                 const uint64_t* __restrict__ n_dev, const uint64_t* __restrict__ base_dev) {
+                                 const uint64_t* __restrict__ n_dev, const uint64_t* __restrict__ base_dev,
+                                 unsigned long long* __restrict__ total_out) {
     __shared__ uint64_t warp_tot[32];
     __shared__ uint64_t tot;
     if (n_dev) n = *n_dev;
@@ -457,16 +462,19 @@ __global__ void k_scan_one_block(const uint32_t* __restrict__ counts, uint64_t n
         }
         carry += tot;  // read after the scan's closing barrier, rewritten only in the next tile's scan
     }
-    if (threadIdx.x == 0) out[n] = carry;
+    if (threadIdx.x == 0) {
+        out[n] = carry;
+        if (total_out) *total_out = carry;
+    }
 }
 
 cudaError_t launch_scan_counts(const uint32_t* counts, uint64_t n, uint64_t* offsets, uint64_t* tmp,
                                uint64_t tmp_words, cudaStream_t s, const uint64_t* n_dev, int* n_launched,
-                               const uint64_t* base_dev) {
+                               const uint64_t* base_dev, unsigned long long* total_out) {
     // with n_dev, n is the capacity the grids are sized for and the true count is read on the device;
     // with base_dev, every offset is shifted by the value it points to
     if (n <= SCAN_ONE_BLOCK_MAX) {
-        k_scan_one_block<<<1, SCAN_THREADS, 0, s>>>(counts, n, offsets, n_dev, base_dev);
+        k_scan_one_block<<<1, SCAN_THREADS, 0, s>>>(counts, n, offsets, n_dev, base_dev, total_out);
         if (n_launched) *n_launched = 1;
         return cudaGetLastError();
     }
@@ -475,7 +483,7 @@ cudaError_t launch_scan_counts(const uint32_t* counts, uint64_t n, uint64_t* off
     if (tmp_words < tiles + 1) return cudaErrorInvalidValue;
     k_scan_tiles<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(counts, n, offsets, tmp, n_dev, base_dev);
     k_scan_sums<<<1, SCAN_THREADS, 0, s>>>(tmp, tiles, n_dev);
-    k_scan_add<<<(unsigned)tiles, 256, 0, s>>>(offsets, n, tmp, tiles, n_dev, base_dev);
+    k_scan_add<<<(unsigned)tiles, 256, 0, s>>>(offsets, n, tmp, tiles, n_dev, base_dev, total_out);
     if (n_launched) *n_launched = 3;
     return cudaGetLastError();
 }
@@ -544,11 +552,9 @@ cudaError_t launch_cluster_order(const BatchView& b, uint64_t* keys, uint32_t* h
 
 __global__ void k_gather(QueryOut o, const uint64_t* __restrict__ id_offsets, uint64_t n,
                          uint32_t* __restrict__ ids, const DevStatus* st, const uint64_t* __restrict__ n_dev,
-                         uint64_t ids_cap, unsigned long long* total_out) {
-    if (n_dev) n = *n_dev;
-    // the number of result IDs, for a caller that reads the status block only
-    if (total_out && blockIdx.x == 0 && threadIdx.x == 0) *total_out = id_offsets[n];
+                         uint64_t ids_cap) {
     if (st->err != NO_ERR || st->cursor > o.stage_cap) return;
+    if (n_dev) n = *n_dev;
     if (id_offsets[n] > ids_cap) return;  // the caller sees the total and reports the shortfall
     const int lane = threadIdx.x & 31;
     uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -563,11 +569,10 @@ __global__ void k_gather(QueryOut o, const uint64_t* __restrict__ id_offsets, ui
 }
 
 cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_t n, uint32_t* ids,
-                          const DevStatus* st, cudaStream_t s, const uint64_t* n_dev, uint64_t ids_cap,
-                          unsigned long long* total_out) {
+                          const DevStatus* st, cudaStream_t s, const uint64_t* n_dev, uint64_t ids_cap) {
     if (n == 0) return cudaSuccess;
     int blocks = grid_for(n * 32, 256, 152 * 16);
-    k_gather<<<blocks, 256, 0, s>>>(o, id_offsets, n, ids, st, n_dev, ids_cap, total_out);
+    k_gather<<<blocks, 256, 0, s>>>(o, id_offsets, n, ids, st, n_dev, ids_cap);
     return cudaGetLastError();
 }
 

@@ -295,6 +295,7 @@ void default_config(rambo* h) {
     h->cfg.cluster = 0;
     h->cfg.row_load = 0;
     h->cfg.warps_per_query = 0;
+    h->cfg.host_chunks = 0;
 }
 
 int decode_err(rambo* h, unsigned long long e) {
@@ -653,7 +654,7 @@ int run_query_pipelined(rambo* h, BatchView b, const void* d_data, int seq, uint
     RK(h->h_id_off.ensure(n + 1));
     uint64_t* d_off = h->id_off.p;
     const uint64_t cap = h->ids.cap < h->h_ids.cap ? h->ids.cap : h->h_ids.cap;
-    const int C = n >= (1u << 19) ? PIPE_MAX_CHUNKS : PIPE_MAX_CHUNKS / 2;
+    const int C = h->cfg.host_chunks ? (int)h->cfg.host_chunks : (n >= (1u << 19) ? PIPE_MAX_CHUNKS : PIPE_MAX_CHUNKS / 2);
     uint64_t q_lo[PIPE_MAX_CHUNKS + 1];
     for (int c = 0; c <= C; ++c) q_lo[c] = n * (uint64_t)c / (uint64_t)C;
 
@@ -787,7 +788,8 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
     RK(h->qstart.ensure(n));
     RK(h->scan_tmp.ensure(scan_tmp_words(n)));
     if (h->stage.cap < (1u << 20)) RK(h->stage.ensure(1u << 20));
-    if (!on_device && d.arena && n >= PIPE_MIN_QUERIES && !h->cfg.cluster && !h->cfg.l2_fetch_bytes) {
+    if (!on_device && d.arena && n >= PIPE_MIN_QUERIES && !h->cfg.cluster && !h->cfg.l2_fetch_bytes &&
+        h->cfg.host_chunks != 1) {
         const int rc = run_query_pipelined(h, b, d_data, seq, k, n, s, d);
         if (rc != PIPE_FALLBACK) return rc;
         h->launches = 0;
@@ -1286,7 +1288,9 @@ int rambo_get_query_config(const rambo_t* h, rambo_query_config_t* out) {
 
 int rambo_set_query_config(rambo_t* h, const rambo_query_config_t* cfg) {
     if (!h || !cfg) return RAMBO_EINVAL;
-    if (!query_config_supported((int)cfg->words_per_lane, (int)cfg->lanes_per_key, h->S)) return RAMBO_EINVAL;
+    // (indexes served by the block-per-query kernel ignore the tiling fields)
+    if (!query_is_wide(h->R, h->S) && !query_config_supported((int)cfg->words_per_lane, (int)cfg->lanes_per_key, h->S))
+        return RAMBO_EINVAL;
     if (cfg->warps_per_block != 0 && cfg->warps_per_block != 1 && cfg->warps_per_block != 2 &&
         cfg->warps_per_block != 4 && cfg->warps_per_block != 8)
         return RAMBO_EINVAL;
@@ -1299,6 +1303,7 @@ int rambo_set_query_config(rambo_t* h, const rambo_query_config_t* cfg) {
         return RAMBO_EINVAL;
     if (cfg->l2_fetch_bytes && cfg->l2_fetch_bytes != 32 && cfg->l2_fetch_bytes != 64 && cfg->l2_fetch_bytes != 128)
         return RAMBO_EINVAL;
+    if (cfg->host_chunks > (uint32_t)PIPE_MAX_CHUNKS) return RAMBO_EINVAL;
     h->cfg = *cfg;
     return RAMBO_OK;
 }
@@ -1323,6 +1328,7 @@ int rambo_list_query_configs(const rambo_t* h, rambo_query_config_t* out, int ca
                 out[n].cluster = 0;
                 out[n].row_load = 0;
                 out[n].warps_per_query = 0;
+                out[n].host_chunks = h->cfg.host_chunks;
             }
             ++n;
         }
@@ -1377,6 +1383,7 @@ int rambo_autotune(rambo_t* h, int kind, const void* data, const uint64_t* offse
             cfg.set_stage = keep.set_stage;
             cfg.row_load = keep.row_load;
             cfg.warps_per_query = keep.warps_per_query;
+            cfg.host_chunks = keep.host_chunks;
             if (rambo_set_query_config(h, &cfg) != RAMBO_OK) continue;
             float t_min = -1.0f;
             for (int r = 0; r < reps; ++r) {

@@ -293,11 +293,12 @@ cudaError_t launch_resolve_bad_base(const BatchView& b, DevStatus* st, cudaStrea
 cudaError_t launch_register(const BatchView& b, uint32_t* reg, DevStatus* st, cudaStream_t s);
 cudaError_t launch_scan_counts(const uint32_t* counts, uint64_t n, uint64_t* offsets,
                                uint64_t* tmp, uint64_t tmp_words, cudaStream_t s, const uint64_t* n_dev = nullptr,
-                               int* n_launched = nullptr, const uint64_t* base_dev = nullptr);
+                               int* n_launched = nullptr, const uint64_t* base_dev = nullptr,
+                               unsigned long long* total_out = nullptr);
 uint64_t scan_tmp_words(uint64_t n);
 cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_t n, uint32_t* ids,
                           const DevStatus* st, cudaStream_t s, const uint64_t* n_dev = nullptr,
-                          uint64_t ids_cap = ~0ull, unsigned long long* total_out = nullptr);
+                          uint64_t ids_cap = ~0ull);
 // queries: validation and (bases != NULL) packing in one launch; n_words is
 // the packed capacity (a descriptor batch packs total/32 + 2 words of it)
 cudaError_t launch_intake(const BatchView& b, uint64_t min_len, uint64_t K, const uint8_t* bases, uint64_t* packed,

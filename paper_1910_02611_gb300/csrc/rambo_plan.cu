@@ -158,12 +158,12 @@ int plan_capture(rambo_plan* p, bool timed) {
     if (e == cudaSuccess) e = mark(p, 2, s, timed);
     if (e == cudaSuccess) {
         int n_scan = 0;
-        e = launch_scan_counts(p->qcount, p->max_q, p->id_off, p->scan_tmp, scan_words, s, p->d_desc, &n_scan);
+        // the scan also stores the number of result IDs in the status block
+        e = launch_scan_counts(p->qcount, p->max_q, p->id_off, p->scan_tmp, scan_words, s, p->d_desc, &n_scan,
+                               nullptr, &p->st->spare[1]);
         n_launch += n_scan;
     }
-    // the gather also stores the number of result IDs in the status block
-    if (e == cudaSuccess)
-        e = launch_gather(o, p->id_off, p->max_q, p->ids, p->st, s, p->d_desc, p->max_ids, &p->st->spare[1]);
+    if (e == cudaSuccess) e = launch_gather(o, p->id_off, p->max_q, p->ids, p->st, s, p->d_desc, p->max_ids);
     ++n_launch;
     if (e == cudaSuccess) e = mark(p, 3, s, timed);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->h_st, p->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);

@@ -487,6 +487,7 @@ def run_ours(args):
         ho = torch.from_numpy(q.offsets.view(np.int64)).pin_memory().numpy().view(np.uint64)
         host_batches.append((hd.view(np.uint64) if q.kind == "keys" else hd, ho, keys_in(q, w.k), len(q)))
     e2e_s, e2e_keys, h2d, d2h = 0.0, 0, 0, 0
+    e2e_dev_ms, e2e_launch = [], set()
     n_e2e = 0 if args.no_extras else max(1, min(args.e2e_steps, args.steps))
     # untimed warm-up over every batch: the handle's pinned result arena and
     # input buffers reach their largest size before the timed calls
@@ -505,6 +506,9 @@ def run_ours(args):
         ids, offs = g.query(hd, ho, kind=batches[0].kind, k=w.k, copy=False)
         e2e_s += time.perf_counter() - t0
         e2e_keys += nk
+        st = g.last_query_stats()
+        e2e_dev_ms.append(st["device_ms"])
+        e2e_launch.add(st["kernel_launches"])
         h2d += hd.nbytes + ho.nbytes
         d2h += offs.nbytes + ids.nbytes
 
@@ -609,7 +613,9 @@ def run_ours(args):
         "results_per_step": n_ids / args.steps,
         "result_bytes_per_s": n_ids * 4 / (total_ms_max / 1000),
         "e2e": ({"value": e2e_keys_all / e2e_s_max, "unit": UNIT, "h2d_bytes_per_step": h2d // n_e2e,
-                 "d2h_bytes_per_step": d2h // n_e2e} if n_e2e else None),
+                 "d2h_bytes_per_step": d2h // n_e2e, "steps": n_e2e, "ms_per_step": 1000 * e2e_s / n_e2e,
+                 "device_ms_per_step": statistics.mean(e2e_dev_ms),
+                 "kernel_launches_per_call": sorted(e2e_launch)} if n_e2e else None),
         "gpu_launches": launches,
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",

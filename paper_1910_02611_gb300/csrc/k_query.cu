@@ -31,6 +31,19 @@ uint32_t query_smem_words_per_warp(uint32_t R, uint32_t S, uint64_t K, int use_b
     return (QK_CTL + R * S + QK_ID_CAP + (use_bitmap ? qk_bitmap_words(K) : 0) + 3u) & ~3u;
 }
 
+// Shared memory of the grouped instance: every warp's control, mask and
+// staging words, then one bitmap per query group.  group > 1 fixes the group
+// size (min(group, warps per block)); group = 0 lets the device choose it
+// from the batch, at least 2 warps, so a block holds at most wpb/2 groups.
+size_t query_group_smem_bytes(uint32_t R, uint32_t S, uint64_t K, int wpb, int group) {
+    const uint32_t small = query_smem_words_per_warp(R, S, K, 0);
+    const uint32_t bwr = (qk_bitmap_words(K) + 3u) & ~3u;
+    int P = group > 1 ? (group < wpb ? group : wpb) : 2;
+    if (P < 2) P = 2;
+    const int groups = wpb / P > 0 ? wpb / P : 1;
+    return ((size_t)small * wpb + (size_t)bwr * groups) * 4;
+}
+
 int query_max_blocks_per_sm(int V, int G, uint32_t eta, bool grouped, int warps_per_block, size_t smem_per_block) {
     const void* f = kernel_ptr(V, G, eta, grouped);
     if (!f) return 0;
@@ -70,8 +83,10 @@ cudaError_t launch_query(const IndexView& ix, const HashParams& hp, const BatchV
         if (e == cudaSuccess && n_launched) *n_launched = 1;
         return e;
     }
-    const uint32_t spw = query_smem_words_per_warp(ix.R, ix.S, ix.K, use_bitmap);
-    const size_t smem = (size_t)spw * 4 * t.warps_per_block;
+    // one-warp instance: a bitmap in every warp's region; grouped instance:
+    // one per group after the warps' regions
+    const uint32_t spw_warp = query_smem_words_per_warp(ix.R, ix.S, ix.K, use_bitmap);
+    const uint32_t spw_group = query_smem_words_per_warp(ix.R, ix.S, ix.K, 0);
     // Which instance serves the batch: known here for host-sized batches;
     // for a batch sized on the device (a captured plan) both are launched
     // and the one that does not match returns at once.
@@ -91,6 +106,9 @@ cudaError_t launch_query(const IndexView& ix, const HashParams& hp, const BatchV
         if (grouped ? !run_group : !run_warp) continue;
         const void* f = kernel_ptr(t.V, t.G, ix.eta, grouped);
         if (!f) return cudaErrorInvalidValue;
+        const uint32_t spw = grouped ? spw_group : spw_warp;
+        const size_t smem = grouped ? query_group_smem_bytes(ix.R, ix.S, ix.K, t.warps_per_block, t.group)
+                                    : (size_t)spw * 4 * t.warps_per_block;
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;

@@ -336,7 +336,43 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                         // partition rows are two independent coalesced loads.
                         const uint32_t* cellmask = sM + rstar * ix.S;
                         const uint64_t cbase = (uint64_t)rstar * ix.B;
-                        for (uint32_t w = 0; w < ix.W; ++w) {
+                        // large cells (64+ members on average): one hit cell at a
+                        // time, its members read as a contiguous run
+                        const bool by_cell = ix.K >= 64ull * ix.B;
+                        for (uint32_t w = 0; by_cell && w < ix.W; ++w) {
+                            uint32_t hits = cellmask[w];
+                            while (hits) {
+                                const uint64_t cell = cbase + w * 32 + (uint32_t)(__ffs(hits) - 1);
+                                hits &= hits - 1;
+                                const uint32_t m0 = (uint32_t)__ldg(ix.mem_off + cell);
+                                const uint32_t m1 = (uint32_t)__ldg(ix.mem_off + cell + 1);
+                                constexpr int SC = 4;
+                                for (uint32_t u0 = m0; u0 < m1; u0 += 32 * SC) {
+                                    uint32_t id[SC];
+                                    uint4 ph[SC];
+#pragma unroll
+                                    for (int c = 0; c < SC; ++c) {
+                                        const uint32_t pos = u0 + 32 * c + lane;
+                                        const bool v = pos < m1;
+                                        id[c] = v ? __ldg(ix.mem_ids + pos) : 0xffffffffu;
+                                        ph[c] = v ? __ldg(ix.mem_phi + pos) : make_uint4(0, 0, 0, 0);
+                                    }
+#pragma unroll
+                                    for (int c = 0; c < SC; ++c) {
+                                        if (id[c] == 0xffffffffu) continue;
+                                        const uint32_t cl[8] = {ph[c].x & 0xffffu, ph[c].x >> 16, ph[c].y & 0xffffu,
+                                                                ph[c].y >> 16,     ph[c].z & 0xffffu, ph[c].z >> 16,
+                                                                ph[c].w & 0xffffu, ph[c].w >> 16};
+                                        bool ok = true;
+#pragma unroll
+                                        for (int r = 0; r < RF; ++r)
+                                            if (r < R && r != rstar) ok &= (sM[r * ix.S + (cl[r] >> 5)] >> (cl[r] & 31)) & 1u;
+                                        if (ok) atomicOr(sBits + (id[c] >> 5), 1u << (id[c] & 31));
+                                    }
+                                }
+                            }
+                        }
+                        for (uint32_t w = 0; !by_cell && w < ix.W; ++w) {
                             const uint32_t hits = cellmask[w];
                             if (!hits) continue;
                             uint32_t m0 = 0, cnt = 0;
@@ -597,13 +633,14 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
         const unsigned gi = wid / P, gw = wid % P;
         const bool leader = gw == 0 && lane == 0;
         // the group's shared state lives in its first warp's region; each warp
-        // keeps its own staging words
-        // (per-warp region: [QK_CTL] control, [R][S] masks, [QK_ID_CAP] staging,
-        // [ceil(K/32)] bitmap when the set stage uses one)
+        // keeps its own staging words.  Layout of this instance: per warp
+        // [QK_CTL] control, [R][S] masks, [QK_ID_CAP] staging (smem_per_warp
+        // words, no bitmap), then one ceil(K/32)-word bitmap per query group
+        // (groups have at least two warps, so half a bitmap per warp at most)
         uint32_t* lead = qk_smem + (gi * P) * smem_per_warp;
         uint32_t* ctl = lead;                                                // group control words
         uint32_t* sM = lead + QK_CTL;                                        // [R][S] running masks
-        uint32_t* sBits = sM + R * ix.S + QK_ID_CAP;                         // set-stage bitmap
+        uint32_t* sBits = qk_smem + wpb * smem_per_warp + gi * ((bw + 3u) & ~3u);  // the group's bitmap
         uint32_t* sIds = qk_smem + wid * smem_per_warp + QK_CTL + R * ix.S;  // this warp's staging
         volatile unsigned long long* ctl_ticket = reinterpret_cast<volatile unsigned long long*>(ctl);
         volatile unsigned long long* ctl_start = reinterpret_cast<volatile unsigned long long*>(ctl + 2);
@@ -823,7 +860,43 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                             // independent coalesced loads.
                             const uint32_t* cellmask = sM + rstar * ix.S;
                             const uint64_t cbase = (uint64_t)rstar * ix.B;
-                            for (uint32_t w = 0; w < ix.W; ++w) {
+                            // large cells (64+ members on average): one hit cell at a
+                            // time, its members a contiguous run the group's warps share
+                            const bool by_cell = ix.K >= 64ull * ix.B;
+                            for (uint32_t w = 0; by_cell && w < ix.W; ++w) {
+                                uint32_t hits = cellmask[w];
+                                while (hits) {
+                                    const uint64_t cell = cbase + w * 32 + (uint32_t)(__ffs(hits) - 1);
+                                    hits &= hits - 1;
+                                    const uint32_t m0 = (uint32_t)__ldg(ix.mem_off + cell);
+                                    const uint32_t m1 = (uint32_t)__ldg(ix.mem_off + cell + 1);
+                                    constexpr int SC = 4;
+                                    for (uint32_t u0 = m0 + gw * 32 * SC; u0 < m1; u0 += P * 32 * SC) {
+                                        uint32_t id[SC];
+                                        uint4 ph[SC];
+#pragma unroll
+                                        for (int c = 0; c < SC; ++c) {
+                                            const uint32_t pos = u0 + 32 * c + lane;
+                                            const bool v = pos < m1;
+                                            id[c] = v ? __ldg(ix.mem_ids + pos) : 0xffffffffu;
+                                            ph[c] = v ? __ldg(ix.mem_phi + pos) : make_uint4(0, 0, 0, 0);
+                                        }
+#pragma unroll
+                                        for (int c = 0; c < SC; ++c) {
+                                            if (id[c] == 0xffffffffu) continue;
+                                            const uint32_t cl[8] = {ph[c].x & 0xffffu, ph[c].x >> 16, ph[c].y & 0xffffu,
+                                                                    ph[c].y >> 16,     ph[c].z & 0xffffu, ph[c].z >> 16,
+                                                                    ph[c].w & 0xffffu, ph[c].w >> 16};
+                                            bool ok = true;
+#pragma unroll
+                                            for (int r = 0; r < RF; ++r)
+                                                if (r < R && r != rstar) ok &= (sM[r * ix.S + (cl[r] >> 5)] >> (cl[r] & 31)) & 1u;
+                                            if (ok) atomicOr(sBits + (id[c] >> 5), 1u << (id[c] & 31));
+                                        }
+                                    }
+                                }
+                            }
+                            for (uint32_t w = 0; !by_cell && w < ix.W; ++w) {
                                 const uint32_t hits = cellmask[w];
                                 if (!hits) continue;
                                 uint32_t m0 = 0, cnt = 0;

@@ -579,7 +579,7 @@ int resolve_tuning(rambo* h, uint64_t n, int& use_bitmap, QueryTuning& t) {
     t.group_warps = 0;
     if (use_bitmap && t.group != 1 && t.warps_per_block > 1) {
         int per_sm_g = query_max_blocks_per_sm(t.V, t.G, h->eta, true, t.warps_per_block,
-                                               spw_bytes * (size_t)t.warps_per_block);
+                                               query_group_smem_bytes(h->R, h->S, h->K, t.warps_per_block, t.group));
         if (h->cfg.blocks_per_sm && (int)h->cfg.blocks_per_sm < per_sm_g) per_sm_g = (int)h->cfg.blocks_per_sm;
         uint64_t bg = (uint64_t)per_sm_g * h->num_sms;
         if (bg > n) bg = n;

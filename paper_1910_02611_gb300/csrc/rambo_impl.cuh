@@ -331,6 +331,7 @@ cudaError_t launch_bucket_apply(uint32_t* rows, uint64_t win_word0, const uint32
 // k_query*.cu
 bool query_config_supported(int V, int G, uint32_t S);
 uint32_t query_smem_words_per_warp(uint32_t R, uint32_t S, uint64_t K, int use_bitmap);
+size_t query_group_smem_bytes(uint32_t R, uint32_t S, uint64_t K, int wpb, int group);
 int query_max_blocks_per_sm(int V, int G, uint32_t eta, bool grouped, int warps_per_block, size_t smem_per_block);
 unsigned query_group_size(uint64_t n, int group, unsigned wpb, uint64_t group_warps, int use_bitmap);
 cudaError_t launch_query(const IndexView& ix, const HashParams& hp, const BatchView& b, const QueryOut& o,

@@ -462,9 +462,8 @@ typedef struct rambo_query_config {
                                * query calls with on_device = 0, batches of
                                * 65536 queries or more): the batch runs as this
                                * many chunks whose answers are copied while the
-                               * next ones compute; 0 = automatic (4, or 8 from
-                               * 2^19 queries), 1 = one piece, copied at the end;
-                               * at most 8 */
+                               * next ones compute; 0 = automatic (4), 1 = one
+                               * piece, copied at the end; at most 8 */
 } rambo_query_config_t;
 
 int rambo_get_query_config(const rambo_t *h, rambo_query_config_t *out);
@@ -475,11 +474,12 @@ int rambo_set_query_config(rambo_t *h, const rambo_query_config_t *cfg);
  * call from the input and index sizes, 1 = always run the build window by
  * window (each window of tile_bytes of the index stays resident in L2 while
  * the input streams past), 2 = one pass with every update going to device
- * memory, 3 = hash every key once per input chunk, file its updates by
- * 48 MiB window of the index and apply them window by window (needs
- * R * eta <= 32; a chunk whose updates are far from uniform over the rows
- * falls back to mode 1).  Mode 0 takes 3 for large builds.  tile_bytes = 0
- * keeps the current window size of mode 1 (128 MiB initially). */
+ * memory, 3 = file every update by 128 KB slice of the index (passes over
+ * up to 4096 slices, each hashing every key once) and apply each slice in
+ * shared memory (needs R * eta <= 32; falls back to mode 1 when device
+ * memory for the updates is short).  Mode 0 takes 3 for large builds.
+ * tile_bytes = 0 keeps the current window size of mode 1 (128 MiB
+ * initially). */
 int rambo_set_build_tiling(rambo_t *h, uint64_t tile_bytes, int mode);
 
 /* Lists the query-kernel configurations valid for this handle (at most cap),

@@ -474,10 +474,10 @@ int rambo_set_query_config(rambo_t *h, const rambo_query_config_t *cfg);
  * call from the input and index sizes, 1 = always run the build window by
  * window (each window of tile_bytes of the index stays resident in L2 while
  * the input streams past), 2 = one pass with every update going to device
- * memory, 3 = file every update by 128 KB slice of the index (passes over
- * up to 4096 slices, each hashing every key once) and apply each slice in
- * shared memory (needs R * eta <= 32; falls back to mode 1 when device
- * memory for the updates is short).  Mode 0 takes 3 for large builds.
+ * memory, 3 = hash every key once per input chunk, file its updates by
+ * 48 MiB window of the index and apply them window by window while the
+ * window is resident in L2 (needs R * eta <= 32; falls back to mode 1 when
+ * device memory for the updates is short).  Mode 0 takes 3 for large builds.
  * tile_bytes = 0 keeps the current window size of mode 1 (128 MiB
  * initially). */
 int rambo_set_build_tiling(rambo_t *h, uint64_t tile_bytes, int mode);

@@ -346,7 +346,7 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                                 hits &= hits - 1;
                                 const uint32_t m0 = (uint32_t)__ldg(ix.mem_off + cell);
                                 const uint32_t m1 = (uint32_t)__ldg(ix.mem_off + cell + 1);
-                                constexpr int SC = 8;  // candidates in flight per lane (L2 latency)
+                                constexpr int SC = 4;
                                 for (uint32_t u0 = m0; u0 < m1; u0 += 32 * SC) {
                                     uint32_t id[SC];
                                     uint4 ph[SC];
@@ -870,7 +870,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                                     hits &= hits - 1;
                                     const uint32_t m0 = (uint32_t)__ldg(ix.mem_off + cell);
                                     const uint32_t m1 = (uint32_t)__ldg(ix.mem_off + cell + 1);
-                                    constexpr int SC = 8;  // candidates in flight per lane (L2 latency)
+                                    constexpr int SC = 4;
                                     for (uint32_t u0 = m0 + gw * 32 * SC; u0 < m1; u0 += P * 32 * SC) {
                                         uint32_t id[SC];
                                         uint4 ph[SC];

@@ -131,9 +131,7 @@ struct rambo {
     DBuf<uint32_t> stage, qcount, ids, fill, perm, chist, nmask;
     DBuf<uint64_t> ckeys, coff;
     DBuf<uint32_t> brec;               // bucketed build: update records
-    DBuf<unsigned long long> bfill;    // bucketed build: per-slice fill counters + overflow flag
-    DBuf<uint64_t> boff;               // bucketed build: per-slice bucket offsets
-    HBuf<uint64_t> h_boff;             // (pinned host copy)
+    DBuf<unsigned long long> bfill;    // bucketed build: per-window fill counters + overflow flag
     HBuf<uint32_t> h_ids;
     HBuf<uint64_t> h_id_off;
     // host-output pipeline: copy stream, per-chunk events, chunk bases and totals, status copies
@@ -216,8 +214,6 @@ void free_handle(rambo* h) {
     h->ckeys.release();
     h->brec.release();
     h->bfill.release();
-    h->boff.release();
-    h->h_boff.release();
     h->coff.release();
     h->h_ids.release();
     h->h_id_off.release();
@@ -383,71 +379,59 @@ int pack_bases(rambo* h, BatchView& b, const void* d_bases, cudaStream_t s) {
     return RAMBO_OK;
 }
 
-// Bucketed build of a validated, packed, registered batch (k_build_bucket.cu):
-// the index words are cut into 128 KB slices; each pass over up to 4096
-// slices hashes every key once, files the updates that fall in its slices
-// into per-slice buckets sized for uniform hashing with 1.5x margin, and
-// applies every slice in shared memory.  A pass whose records overflow a
-// bucket (keys repeated across many sets make the shares lumpy) is counted
-// exactly and filed again into buckets of exactly that size.  Returns
-// BUCKET_FALLBACK when the device memory budget does not allow it; the caller
-// then builds window by window.
+// Bucketed build of a validated, packed, registered batch: the input is cut
+// into chunks whose update records (R*eta per key, 4 bytes each) fit a
+// budget of device memory; per chunk one scatter launch files every record
+// into its window's bucket (a chunk whose records overflow a bucket is filed
+// again into larger ones) and one apply launch per window ORs the bucket
+// into the rows.  Returns BUCKET_FALLBACK when memory or the bucket count
+// does not allow it; the caller then builds window by window.
 constexpr int BUCKET_FALLBACK = 1;
-constexpr uint32_t BUCKET_MAX_SLICES = 4096;
+constexpr uint64_t BUCKET_WIN_BYTES = 48ull << 20;  // a window: well inside one die's share of L2
 
 int insert_bucketed(rambo* h, const BatchView& b, cudaStream_t s) {
-    const uint64_t total_words = h->index_words();
-    const uint64_t sw = bucket_slice_words();
-    const uint64_t n_slices = (total_words + sw - 1) / sw;
+    const uint64_t rows_total = (uint64_t)h->R * h->m;
+    uint64_t rows_per_win = BUCKET_WIN_BYTES / ((uint64_t)h->S * 4);
+    if (rows_per_win < 1) rows_per_win = 1;
+    if (rows_per_win > rows_total) rows_per_win = rows_total;
+    const uint64_t n_win64 = (rows_total + rows_per_win - 1) / rows_per_win;
+    if (n_win64 > 4096) return BUCKET_FALLBACK;
+    const uint32_t n_win = (uint32_t)n_win64;
     const uint64_t per_key = (uint64_t)h->R * h->eta;
-    // update records: up to 3e9 per pass (12 GB), or a third of the free memory
+    // records per chunk: up to 3e9 (12 GB), or a third of the free memory
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
     uint64_t budget = (uint64_t)free_b / 3 / 4;
     if (budget > 3000000000ull) budget = 3000000000ull;
-    const double per_slice = (double)b.total * (double)per_key * (double)sw / (double)total_words;
-    const uint64_t cap = (uint64_t)(per_slice * 1.5) + 4096;
-    uint64_t spp = budget / cap;
-    if (spp > BUCKET_MAX_SLICES) spp = BUCKET_MAX_SLICES;
-    if (spp < 1 || budget < (1ull << 22)) return BUCKET_FALLBACK;
-    RK(h->bfill.ensure(BUCKET_MAX_SLICES + 1));  // [slices] fill counters, then the overflow flag
-    RK(h->boff.ensure(BUCKET_MAX_SLICES + 1));
-    RK(h->h_boff.ensure(BUCKET_MAX_SLICES + 1));
-    unsigned long long* fill = h->bfill.p;
-    unsigned long long* overflow = h->bfill.p + BUCKET_MAX_SLICES;
+    if (budget < (1ull << 24)) return BUCKET_FALLBACK;
+    uint64_t chunk_keys = (uint64_t)((double)budget / 1.6 / (double)per_key);
+    if (chunk_keys > b.total) chunk_keys = b.total;
+    if (chunk_keys < 1) chunk_keys = 1;
+    // a window's share of a chunk's records (each distinct key's positions are
+    // uniform over the rows; keys repeated across sets make the shares lumpier)
+    const double expect = (double)chunk_keys * (double)per_key * (double)rows_per_win / (double)rows_total;
+    uint64_t cap = (uint64_t)(expect * 1.5) + 65536;
+    RK(h->bfill.ensure(n_win + 1));  // [n_win] fill counters, then the overflow flag
     const IndexView ix = h->view();
-    for (uint64_t s_lo = 0; s_lo < n_slices; s_lo += spp) {
-        const uint32_t n_sl = (uint32_t)(n_slices - s_lo < spp ? n_slices - s_lo : spp);
-        // optimistic buckets of cap records each
-        for (uint32_t i = 0; i <= n_sl; ++i) h->h_boff.p[i] = (uint64_t)i * cap;
-        RK(h->brec.ensure((uint64_t)n_sl * cap));
-        CK(cudaMemcpyAsync(h->boff.p, h->h_boff.p, (n_sl + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
-        CK(cudaMemsetAsync(fill, 0, n_sl * sizeof(unsigned long long), s));
-        CK(cudaMemsetAsync(overflow, 0, sizeof(unsigned long long), s));
-        CK(launch_bucket_scatter(ix, h->hp, b, s_lo, n_sl, h->boff.p, h->brec.p, fill, overflow, h->st, h->num_sms,
-                                 s));
-        CK(cudaMemcpyAsync(h->h_small, overflow, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (h->h_small[0]) {
-            // count this pass's records per slice exactly, then file them again
-            CK(cudaMemsetAsync(fill, 0, n_sl * sizeof(unsigned long long), s));
-            CK(launch_bucket_scatter(ix, h->hp, b, s_lo, n_sl, h->boff.p, nullptr, fill, overflow, h->st,
-                                     h->num_sms, s));
-            CK(cudaMemcpyAsync(h->h_boff.p + 1, fill, n_sl * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    for (uint64_t p_lo = 0; p_lo < b.total; p_lo += chunk_keys) {
+        const uint64_t p_hi = p_lo + chunk_keys < b.total ? p_lo + chunk_keys : b.total;
+        for (int attempt = 0;; ++attempt) {
+            if (h->brec.ensure(n_win * cap) != RAMBO_OK) return BUCKET_FALLBACK;
+            CK(cudaMemsetAsync(h->bfill.p, 0, (n_win + 1) * sizeof(unsigned long long), s));
+            CK(launch_bucket_scatter(ix, h->hp, b, p_lo, p_hi, rows_per_win, n_win, cap, h->brec.p, h->bfill.p,
+                                     h->bfill.p + n_win, h->st, h->num_sms, s));
+            CK(cudaMemcpyAsync(h->h_small, h->bfill.p + n_win, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               s));
             CK(cudaStreamSynchronize(s));
-            h->h_boff.p[0] = 0;
-            for (uint32_t i = 1; i <= n_sl; ++i) h->h_boff.p[i] += h->h_boff.p[i - 1];
-            if (h->h_boff.p[n_sl] > 2 * budget) return BUCKET_FALLBACK;
-            if (h->brec.ensure(h->h_boff.p[n_sl] + 1) != RAMBO_OK) return BUCKET_FALLBACK;
-            CK(cudaMemcpyAsync(h->boff.p, h->h_boff.p, (n_sl + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
-            CK(cudaMemsetAsync(fill, 0, n_sl * sizeof(unsigned long long), s));
-            CK(cudaMemsetAsync(overflow, 0, sizeof(unsigned long long), s));
-            CK(launch_bucket_scatter(ix, h->hp, b, s_lo, n_sl, h->boff.p, h->brec.p, fill, overflow, h->st,
-                                     h->num_sms, s));
+            if (!h->h_small[0]) break;
+            // a bucket overflowed: file the chunk again into larger buckets
+            if (attempt == 3) return BUCKET_FALLBACK;
+            cap *= 2;
         }
-        CK(launch_bucket_apply(h->rows, total_words, s_lo, n_sl, h->boff.p, h->brec.p, fill, s));
+        for (uint32_t w = 0; w < n_win; ++w)
+            CK(launch_bucket_apply(h->rows, (uint64_t)w * rows_per_win * h->S, h->brec.p, h->bfill.p, w, cap,
+                                   h->num_sms, s));
     }
-    CK(cudaStreamSynchronize(s));
     return RAMBO_OK;
 }
 

@@ -319,14 +319,13 @@ constexpr uint32_t CLUSTER_BUCKETS = 1u << 16;
 cudaError_t launch_insert(const IndexView& ix, const HashParams& hp, const BatchView& b,
                           uint64_t row_lo, uint64_t row_hi, DevStatus* st, int num_sms, cudaStream_t s);
 
-// k_build_bucket.cu: construction with the bit updates filed per 128 KB slice
-// of the index and applied in shared memory
-uint32_t bucket_slice_words();
-cudaError_t launch_bucket_scatter(const IndexView& ix, const HashParams& hp, const BatchView& b, uint64_t s_lo,
-                                  uint32_t n_sl, const uint64_t* bucket_off, uint32_t* rec, unsigned long long* fill,
-                                  unsigned long long* overflow, const DevStatus* st, int num_sms, cudaStream_t s);
-cudaError_t launch_bucket_apply(uint32_t* rows, uint64_t total_words, uint64_t s_lo, uint32_t n_sl,
-                                const uint64_t* bucket_off, const uint32_t* rec, const unsigned long long* fill,
+// k_build_bucket.cu: hash-once construction (records filed by window, applied window by window)
+cudaError_t launch_bucket_scatter(const IndexView& ix, const HashParams& hp, const BatchView& b, uint64_t p_lo,
+                                  uint64_t p_hi, uint64_t rows_per_win, uint32_t n_win, uint64_t cap, uint32_t* rec,
+                                  unsigned long long* fill, unsigned long long* overflow, const DevStatus* st,
+                                  int num_sms, cudaStream_t s);
+cudaError_t launch_bucket_apply(uint32_t* rows, uint64_t win_word0, const uint32_t* rec,
+                                const unsigned long long* fill, uint32_t win, uint64_t cap, int num_sms,
                                 cudaStream_t s);
 
 // k_query*.cu

@@ -1299,7 +1299,7 @@ int rambo_set_query_config(rambo_t* h, const rambo_query_config_t* cfg) {
     if (cfg->set_stage > 3) return RAMBO_EINVAL;
     if (cfg->set_stage == 2 && !h->mem_off) return RAMBO_EINVAL;
     if (cfg->set_stage == 3 && !h->mem_bits) return RAMBO_EINVAL;
-    if (cfg->visit_order > 2 || cfg->cluster > 1 || cfg->row_load > 5) return RAMBO_EINVAL;
+    if (cfg->visit_order > 2 || cfg->cluster > 1 || cfg->row_load > 7) return RAMBO_EINVAL;
     if (cfg->warps_per_query != 0 && cfg->warps_per_query != 1 && cfg->warps_per_query != 2 &&
         cfg->warps_per_query != 4 && cfg->warps_per_query != 8)
         return RAMBO_EINVAL;
@@ -1542,7 +1542,7 @@ int rambo_random_row_probe(const uint32_t* dev_buf, uint64_t n_rows, uint32_t ro
                            void* stream) {
     if (!dev_buf || !ms || !blocks || !threads || threads > 256 || !n_rows)
         return RAMBO_EINVAL;
-    if (!(row_words == 1 || row_words == 2 || row_words % 4 == 0) || row_load > 5) return RAMBO_EINVAL;
+    if (!(row_words == 1 || row_words == 2 || row_words % 4 == 0) || row_load > 7) return RAMBO_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     uint32_t* sink = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;

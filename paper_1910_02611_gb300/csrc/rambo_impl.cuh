@@ -92,7 +92,8 @@ __device__ __forceinline__ uint64_t kmer_at(const uint64_t* __restrict__ packed,
 // Loads of one, two or four 32-bit words of an index row with a selectable
 // cache operator: 0 = ld.global.nc (read-only path), 1 = .cg (L2 only),
 // 2 = .cs (streaming, evict first), 3 = .lu (last use), 4 = .cv (uncached),
-// 5 = ld.global.nc.L1::no_allocate.  The row data and results never depend on
+// 5 = ld.global.nc.L1::no_allocate, 6 = ld.global.nc with the L2 prefetch
+// size hint .L2::64B, 7 = both.  The row data and results never depend on
 // the choice; it only changes how the memory system fetches isolated rows.
 __device__ __forceinline__ uint32_t ld_row1(const uint32_t* p, int kind) {
     switch (kind) {
@@ -103,6 +104,16 @@ __device__ __forceinline__ uint32_t ld_row1(const uint32_t* p, int kind) {
         case 5: {
             uint32_t v;
             asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+            return v;
+        }
+        case 6: {
+            uint32_t v;
+            asm volatile("ld.global.nc.L2::64B.u32 %0, [%1];" : "=r"(v) : "l"(p));
+            return v;
+        }
+        case 7: {
+            uint32_t v;
+            asm volatile("ld.global.nc.L1::no_allocate.L2::64B.u32 %0, [%1];" : "=r"(v) : "l"(p));
             return v;
         }
         default: return __ldg(p);
@@ -120,6 +131,16 @@ __device__ __forceinline__ uint2 ld_row2(const uint32_t* p, int kind) {
             asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(q));
             return v;
         }
+        case 6: {
+            uint2 v;
+            asm volatile("ld.global.nc.L2::64B.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(q));
+            return v;
+        }
+        case 7: {
+            uint2 v;
+            asm volatile("ld.global.nc.L1::no_allocate.L2::64B.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(q));
+            return v;
+        }
         default: return __ldg(q);
     }
 }
@@ -133,6 +154,20 @@ __device__ __forceinline__ uint4 ld_row4(const uint32_t* p, int kind) {
         case 5: {
             uint4 v;
             asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                         : "l"(q));
+            return v;
+        }
+        case 6: {
+            uint4 v;
+            asm volatile("ld.global.nc.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                         : "l"(q));
+            return v;
+        }
+        case 7: {
+            uint4 v;
+            asm volatile("ld.global.nc.L1::no_allocate.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];"
                          : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                          : "l"(q));
             return v;

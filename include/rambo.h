@@ -450,7 +450,8 @@ typedef struct rambo_query_config {
     uint32_t row_load;        /* cache operator of the row reads: 0 = ld.global.nc,
                                * 1 = .cg, 2 = .cs, 3 = .lu, 4 = .cv,
                                * 5 = .nc with L1::no_allocate, 6 = .nc with the
-                               * L2 prefetch-size hint L2::64B, 7 = 5 and 6 */
+                               * L2 prefetch-size hint L2::64B, 7 = 5 and 6
+                               * (the default) */
     uint32_t warps_per_query; /* 1 = one warp per query; 2, 4, 8 = that many warps
                                * of a block share each query (its terms and its
                                * set stage), capped at warps_per_block; 0 = from

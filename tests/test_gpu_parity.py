@@ -83,6 +83,9 @@ def test_queries_identical_every_kernel_config(pair):
         assert_query_equal(g, o, q, k=w.k)
         g.set_config(**{**base, "cluster": 1})
         assert_query_equal(g, o, w.queries, k=w.k)
+        for load in range(8):  # every cache operator / L2 prefetch-size hint of the row reads
+            g.set_config(**{**base, "row_load": load})
+            assert_query_equal(g, o, q, k=w.k)
     finally:
         g.set_config(**base)
 

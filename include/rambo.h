@@ -317,6 +317,9 @@ typedef struct rambo_server_stats {
     /* worker thread time: staging and launching batches, waiting for and
      * copying out finished batches, running inserts, idle */
     uint64_t admit_ns, finish_ns, insert_ns, idle_ns;
+    /* queries whose batch was deferred (requeued) because pinned host memory
+     * for its answers was refused */
+    uint64_t deferred;
 } rambo_server_stats_t;
 int rambo_server_create(rambo_t *h, const rambo_server_config_t *cfg, rambo_server_t **out);
 /* Queues one query (kind 0: n_items uint64 keys; kind 1: n_items ASCII
@@ -343,6 +346,14 @@ int rambo_server_reset_stats(rambo_server_t *s);
 int rambo_server_replay(rambo_server_t *s, const uint8_t *kinds, const uint8_t *bytes,
                         const uint64_t *byte_offsets, const uint64_t *arrival_ns, uint64_t n,
                         uint64_t *tickets);
+/* When pinned host memory for a finished batch's answers is refused, the
+ * server does not fail the batch: its queries go back to the front of the
+ * queue and run again after a 200 us pause in admission (collected results
+ * return buffers to the pool meanwhile); a query deferred 64 times fails with
+ * RAMBO_ENOMEM.  This call makes the next n such allocations (answers above
+ * 256 KB) be refused as if cudaMallocHost had failed -- a host-side fault
+ * injection for testing that path (0 ends it; nothing on the GPU fails). */
+int rambo_server_inject_alloc_failures(rambo_server_t *s, uint32_t n);
 /* Finishes all queued work, stops the worker and frees the server. */
 void rambo_server_destroy(rambo_server_t *s);
 

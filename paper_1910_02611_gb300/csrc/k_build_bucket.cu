@@ -37,7 +37,7 @@ __device__ __forceinline__ uint64_t bk_find_item(const uint64_t* __restrict__ of
 // *overflow instead (the caller then builds the batch another way).
 __global__ void __launch_bounds__(BK_THREADS) k_bucket_scatter(IndexView ix, HashParams hp, BatchView b,
                                                                 uint64_t p_lo, uint64_t p_hi, uint32_t kt,
-                                                                uint32_t win_shift, uint32_t n_win,
+                                                                uint64_t rows_per_win, uint32_t n_win,
                                                                 uint64_t cap, uint32_t* __restrict__ rec,
                                                                 unsigned long long* __restrict__ fill,
                                                                 unsigned long long* overflow, const DevStatus* st) {
@@ -88,8 +88,8 @@ __global__ void __launch_bounds__(BK_THREADS) k_bucket_scatter(IndexView ix, Has
                     const uint32_t cell = ph[r];
                     for (uint32_t j = 0; j < eta; ++j) {
                         const uint64_t g = (uint64_t)r * ix.m + ((hp.s[r][j] * y) >> ix.shift);  // global row
-                        const uint32_t win = (uint32_t)(g >> win_shift);  // windows of 2^win_shift rows
-                        const uint64_t row_in = g & ((1ull << win_shift) - 1);
+                        const uint32_t win = (uint32_t)(g / rows_per_win);
+                        const uint64_t row_in = g - (uint64_t)win * rows_per_win;
                         my_rec[nrec] = (uint32_t)(((row_in * ix.S + (cell >> 5)) << 5) | (cell & 31));
                         my_win[nrec] = (uint16_t)win;
                         ++nrec;
@@ -141,7 +141,7 @@ uint32_t bucket_keys_per_thread(uint32_t R, uint32_t eta) {
 }
 
 cudaError_t launch_bucket_scatter(const IndexView& ix, const HashParams& hp, const BatchView& b, uint64_t p_lo,
-                                  uint64_t p_hi, uint32_t win_shift, uint32_t n_win, uint64_t cap, uint32_t* rec,
+                                  uint64_t p_hi, uint64_t rows_per_win, uint32_t n_win, uint64_t cap, uint32_t* rec,
                                   unsigned long long* fill, unsigned long long* overflow, const DevStatus* st,
                                   int num_sms, cudaStream_t s) {
     if (p_hi <= p_lo) return cudaSuccess;
@@ -157,7 +157,7 @@ cudaError_t launch_bucket_scatter(const IndexView& ix, const HashParams& hp, con
     uint64_t blocks = (p_hi - p_lo + span - 1) / span;
     const uint64_t most = (uint64_t)num_sms * 4;
     if (blocks > most) blocks = most;
-    k_bucket_scatter<<<(unsigned)blocks, BK_THREADS, smem, s>>>(ix, hp, b, p_lo, p_hi, kt, win_shift, n_win, cap,
+    k_bucket_scatter<<<(unsigned)blocks, BK_THREADS, smem, s>>>(ix, hp, b, p_lo, p_hi, kt, rows_per_win, n_win, cap,
                                                                  rec, fill, overflow, st);
     return cudaGetLastError();
 }

@@ -356,7 +356,7 @@ cudaError_t launch_insert(const IndexView& ix, const HashParams& hp, const Batch
 
 // k_build_bucket.cu: hash-once construction (records filed by window, applied window by window)
 cudaError_t launch_bucket_scatter(const IndexView& ix, const HashParams& hp, const BatchView& b, uint64_t p_lo,
-                                  uint64_t p_hi, uint32_t win_shift, uint32_t n_win, uint64_t cap, uint32_t* rec,
+                                  uint64_t p_hi, uint64_t rows_per_win, uint32_t n_win, uint64_t cap, uint32_t* rec,
                                   unsigned long long* fill, unsigned long long* overflow, const DevStatus* st,
                                   int num_sms, cudaStream_t s);
 cudaError_t launch_bucket_apply(uint32_t* rows, uint64_t win_word0, const uint32_t* rec,

@@ -43,8 +43,14 @@ struct Op {
     std::vector<uint64_t> set_ids, offsets;
     uint32_t k = 31;
     bool solo = false;  // results overflowed a shared batch: run alone
+    uint32_t deferrals = 0;  // times its batch was deferred for want of pinned memory
     Clock::time_point t_submit;
 };
+
+// A query whose batch could not get pinned memory for its answers this many
+// times fails with RAMBO_ENOMEM; before that it is requeued and retried.
+constexpr uint32_t MAX_DEFERRALS = 64;
+constexpr auto DEFER_BACKOFF = std::chrono::microseconds(200);
 
 // Pinned host buffers for finished batches' large answers, reused across
 // batches: a batch's IDs are copied from the device straight into one, its
@@ -133,6 +139,11 @@ struct rambo_server {
     bool stop = false;
     std::thread worker;
     std::shared_ptr<PinnedPool> pool = std::make_shared<PinnedPool>();
+    // pinned-memory refusals: injected ones (host-side test hook), deferral
+    // count, and the time before which no new batch is admitted
+    std::atomic<uint32_t> inject_alloc_fail{0};
+    uint64_t n_deferred = 0;
+    Clock::time_point backoff_until{};
     // statistics
     uint64_t n_queries = 0, n_batches = 0, n_inserts = 0, keys_done = 0;
     std::atomic<uint64_t> admit_ns{0}, finish_ns{0}, insert_ns{0}, idle_ns{0};
@@ -164,14 +175,23 @@ void finish_slot(rambo_server* S, Slot& sl) {
     const uint64_t nq = sl.members.size();
     std::shared_ptr<ResultBuf> buf;
     const uint64_t* off = nullptr;
+    bool refused = false;  // no pinned memory for the answers
     if (rc == RAMBO_OK) {
         buf = std::make_shared<ResultBuf>();
         buf->pool = S->pool;
         const size_t off_bytes = (nq + 1) * 8, bytes = off_bytes + n_ids * 4;
         const bool small = bytes <= SMALL_RESULT_BYTES;
-        void* dst = small ? sl.staging : (buf->mem = S->pool->get(bytes, &buf->cap));
+        void* dst = sl.staging;
+        if (!small) {
+            // a refusal injected by rambo_server_inject_alloc_failures stands in for cudaMallocHost failing
+            uint32_t inj = S->inject_alloc_fail.load();
+            while (inj && !S->inject_alloc_fail.compare_exchange_weak(inj, inj - 1)) {
+            }
+            dst = inj ? nullptr : (buf->mem = S->pool->get(bytes, &buf->cap));
+        }
         if (!dst) {
             rc = RAMBO_ENOMEM;
+            refused = true;
         } else {
             uint8_t* base = static_cast<uint8_t*>(dst);
             bool ok = cudaMemcpyAsync(base, d_off, off_bytes, cudaMemcpyDeviceToHost, sl.stream) == cudaSuccess;
@@ -191,6 +211,33 @@ void finish_slot(rambo_server* S, Slot& sl) {
         }
     }
     const auto now = Clock::now();
+    if (refused) {
+        // no pinned memory for the answers: defer the batch -- its queries go
+        // back to the front of the queue and run again after a short
+        // back-off (collected results return buffers to the pool meanwhile);
+        // a query deferred MAX_DEFERRALS times fails with RAMBO_ENOMEM
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto& qq = S->q[sl.kind];
+        for (auto it = sl.members.rbegin(); it != sl.members.rend(); ++it) {
+            if (++it->deferrals <= MAX_DEFERRALS) {
+                qq.push_front(std::move(*it));
+                ++S->n_deferred;
+                continue;
+            }
+            Done d;
+            d.status = RAMBO_ENOMEM;
+            d.latency_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(now - it->t_submit).count();
+            S->done.emplace(it->ticket, std::move(d));
+            --S->outstanding;
+        }
+        sl.members.clear();
+        sl.busy = false;
+        S->backoff_until = now + DEFER_BACKOFF;
+        S->cv_work.notify_one();
+        S->cv_done.notify_all();
+        S->finish_ns += ns_since(t0);
+        return;
+    }
     if (rc == RAMBO_ENOSPC && sl.members.size() > 1) {
         // the batch's answers did not fit the slot: requeue its queries at the
         // front, each to run alone (their order among queries does not matter)
@@ -337,8 +384,9 @@ void worker_main(rambo_server* S) {
         }
         const auto t_adm = Clock::now();
         bool launched = false;
-        for (auto& sl : S->slots)
-            if (!sl.busy && admit(S, sl)) launched = true;
+        if (t_adm >= S->backoff_until)  // (after a pinned-memory refusal, admission pauses briefly)
+            for (auto& sl : S->slots)
+                if (!sl.busy && admit(S, sl)) launched = true;
         if (launched) S->admit_ns += ns_since(t_adm);
         did |= launched;
         if (!did) {
@@ -497,6 +545,7 @@ int rambo_server_stats(rambo_server_t* S, rambo_server_stats_t* out) {
     out->finish_ns = S->finish_ns;
     out->insert_ns = S->insert_ns;
     out->idle_ns = S->idle_ns;
+    out->deferred = S->n_deferred;
     if (!S->latencies.empty()) {
         std::vector<uint64_t> l = S->latencies;
         std::sort(l.begin(), l.end());
@@ -512,8 +561,15 @@ int rambo_server_reset_stats(rambo_server_t* S) {
     std::lock_guard<std::mutex> lk(S->mu);
     S->n_queries = S->n_batches = S->n_inserts = S->keys_done = 0;
     S->admit_ns = S->finish_ns = S->insert_ns = S->idle_ns = 0;
+    S->n_deferred = 0;
     S->latencies.clear();
     S->any = false;
+    return RAMBO_OK;
+}
+
+int rambo_server_inject_alloc_failures(rambo_server_t* S, uint32_t n) {
+    if (!S) return RAMBO_EINVAL;
+    S->inject_alloc_fail.store(n);
     return RAMBO_OK;
 }
 

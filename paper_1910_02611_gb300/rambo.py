@@ -40,7 +40,7 @@ class ServerConfig(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("queries", _u64), ("batches", _u64), ("inserts", _u64), ("keys", _u64), ("seconds", C.c_double),
                 ("p50_ns", _u64), ("p99_ns", _u64), ("max_ns", _u64), ("admit_ns", _u64), ("finish_ns", _u64),
-                ("insert_ns", _u64), ("idle_ns", _u64)]
+                ("insert_ns", _u64), ("idle_ns", _u64), ("deferred", _u64)]
 
 
 class QueryConfig(C.Structure):
@@ -100,6 +100,7 @@ SIGNATURES = {
     "rambo_server_stats": (_i32, [_p, C.POINTER(ServerStats)]),
     "rambo_server_reset_stats": (_i32, [_p]),
     "rambo_server_replay": (_i32, [_p, _p, _p, _p, _p, _u64, _p]),
+    "rambo_server_inject_alloc_failures": (_i32, [_p, _u32]),
     "rambo_server_destroy": (None, [_p]),
     "rambo_autotune": (_i32, [_p, _i32, _p, _p, _u64, _u32, _i32, _i32, C.POINTER(QueryConfig), _p]),
     "rambo_save": (_i32, [_p, C.c_char_p]),
@@ -675,6 +676,12 @@ class Server:
         if rc:
             raise RamboError(rc, "rambo_server_replay")
         return t
+
+    def inject_alloc_failures(self, n: int) -> None:
+        """Refuse the next n pinned allocations for answers (testing the deferral path)."""
+        rc = load_library().rambo_server_inject_alloc_failures(self._s, n)
+        if rc:
+            raise RamboError(rc, "rambo_server_inject_alloc_failures")
 
     def close(self) -> None:
         if getattr(self, "_s", None) is not None and self._s.value:

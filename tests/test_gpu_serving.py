@@ -264,3 +264,42 @@ def test_server_requeues_batches_whose_answers_overflow_the_slot():
             assert np.array_equal(ids, want[i]), i
     assert 0 < n_big < len(ops)
     srv.close()
+
+
+def test_server_defers_batches_when_pinned_memory_is_refused():
+    # Pinned host memory for a batch's answers refused (injected on the host:
+    # the next n allocations fail as if cudaMallocHost had): the batch's
+    # queries are requeued and answered later, identically; a query refused
+    # 64 times fails with RAMBO_ENOMEM; the server keeps serving afterwards.
+    from paper_1910_02611_gb300 import ENOMEM, RamboError
+
+    Rambo, _, _, Server = _mods()
+    rng = np.random.default_rng(9)
+    K = 70_000  # every answer alone (70000 IDs, 280 KB) goes to the pinned pool
+    g = Rambo(K, 64, 2, 1 << 6, 1, 42)  # tiny filters: every key hits every set
+    keys = rng.integers(0, 1 << 62, K * 40, dtype=np.uint64)
+    g.insert(np.arange(K, dtype=np.uint64), keys, np.arange(K + 1, dtype=np.uint64) * np.uint64(40), kind="keys")
+    want, _ = g.query(keys[:1], np.array([0, 1], np.uint64), kind="keys")
+    assert want.size == K
+    srv = Server(g, slots=1, max_batch_queries=64, max_batch_bases=0, max_batch_keys=64, max_batch_ids=1 << 23)
+    try:
+        srv.inject_alloc_failures(3)
+        tickets = [srv.submit(keys[i: i + 1], kind="keys") for i in range(200)]
+        for t in tickets:
+            ids, _ = srv.result(t)
+            assert np.array_equal(ids, want)
+        assert srv.stats()["deferred"] >= 1
+        srv.inject_alloc_failures(1_000_000)
+        tickets = [srv.submit(keys[i: i + 1], kind="keys") for i in range(40)]
+        for t in tickets:
+            with pytest.raises(RamboError) as e:
+                srv.result(t)
+            assert e.value.code == ENOMEM
+        srv.inject_alloc_failures(0)
+        tickets = [srv.submit(keys[i: i + 1], kind="keys") for i in range(40)]
+        for t in tickets:
+            ids, _ = srv.result(t)
+            assert np.array_equal(ids, want)
+    finally:
+        srv.close()
+        g.close()

@@ -393,35 +393,58 @@ def run_ours(args):
         need = max(need, n_ids)
     del probe_ids, probe_off
     out_cap = max(1 << 20, int(need * 1.02) + 1024)
-    out_ids = torch.empty(out_cap, dtype=torch.int32, device=dev)
     out_off = torch.empty(max(len(q) for q in batches) + 1, dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {}  # the direct call's result buffer, allocated when first needed
 
     def one_step(i):
         qd, qo, nk, nq = dev_batches[i % len(dev_batches)]
-        g.query_into(qd, qo, out_ids, out_off[: nq + 1], kind=batches[0].kind, k=w.k)
+        if "ids" not in out:
+            out["ids"] = torch.empty(out_cap, dtype=torch.int32, device=dev)
+        g.query_into(qd, qo, out["ids"], out_off[: nq + 1], kind=batches[0].kind, k=w.k)
         return nk
 
     plans = []
+    n_plans = 0
     if args.api == "plan":
         from paper_1910_02611_gb300 import Plan
         from paper_1910_02611_gb300.rambo import _CudaArray
 
-        # one graph-captured plan per batch, its inputs copied into the plan's
-        # device buffers before the timed region
-        for (qd, qo, nk, nq), q in zip(dev_batches, batches):
-            items = int(q.offsets[-1] - q.offsets[0])
-            plan = Plan(g, q.kind, max_queries=nq, max_items=max(items, 1), max_ids=out_cap, k=w.k)
-            nbytes = items * (8 if q.kind == "keys" else 1)
-            dst = torch.as_tensor(_CudaArray(plan.dev_data_ptr, nbytes, "|u1"), device=dev)
-            dst.copy_(qd.view(torch.uint8)[:nbytes])
-            dst_off = torch.as_tensor(_CudaArray(plan.dev_offsets_ptr, nq + 1, "<i8"), device=dev)
-            dst_off.copy_(qo - qo[0])
-            plans.append((plan, nq, items, nk))
+        # graph-captured plans, one per batch with its inputs copied into the
+        # plan's device buffers before the timed region -- as many as memory
+        # holds (a plan owns its result and staging buffers, device and pinned
+        # host); with fewer plans than batches, each step first copies its
+        # batch's inputs into the plan's device buffers (inside the step)
+        elem = 8 if batches[0].kind == "keys" else 1
+        max_nq = max(len(q) for q in batches)
+        max_items = max(max(int(q.offsets[-1] - q.offsets[0]) for q in batches), 1)
+        stage_words = min(out_cap, max_nq * ((w.K + 31) // 32))
+        dev_per_plan = 4 * (stage_words + out_cap) + max_items * (elem + 1) + 40 * max_nq
+        host_per_plan = 4 * out_cap + max_items * elem + 16 * max_nq
+        free_dev = torch.cuda.mem_get_info(dev)[0]
+        host_avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        n_plans = max(1, min(len(batches), int(0.5 * free_dev // dev_per_plan), int(0.4 * host_avail // host_per_plan)))
+        for j in range(n_plans):
+            plan = Plan(g, batches[0].kind, max_queries=max_nq, max_items=max_items, max_ids=out_cap, k=w.k)
+            dst = torch.as_tensor(_CudaArray(plan.dev_data_ptr, max_items * elem, "|u1"), device=dev)
+            dst_off = torch.as_tensor(_CudaArray(plan.dev_offsets_ptr, max_nq + 1, "<i8"), device=dev)
+            plans.append((plan, dst, dst_off))
+
+        def load_batch(j, i):
+            qd, qo, nk, nq = dev_batches[i % len(dev_batches)]
+            items = int(batches[i % len(batches)].offsets[-1] - batches[i % len(batches)].offsets[0])
+            _, dst, dst_off = plans[j]
+            dst[: items * elem].copy_(qd.view(torch.uint8)[: items * elem])
+            dst_off[: nq + 1].copy_(qo - qo[0])
+            return nq, max(items, 1), nk
+
+        resident = [load_batch(j, j) for j in range(n_plans)]
         torch.cuda.synchronize()
 
         def plan_step(i):
-            plan, nq, items, nk = plans[i % len(plans)]
+            j = i % n_plans
+            nq, items, nk = load_batch(j, i) if n_plans < len(batches) else resident[j]
+            plan = plans[j][0]
             plan.launch_device(nq, items, stream=stream)
             plan.wait(to_host=False, copy=False, stream=stream)
             return nk
@@ -452,7 +475,7 @@ def run_ours(args):
         # counters of this step's batch, and the query kernel's time from CUDA
         # events recorded on the launching stream around it (inside the graph
         # for a plan replay)
-        st = plans[i % len(plans)][0].last_stats() if plans else g.last_query_stats()
+        st = plans[i % n_plans][0].last_stats() if plans else g.last_query_stats()
         probed += st["keys_probed"]
         rows_read += st["rows_read"]
         qk_ms.append(st["query_kernel_ms"])
@@ -465,7 +488,11 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
     qk_timing = "CUDA events recorded by nodes of the replayed graph around the query kernel" if plans else \
         "CUDA events recorded by the library on the call's stream around the query kernel"
-    if plans and not all(x > 0 for x in qk_ms):
+    used_plans = len(plans)
+    for pl in plans:  # their buffers are not needed past the timed region
+        pl[0].close()
+    plans = []
+    if used_plans and not all(x > 0 for x in qk_ms):
         # the graph was captured without its timing nodes: time the same kernel
         # on the same batches through direct calls, after the timed region
         qk_timing = "direct calls of the same batches after the timed region (graph without timing nodes)"
@@ -603,10 +630,11 @@ def run_ours(args):
                         f"{len(batches[0])} {'query sequences' if batches[0].kind == 'seq' else 'key queries'} "
                         f"per step (scale {args.scale})",
             "parallelism": f"replicas x{world} (one index per GPU, disjoint batches)",
-            "api": "CUDA-graph plan replay" if plans else "rambo_query_*_into call",
+            "api": "CUDA-graph plan replay" if used_plans else "rambo_query_*_into call",
             "autotuned": bool(tuned),
             "l2": f"flushed before every step (256 MiB write); index {g.info().index_bytes / 2**30:.1f} GiB",
             "batches": len(batches),
+            "plans": used_plans,
         },
         "batch_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "keys_probed_frac": probed / max(keys, 1),

@@ -212,12 +212,14 @@ int rambo_query_seq_batch_into(rambo_t *h, const uint8_t *bases, const uint64_t 
  * memory budget is fixed up front) -- but can still launch kernels.  It
  * computes exactly what rambo_query_seq_batch_into computes; every pointer
  * (bases, offsets, ids, id_offsets) is device memory owned by the caller.
- * Its working memory (2-bit packed bases, per-query counts and staged IDs)
- * is one array of 30 MiB (31,459,072 bytes) in device global memory on every
- * GPU the library is used on, held until the process exits.  Limits: at most
- * 2^19 queries, 2^25 bases (offsets[n] - offsets[0]) and 4,194,304 result IDs
- * staged per call; larger requests return RAMBO_E2BIG before any kernel runs
- * (results beyond the staging limit are detected after the query kernel and
+ * Its working memory (2-bit packed bases, per-query counts and staged
+ * answers) is one array of 30 MiB (31,459,072 bytes) in device global memory
+ * on every GPU the library is used on, held until the process exits.
+ * Limits: at most 2^19 queries, 2^25 bases (offsets[n] - offsets[0]) and
+ * 4,194,304 staging words per call, where a query's answer takes the smaller
+ * of its ID count and ceil(K/32) words (dense answers are staged as a K-bit
+ * bitmap); larger requests return RAMBO_E2BIG before any kernel runs
+ * (answers beyond the staging limit are detected after the query kernel and
  * also return RAMBO_E2BIG).  rambo_create and rambo_load, which allocate
  * anyway, do the set-up with the handle's device current: they look up the
  * array's device address (cudaGetSymbolAddress, which under lazy module
@@ -287,9 +289,17 @@ int rambo_plan_launches_per_replay(const rambo_plan_t *p);
  * counters come from the batch's own status block).  query_kernel_ms and
  * device_ms come from CUDA events that nodes of the captured graph record
  * around the query kernel and around the whole replay; both are 0 if the
- * graph could not be captured with those nodes. */
+ * batch ran on the graph without those nodes (see rambo_plan_set_timing). */
 struct rambo_query_stats;
 int rambo_plan_last_stats(const rambo_plan_t *p, struct rambo_query_stats *out);
+/* A plan holds two captured graphs of the same work: one with event-record
+ * nodes around the query kernel and the replay (the default; its batches
+ * report query_kernel_ms and device_ms) and one without them, whose replays
+ * start and finish a few microseconds sooner (latency-bound small batches,
+ * the server's plans).  on = 1 selects the first, 0 the second; answers are
+ * identical.  RAMBO_ESTATE while a batch is in flight, RAMBO_ECUDA when the
+ * timed graph could not be captured (the plan then runs the plain one). */
+int rambo_plan_set_timing(rambo_plan_t *p, int on);
 
 /* ---- Continuous-batching server (no counterpart in the paper; uses Sec.
  * 3.1's streaming updates) ----

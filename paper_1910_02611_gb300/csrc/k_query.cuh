@@ -29,8 +29,10 @@
 //          with the fewest hit cells and tests the other tables; "union" ORs
 //          the hit cells' member bitmaps per table and ANDs the tables;
 //   A6     the bitmap is compacted in ascending ID order, with coalesced
-//          stores, into a staging arena (one atomic reservation per query); a
-//          scan + gather then lays the lists out in query order.
+//          stores, into a staging arena (one atomic reservation per query),
+//          or, when the answer holds more IDs than the bitmap has words,
+//          the bitmap itself is staged; a scan + gather then lays the lists
+//          out in query order (expanding staged bitmaps).
 #pragma once
 
 #include "rambo_impl.cuh"
@@ -506,14 +508,25 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                     // compaction: ascending IDs from the bitmap, bitmap cleared.
                     // 32 words (1024 IDs) at a time: lanes expand their word's bits
                     // into shared memory at their prefix position, then the warp
-                    // copies the run out with coalesced stores.
+                    // copies the run out with coalesced stores.  An answer with
+                    // more IDs than bitmap words is staged as the bitmap.
                     for (uint32_t w = lane; w < bw; w += 32) count += __popc(sBits[w]);
                     count = __reduce_add_sync(FULL, count);
-                    if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)count);
+                    // a dense answer is staged as the bitmap (fewer words)
+                    const bool as_bits = count > bw && o.bits_words == bw;
+                    const uint32_t words = as_bits ? bw : count;
+                    if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)words);
                     start = __shfl_sync(FULL, start, 0);
-                    const bool write = count && start + count <= o.stage_cap;
+                    const bool write = count && start + words <= o.stage_cap;
                     uint32_t at = 0;
-                    for (uint32_t w0b = 0; w0b < bw; w0b += 32) {
+                    if (as_bits) {
+                        for (uint32_t w = lane; w < bw; w += 32) {
+                            if (write) o.stage[start + w] = sBits[w];
+                            sBits[w] = 0;
+                        }
+                        start |= QSTART_BITMAP;
+                    }
+                    for (uint32_t w0b = 0; w0b < bw && !as_bits; w0b += 32) {
                         const uint32_t w = w0b + lane;
                         uint32_t bits = (w < bw) ? sBits[w] : 0u;
                         uint32_t c = __popc(bits);
@@ -1047,12 +1060,22 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                             if (p2 < gw) before += c2;
                             count += c2;
                         }
-                        if (leader) *ctl_start = count ? atomicAdd(&st->cursor, (unsigned long long)count) : 0ull;
+                        // a dense answer is staged as the bitmap (fewer words)
+                        const bool as_bits = count > bw && o.bits_words == bw;
+                        const uint32_t words = as_bits ? bw : count;
+                        if (leader) *ctl_start = count ? atomicAdd(&st->cursor, (unsigned long long)words) : 0ull;
                         qk_group_sync(P, gi);
                         start = *ctl_start;
-                        const bool write = count && start + count <= o.stage_cap;
+                        const bool write = count && start + words <= o.stage_cap;
                         uint32_t at = before;
-                        for (uint32_t w0b = wlo; w0b < whi; w0b += 32) {
+                        if (as_bits) {
+                            for (uint32_t w = wlo + lane; w < whi; w += 32) {
+                                if (write) o.stage[start + w] = sBits[w];
+                                sBits[w] = 0;
+                            }
+                            start |= QSTART_BITMAP;
+                        }
+                        for (uint32_t w0b = wlo; w0b < whi && !as_bits; w0b += 32) {
                             const uint32_t w = w0b + lane;
                             uint32_t bits = (w < whi) ? sBits[w] : 0u;
                             uint32_t c = __popc(bits);

@@ -548,31 +548,68 @@ cudaError_t launch_cluster_order(const BatchView& b, uint64_t* keys, uint32_t* h
 }
 
 // ---------------------------------------------------------------------------
-// gather staged result IDs into CSR order: one warp per query
+// gather staged result IDs into CSR order: one warp per query.  A query
+// staged as its K-bit bitmap is expanded 32 words (up to 1024 IDs) at a
+// time: lanes write their word's set bits as IDs into the warp's run in
+// shared memory at their prefix position, then the warp stores the run with
+// coalesced writes.
 
-__global__ void k_gather(QueryOut o, const uint64_t* __restrict__ id_offsets, uint64_t n,
-                         uint32_t* __restrict__ ids, const DevStatus* st, const uint64_t* __restrict__ n_dev,
-                         uint64_t ids_cap) {
+constexpr int GA_THREADS = 256;
+constexpr int GA_RUN = 1024;  // IDs of 32 bitmap words
+
+__global__ void __launch_bounds__(GA_THREADS) k_gather(QueryOut o, const uint64_t* __restrict__ id_offsets, uint64_t n,
+                                                        uint32_t* __restrict__ ids, const DevStatus* st,
+                                                        const uint64_t* __restrict__ n_dev, uint64_t ids_cap) {
+    __shared__ uint32_t s_run[GA_THREADS / 32][GA_RUN];
     if (st->err != NO_ERR || st->cursor > o.stage_cap) return;
     if (n_dev) n = *n_dev;
     if (id_offsets[n] > ids_cap) return;  // the caller sees the total and reports the shortfall
-    const int lane = threadIdx.x & 31;
+    const unsigned lane = threadIdx.x & 31;
+    uint32_t* run = s_run[threadIdx.x >> 5];
     uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t q = warp; q < n; q += nwarps) {
-        uint32_t c = o.qcount[q];
+        const uint32_t c = o.qcount[q];
         if (!c) continue;
-        const uint32_t* src = o.stage + o.qstart[q];
+        const uint64_t s0 = o.qstart[q];
         uint32_t* dst = ids + id_offsets[q];
-        for (uint32_t t = lane; t < c; t += 32) dst[t] = src[t];
+        if (!(s0 & QSTART_BITMAP)) {
+            const uint32_t* src = o.stage + s0;
+            for (uint32_t t = lane; t < c; t += 32) dst[t] = src[t];
+            continue;
+        }
+        const uint32_t* src = o.stage + (s0 & ~QSTART_BITMAP);
+        const uint32_t bw = o.bits_words;
+        uint32_t at = 0;
+        for (uint32_t w0 = 0; w0 < bw; w0 += 32) {
+            const uint32_t w = w0 + lane;
+            uint32_t bits = w < bw ? __ldcs(src + w) : 0u;  // read once
+            const uint32_t cw = __popc(bits);
+            uint32_t incl = cw;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= (unsigned)off) incl += y;
+            }
+            const uint32_t blk = __shfl_sync(0xffffffffu, incl, 31);
+            uint32_t pos = incl - cw;
+            while (bits) {
+                run[pos++] = w * 32 + (__ffs(bits) - 1);
+                bits &= bits - 1;
+            }
+            __syncwarp();
+            for (uint32_t t = lane; t < blk; t += 32) dst[at + t] = run[t];
+            __syncwarp();  // the run is rewritten by the next 32 words
+            at += blk;
+        }
     }
 }
 
 cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_t n, uint32_t* ids,
                           const DevStatus* st, cudaStream_t s, const uint64_t* n_dev, uint64_t ids_cap) {
     if (n == 0) return cudaSuccess;
-    int blocks = grid_for(n * 32, 256, 152 * 16);
-    k_gather<<<blocks, 256, 0, s>>>(o, id_offsets, n, ids, st, n_dev, ids_cap);
+    int blocks = grid_for(n * 32, GA_THREADS, 152 * 16);
+    k_gather<<<blocks, GA_THREADS, 0, s>>>(o, id_offsets, n, ids, st, n_dev, ids_cap);
     return cudaGetLastError();
 }
 

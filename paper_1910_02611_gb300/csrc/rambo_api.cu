@@ -688,7 +688,7 @@ int run_query_pipelined(rambo* h, BatchView b, const void* d_data, int seq, uint
         int ub = 0;
         QueryTuning t{};
         RK(resolve_tuning(h, nc, ub, t));
-        QueryOut oc{h->stage.p, h->stage.cap, h->qstart.p + q_lo[c], h->qcount.p + q_lo[c]};
+        QueryOut oc{h->stage.p, h->stage.cap, h->qstart.p + q_lo[c], h->qcount.p + q_lo[c], stage_bits_words(h->K)};
         if (c) CK(cudaMemsetAsync(&h->st->ticket, 0, sizeof(unsigned long long), s));  // a fresh work queue
         int nl = 0, n_scan = 0;
         CK(launch_query(h->view(), h->hp, bc, oc, t, ub, h->st, s, &nl));
@@ -825,7 +825,7 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
             b.perm = h->perm.p;
             h->launches += 5;
         }
-        QueryOut o{h->stage.p, h->stage.cap, h->qstart.p, h->qcount.p};
+        QueryOut o{h->stage.p, h->stage.cap, h->qstart.p, h->qcount.p, stage_bits_words(h->K)};
         size_t l2_prev = 0;
         if (h->cfg.l2_fetch_bytes) {
             CK(cudaDeviceGetLimit(&l2_prev, cudaLimitMaxL2FetchGranularity));
@@ -856,7 +856,7 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
     CK(cudaEventElapsedTime(&h->last.query_kernel_ms, h->ev[1], h->ev[2]));
     if (d.needed) *d.needed = total_ids;
     if (!d.arena && total_ids > d.ids_cap) return RAMBO_ENOSPC;
-    QueryOut o{h->stage.p, h->stage.cap, h->qstart.p, h->qcount.p};
+    QueryOut o{h->stage.p, h->stage.cap, h->qstart.p, h->qcount.p, stage_bits_words(h->K)};
     if (on_device) {
         uint32_t* d_ids;
         if (!d.arena) {

@@ -286,11 +286,19 @@ __device__ __forceinline__ bool query_batch_rejected(const BatchView& b, DevStat
     return bad_base || *(volatile unsigned long long*)&st->err != NO_ERR;
 }
 
+// A query's answer is staged either as its ascending ID list (count words)
+// or, when that list would be longer than the query's K-bit set bitmap, as
+// the bitmap itself (bits_words words; the gather expands it): dense answers
+// then cross the staging arena in K/8 bytes instead of 4 bytes per ID.
+constexpr uint64_t QSTART_BITMAP = 1ull << 63;  // flag in qstart: staged as a bitmap
+__host__ __device__ inline uint32_t stage_bits_words(uint64_t K) { return (uint32_t)((K + 31) / 32); }
+
 struct QueryOut {
-    uint32_t* stage;       // staged IDs (arena)
-    uint64_t stage_cap;
-    uint64_t* qstart;      // per query: first staged ID
+    uint32_t* stage;       // staging arena (32-bit words)
+    uint64_t stage_cap;    // its capacity in words
+    uint64_t* qstart;      // per query: first staged word (| QSTART_BITMAP when staged as a bitmap)
     uint32_t* qcount;      // per query: number of IDs
+    uint32_t bits_words;   // ceil(K/32) when bitmap staging is allowed, else 0
 };
 
 struct QueryTuning {

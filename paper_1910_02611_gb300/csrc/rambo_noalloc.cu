@@ -29,7 +29,7 @@ namespace {
 // limits of one call
 constexpr uint64_t NA_MAX_QUERIES = 1ull << 19;
 constexpr uint64_t NA_MAX_BASES = 1ull << 25;
-constexpr uint64_t NA_STAGE_IDS = 1ull << 22;
+constexpr uint64_t NA_STAGE_WORDS = 1ull << 22;
 
 constexpr uint64_t align256(uint64_t x) { return (x + 255) / 256 * 256; }
 
@@ -42,7 +42,7 @@ constexpr uint64_t OFF_QCOUNT = align256(OFF_PACKED + NA_PACKED_WORDS * 8);
 constexpr uint64_t OFF_QSTART = align256(OFF_QCOUNT + NA_MAX_QUERIES * 4);
 constexpr uint64_t OFF_SCAN = align256(OFF_QSTART + NA_MAX_QUERIES * 8);
 constexpr uint64_t OFF_STAGE = align256(OFF_SCAN + NA_SCAN_WORDS * 8);
-constexpr uint64_t NA_SCRATCH_BYTES = align256(OFF_STAGE + NA_STAGE_IDS * 4);
+constexpr uint64_t NA_SCRATCH_BYTES = align256(OFF_STAGE + NA_STAGE_WORDS * 4);
 // the size the header states for the array
 static_assert(sizeof(DevStatus) <= 256, "status block fits its 256-byte slot");
 static_assert(NA_SCRATCH_BYTES == 31459072ull, "fixed scratch is the 31,459,072 bytes the header states");
@@ -156,7 +156,7 @@ extern "C" int rambo_query_seq_batch_noalloc(rambo_t* h, const uint8_t* bases, c
     b.packed = packed;
     // validation and packing in one launch (the query kernel reports an unresolved base)
     NA_CK(launch_intake(b, k, ix.K, bases + ends[0], packed, total / 32 + 2, nullptr, st, s));
-    QueryOut o{stage, NA_STAGE_IDS, qstart, qcount};
+    QueryOut o{stage, NA_STAGE_WORDS, qstart, qcount, stage_bits_words(ix.K)};
     NA_CK(launch_query(ix, hp, b, o, t, use_bitmap, st, s));
     NA_CK(launch_scan_counts(qcount, n, id_offsets, scan_tmp, NA_SCAN_WORDS, s));
     DevStatus hst;
@@ -166,7 +166,7 @@ extern "C" int rambo_query_seq_batch_noalloc(rambo_t* h, const uint8_t* bases, c
     NA_CK(cudaStreamSynchronize(s));
     rc = decode(hst.err);
     if (rc) return rc;
-    if (hst.cursor > NA_STAGE_IDS) return RAMBO_E2BIG;
+    if (hst.cursor > NA_STAGE_WORDS) return RAMBO_E2BIG;
     if (needed) *needed = total_ids;
     if (total_ids > ids_cap) return RAMBO_ENOSPC;
     NA_CK(launch_gather(o, id_offsets, n, ids, st, s));

@@ -48,6 +48,7 @@ struct rambo_plan {
     uint32_t k = 31;
     int canon = 0, skipn = 0;
     uint64_t max_q = 0, max_items = 0, max_ids = 0;
+    uint64_t stage_words = 0;  // staging arena: max_ids, or less when dense answers are staged as bitmaps
     int device = 0;
     size_t elem = 1;
     // device
@@ -74,8 +75,11 @@ struct rambo_plan {
     uint64_t* h_id_off = nullptr;
     // graph
     cudaStream_t cap = nullptr;
-    cudaGraph_t graph = nullptr;
+    cudaGraph_t graph = nullptr;        // with the timing nodes (null if they could not be captured)
     cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph_plain = nullptr;  // the same work without them
+    cudaGraphExec_t exec_plain = nullptr;
+    bool use_timed = true;              // rambo_plan_set_timing
     cudaEvent_t ev_done = nullptr;
     // timing events recorded by nodes of the graph itself: replay start,
     // query kernel start and end, replay end (null when not captured)
@@ -96,6 +100,8 @@ void plan_free(rambo_plan* p) {
     cudaSetDevice(p->device);
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->exec_plain) cudaGraphExecDestroy(p->exec_plain);
+    if (p->graph_plain) cudaGraphDestroy(p->graph_plain);
     if (p->ev_done) cudaEventDestroy(p->ev_done);
     for (cudaEvent_t e : p->ev_t)
         if (e) cudaEventDestroy(e);
@@ -148,7 +154,7 @@ int plan_capture(rambo_plan* p, bool timed) {
                           p->kind == 1 ? p->max_items / 32 + 2 : 0, p->d_nmask, p->st, s),
         ++n_launch;
     if (e == cudaSuccess && p->kind == 1 && p->skipn) e = launch_check_windows(b, p->st, s), ++n_launch;
-    QueryOut o{p->stage, p->max_ids, p->qstart, p->qcount};
+    QueryOut o{p->stage, p->stage_words, p->qstart, p->qcount, stage_bits_words(ix.K)};
     if (e == cudaSuccess) e = mark(p, 1, s, timed);
     if (e == cudaSuccess) {
         int nq = 0;
@@ -174,10 +180,11 @@ int plan_capture(rambo_plan* p, bool timed) {
         cudaGetLastError();
         return map_cuda(e != cudaSuccess ? e : e2);
     }
-    p->graph = g;
-    PK(cudaGraphInstantiate(&p->exec, g, 0));
+    cudaGraph_t& graph = timed ? p->graph : p->graph_plain;
+    cudaGraphExec_t& exec = timed ? p->exec : p->exec_plain;
+    graph = g;
+    PK(cudaGraphInstantiate(&exec, g, 0));
     p->launches_per_replay = n_launch;
-    p->timed = timed;
     return RAMBO_OK;
 }
 
@@ -234,6 +241,13 @@ int rambo_plan_create(rambo_t* h, int kind, uint64_t max_queries, uint64_t max_i
     p->max_q = max_queries;
     p->max_items = max_items;
     p->max_ids = max_ids;
+    // a query stages at most ceil(K/32) words when the kernel keeps its set
+    // bitmap (denser answers are staged as the bitmap), never more than its IDs
+    p->stage_words = max_ids;
+    if (ub && !t.wide) {
+        const uint64_t bw = stage_bits_words(ix.K);
+        if (max_queries <= max_ids / bw) p->stage_words = max_queries * bw;
+    }
     p->elem = kind == 0 ? 8 : 1;
     auto fail = [&](int code) {
         plan_free(p);
@@ -247,7 +261,7 @@ int rambo_plan_create(rambo_t* h, int kind, uint64_t max_queries, uint64_t max_i
               cudaMalloc(&p->qcount, max_queries * 4) == cudaSuccess &&
               cudaMalloc(&p->qstart, max_queries * 8) == cudaSuccess &&
               cudaMalloc(&p->scan_tmp, scan_tmp_words(max_queries) * 8) == cudaSuccess &&
-              cudaMalloc(&p->stage, max_ids * 4) == cudaSuccess && cudaMalloc(&p->ids, max_ids * 4) == cudaSuccess &&
+              cudaMalloc(&p->stage, p->stage_words * 4) == cudaSuccess && cudaMalloc(&p->ids, max_ids * 4) == cudaSuccess &&
               cudaMalloc(&p->id_off, (max_queries + 1) * 8) == cudaSuccess &&
               cudaMalloc(&p->d_head, sizeof(PlanHead)) == cudaSuccess &&
               cudaMallocHost(&p->h_data, max_items * p->elem + 16) == cudaSuccess &&
@@ -273,14 +287,17 @@ int rambo_plan_create(rambo_t* h, int kind, uint64_t max_queries, uint64_t max_i
         if (cudaEventCreate(&ev) != cudaSuccess) return fail(RAMBO_ECUDA);
     p->h_desc[0] = 0;
     p->h_desc[1] = 0;
-    // with timing nodes first; a graph without them answers the same
-    rc = plan_capture(p, true);
-    if (rc == RAMBO_ECUDA) {
-        if (p->graph) cudaGraphDestroy(p->graph);
-        p->graph = nullptr;
-        rc = plan_capture(p, false);
-    }
+    // the graph without timing nodes, then the one with them (the default
+    // when it can be captured; both answer the same)
+    rc = plan_capture(p, false);
     if (rc) return fail(rc);
+    if (plan_capture(p, true) != RAMBO_OK) {
+        if (p->exec) cudaGraphExecDestroy(p->exec);
+        if (p->graph) cudaGraphDestroy(p->graph);
+        p->exec = nullptr;
+        p->graph = nullptr;
+        cudaGetLastError();
+    }
     handle_attach_plan(h, p);
     p->attached = true;
     *out = p;
@@ -314,7 +331,8 @@ int rambo_plan_launch(rambo_plan_t* p, uint64_t n_queries, uint64_t n_items, int
         PK(cudaMemcpyAsync(p->d_off, p->h_off, (n_queries + 1) * 8, cudaMemcpyHostToDevice, s));
         if (n_items) PK(cudaMemcpyAsync(p->d_data, p->h_data, n_items * p->elem, cudaMemcpyHostToDevice, s));
     }
-    PK(cudaGraphLaunch(p->exec, s));
+    p->timed = p->use_timed && p->exec;
+    PK(cudaGraphLaunch(p->timed ? p->exec : p->exec_plain, s));
     PK(cudaEventRecord(p->ev_done, s));
     p->launched_n = n_queries;
     p->busy = true;
@@ -353,7 +371,7 @@ int rambo_plan_wait(rambo_plan_t* p, int to_host, const uint32_t** ids, const ui
         PK(cudaEventElapsedTime(&p->last.device_ms, p->ev_t[0], p->ev_t[3]));
     }
     if (n_ids) *n_ids = total;
-    if (st.cursor > p->max_ids || total > p->max_ids) return RAMBO_ENOSPC;
+    if (st.cursor > p->stage_words || total > p->max_ids) return RAMBO_ENOSPC;
     const uint64_t n = p->launched_n;
     if (to_host) {
         cudaStream_t s = (cudaStream_t)stream;
@@ -370,6 +388,14 @@ int rambo_plan_wait(rambo_plan_t* p, int to_host, const uint32_t** ids, const ui
 }
 
 int rambo_plan_launches_per_replay(const rambo_plan_t* p) { return p ? p->launches_per_replay : 0; }
+
+int rambo_plan_set_timing(rambo_plan_t* p, int on) {
+    if (!p || (on != 0 && on != 1)) return RAMBO_EINVAL;
+    if (p->busy) return RAMBO_ESTATE;
+    if (on && !p->exec) return RAMBO_ECUDA;  // the timed graph could not be captured
+    p->use_timed = on != 0;
+    return RAMBO_OK;
+}
 
 int rambo_plan_last_stats(const rambo_plan_t* p, rambo_query_stats_t* out) {
     if (!p || !out) return RAMBO_EINVAL;

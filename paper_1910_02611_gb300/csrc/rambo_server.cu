@@ -438,6 +438,8 @@ int rambo_server_create(rambo_t* h, const rambo_server_config_t* cfg, rambo_serv
             Slot sl;
             sl.kind = kind;
             rc = rambo_plan_create(h, kind, cfg->max_batch_queries, items, cfg->max_batch_ids, cfg->k, &sl.plan);
+            // replays without timing nodes: the server reports latency, not kernel times
+            if (rc == RAMBO_OK) rambo_plan_set_timing(sl.plan, 0);
             if (rc == RAMBO_OK && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess)
                 rc = RAMBO_ECUDA;
             if (rc == RAMBO_OK && cudaMallocHost(&sl.staging, SMALL_RESULT_BYTES) != cudaSuccess) {

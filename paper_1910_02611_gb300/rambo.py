@@ -92,6 +92,7 @@ SIGNATURES = {
     "rambo_plan_wait": (_i32, [_p, _i32, C.POINTER(_p), C.POINTER(_p), C.POINTER(_u64), _p]),
     "rambo_plan_launches_per_replay": (_i32, [_p]),
     "rambo_plan_last_stats": (_i32, [_p, C.POINTER(QueryStats)]),
+    "rambo_plan_set_timing": (_i32, [_p, _i32]),
     "rambo_server_create": (_i32, [_p, C.POINTER(ServerConfig), C.POINTER(_p)]),
     "rambo_server_submit": (_i32, [_p, _i32, _p, _u64, C.POINTER(_u64)]),
     "rambo_server_submit_insert": (_i32, [_p, _i32, _p, _p, _p, _u64, C.POINTER(_u64)]),
@@ -586,6 +587,13 @@ class Plan:
                    else np.zeros(0, np.uint32))
             return ids, offs
         return _device_copy(ids_p.value or 0, total, "<u4"), _device_copy(off_p.value, n + 1, "<u8")
+
+    def set_timing(self, on: bool) -> None:
+        """Replay the graph with (True, default) or without (False) its timing
+        nodes (rambo_plan_set_timing)."""
+        rc = load_library().rambo_plan_set_timing(self._p, int(on))
+        if rc:
+            raise RamboError(rc, "rambo_plan_set_timing")
 
     def last_stats(self) -> dict:
         """Counters and CUDA-event times of the last waited batch (rambo_plan_last_stats)."""

@@ -841,3 +841,62 @@ def test_id_space_beyond_the_shared_memory_bitmap(mods):
     g.set_config(**{**base, "warps_per_query": 8})  # no bitmap: stays one warp per query
     assert_query_equal(g, o, synth.Collection("keys", qd, qo))
     g.close()
+
+
+def test_dense_answers_staged_as_bitmaps(mods):
+    # A query whose answer holds more IDs than its K-bit set bitmap has words
+    # is staged as the bitmap and expanded by the gather; sparser answers are
+    # staged as ID lists.  A batch mixing both (K = 2000: 63 bitmap words, the
+    # last one partial) must equal the oracle through the direct call (one
+    # warp per query, and a whole block per query for a small batch), the
+    # host-output pipeline, device inputs and a captured plan, in every set
+    # stage.
+    import torch
+
+    Rambo, Oracle = mods
+    from paper_1910_02611_gb300 import Plan
+
+    rng = np.random.default_rng(2000)
+    K, B, R, m, eta = 2000, 32, 4, 1 << 14, 2
+    vocab = rng.integers(0, 1 << 62, 400, dtype=np.uint64)
+    pop = 1.0 / np.arange(1, vocab.size + 1) ** 1.1
+    pop /= pop.sum()
+    ids = np.sort(rng.choice(K, 1900, replace=False)).astype(np.uint64)  # 100 IDs never inserted
+    sets = [np.unique(vocab[rng.choice(vocab.size, int(rng.integers(5, 60)), p=pop)]) for _ in ids]
+    data = np.concatenate(sets)
+    off = np.zeros(ids.size + 1, np.uint64)
+    np.cumsum([s.size for s in sets], out=off[1:])
+    g = Rambo(K, B, R, m, eta, 5)
+    o = Oracle(K, B, R, m, eta, 5)
+    g.insert(ids, data, off, kind="keys")
+    o.insert_keys_batch(ids, data, off)
+    n = 70_000  # above the host pipeline's threshold
+    nt = rng.integers(1, 3, n)
+    qo = np.zeros(n + 1, np.uint64)
+    np.cumsum(nt, out=qo[1:])
+    qd = vocab[rng.integers(0, vocab.size, int(qo[-1]))]
+    rids, roff = o.query_batch("keys", qd, qo)
+    cnt = np.diff(roff.astype(np.int64))
+    bw = (K + 31) // 32
+    assert (cnt > bw).sum() > 1000 and ((cnt > 0) & (cnt <= bw)).sum() > 1000  # both staging forms occur
+    base = g.get_config()
+    try:
+        for stage in (0, 1, 2, 3):
+            g.set_config(**{**base, "set_stage": stage})
+            ids_h, off_h = g.query(qd, qo, kind="keys")  # host output: chunked pipeline
+            assert np.array_equal(off_h, roff) and np.array_equal(ids_h, rids)
+            ids_d, off_d = g.query(torch.from_numpy(qd.view(np.int64)).cuda(),
+                                   torch.from_numpy(qo.view(np.int64)).cuda(), kind="keys")
+            assert np.array_equal(off_d.cpu().numpy().view(np.uint64), roff)
+            assert np.array_equal(ids_d.cpu().numpy().view(np.uint32), rids)
+            sub = synth.Collection("keys", qd[: int(qo[6])], qo[:7])  # a block of warps per query
+            assert_query_equal(g, o, sub)
+    finally:
+        g.set_config(**base)
+    nq = 5000
+    plan = Plan(g, "keys", nq, int(qo[nq]), int(roff[nq]) + 1024)
+    plan.launch_host(qd[: int(qo[nq])], qo[: nq + 1])
+    ids_p, off_p = plan.wait()
+    assert np.array_equal(off_p, roff[: nq + 1]) and np.array_equal(ids_p, rids[: int(roff[nq])])
+    plan.close()
+    g.close()

@@ -40,13 +40,22 @@ def test_plan_replays_match_query_calls():
     # descriptor copy)
     assert plan.launches_per_replay == 5
     rng = np.random.default_rng(3)
-    for n in (1, 37, 600, 250):
+    for n, timed in ((1, True), (37, False), (600, True), (250, False), (250, True)):
+        # the graph with timing nodes reports the query kernel's time; the
+        # one without them reports none; both answer the same
+        plan.set_timing(timed)
         idx = rng.choice(len(w.queries), n, replace=False)
         q = w.queries.subset(idx)
         plan.launch_host(q.data, q.offsets)
         ids, off = plan.wait(to_host=True)
         rids, roff = o.query_batch("seq", q.data, q.offsets, k=31)
         assert np.array_equal(off, roff) and np.array_equal(ids, rids)
+        st = plan.last_stats()
+        assert (st["query_kernel_ms"] > 0) == timed and (st["device_ms"] > 0) == timed
+        assert st["n_results"] == int(roff[-1]) and st["n_queries"] == n
+    with pytest.raises(RamboError) as e:
+        plan.set_timing(2)
+    assert e.value.code == EINVAL
     # device-side inputs written straight into the plan's buffers
     q = w.queries.subset(np.arange(100))
     dd = torch.from_numpy(q.data).cuda()

@@ -101,9 +101,10 @@ def test_noalloc_large_batch_takes_the_multi_pass_scan():
     g.close()
 
 
-def test_noalloc_reports_e2big_when_staged_ids_exceed_its_limit():
-    # an index whose filters are all ones answers every query with every set:
-    # 1100 queries x 4096 sets = 4,505,600 IDs > the 4,194,304 staging limit
+def test_noalloc_reports_e2big_when_staged_answers_exceed_its_limit():
+    # an index whose filters are all ones answers every query with every set;
+    # such dense answers are staged as K-bit bitmaps (4096 sets: 128 words a
+    # query), so 40,000 queries stage 5,120,000 words > the 4,194,304-word limit
     import torch
 
     from paper_1910_02611_gb300 import E2BIG, Rambo, RamboError
@@ -115,17 +116,21 @@ def test_noalloc_reports_e2big_when_staged_ids_exceed_its_limit():
     sets = synth.random_bases(rng, K * 300)
     off = np.arange(K + 1, dtype=np.uint64) * np.uint64(300)
     g.insert(np.arange(K, dtype=np.uint64), sets, off, kind="seq", k=31)
-    qb = synth.random_bases(rng, 1100 * 31)
+    nq = 40_000
+    qb = synth.random_bases(rng, nq * 31)
     qd = torch.from_numpy(qb).to(dev)
-    qo = torch.from_numpy((np.arange(1101, dtype=np.int64) * 31)).to(dev)
-    ids = torch.empty(1 << 23, dtype=torch.int32, device=dev)
-    out_off = torch.empty(1101, dtype=torch.int64, device=dev)
+    qo = torch.from_numpy((np.arange(nq + 1, dtype=np.int64) * 31)).to(dev)
+    ids = torch.empty(nq * K, dtype=torch.int32, device=dev)
+    out_off = torch.empty(nq + 1, dtype=torch.int64, device=dev)
     n_ref = g.query_into(qd, qo, ids, out_off, kind="seq", k=31)
-    assert n_ref == 1100 * K
+    assert n_ref == nq * K
     with pytest.raises(RamboError) as e:
         g.query_seq_noalloc(qd, qo, ids, out_off, k=31)
     assert e.value.code == E2BIG
-    # a batch within the limit still answers, after the failed call
-    n = g.query_seq_noalloc(qd[: 1000 * 31], qo[:1001], ids, out_off[:1001], k=31)
-    assert n == 1000 * K
+    # a batch within the limit (32,000 x 128 words) still answers, after the failed call
+    n_ok = 32_000
+    n = g.query_seq_noalloc(qd[: n_ok * 31], qo[: n_ok + 1], ids, out_off[: n_ok + 1], k=31)
+    assert n == n_ok * K
+    assert torch.equal(out_off[: n_ok + 1].cpu(), torch.arange(n_ok + 1, dtype=torch.int64) * K)
+    assert torch.equal(ids[:n].view(n_ok, K).cpu(), torch.arange(K, dtype=torch.int32).expand(n_ok, K))
     g.close()

@@ -84,6 +84,10 @@ def parse_args():
                          "(profiling runs: the autotuner's timings under a profiler are not the run's)")
     ap.add_argument("--api", choices=["call", "plan"], default="plan",
                     help="timed step through rambo_query_*_into (call) or a replayed CUDA-graph plan (plan)")
+    ap.add_argument("--plan-timing", action=argparse.BooleanOptionalAction, default=True,
+                    help="replay the plan graph with its event-record nodes around the query kernel (the kernel's "
+                         "time live in the timed region); without them a replay finishes a few microseconds "
+                         "sooner and the kernel is timed by direct calls after the timed region")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -426,6 +430,7 @@ def run_ours(args):
         n_plans = max(1, min(len(batches), int(0.5 * free_dev // dev_per_plan), int(0.4 * host_avail // host_per_plan)))
         for j in range(n_plans):
             plan = Plan(g, batches[0].kind, max_queries=max_nq, max_items=max_items, max_ids=out_cap, k=w.k)
+            plan.set_timing(args.plan_timing)
             dst = torch.as_tensor(_CudaArray(plan.dev_data_ptr, max_items * elem, "|u1"), device=dev)
             dst_off = torch.as_tensor(_CudaArray(plan.dev_offsets_ptr, max_nq + 1, "<i8"), device=dev)
             plans.append((plan, dst, dst_off))
@@ -495,7 +500,8 @@ def run_ours(args):
     if used_plans and not all(x > 0 for x in qk_ms):
         # the graph was captured without its timing nodes: time the same kernel
         # on the same batches through direct calls, after the timed region
-        qk_timing = "direct calls of the same batches after the timed region (graph without timing nodes)"
+        qk_timing = ("direct calls of the same batches after the timed region (graph replayed without timing "
+                     "nodes)")
         qk_ms, probed, rows_read, n_ids = [], 0, 0, 0
         for i in range(args.steps):
             flush.zero_()
@@ -635,6 +641,7 @@ def run_ours(args):
             "l2": f"flushed before every step (256 MiB write); index {g.info().index_bytes / 2**30:.1f} GiB",
             "batches": len(batches),
             "plans": used_plans,
+            "plan_timing_nodes": bool(used_plans and args.plan_timing),
         },
         "batch_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "keys_probed_frac": probed / max(keys, 1),

@@ -574,16 +574,33 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(QueryOut o, const uint64_
         const uint64_t s0 = o.qstart[q];
         uint32_t* dst = ids + id_offsets[q];
         if (!(s0 & QSTART_BITMAP)) {
+            // an ID list: four independent loads in flight per lane
             const uint32_t* src = o.stage + s0;
-            for (uint32_t t = lane; t < c; t += 32) dst[t] = src[t];
+            uint32_t t = lane;
+            for (; t + 96 < c; t += 128) {
+                const uint32_t a0 = __ldcs(src + t), a1 = __ldcs(src + t + 32);
+                const uint32_t a2 = __ldcs(src + t + 64), a3 = __ldcs(src + t + 96);
+                dst[t] = a0;
+                dst[t + 32] = a1;
+                dst[t + 64] = a2;
+                dst[t + 96] = a3;
+            }
+            for (; t < c; t += 32) dst[t] = __ldcs(src + t);
             continue;
         }
+        // a bitmap, 32 words at a time; the words of the next two steps are
+        // loaded ahead so their latency overlaps the expansion of this one
         const uint32_t* src = o.stage + (s0 & ~QSTART_BITMAP);
         const uint32_t bw = o.bits_words;
+        uint32_t cur = lane < bw ? __ldcs(src + lane) : 0u;
+        uint32_t nx1 = 32 + lane < bw ? __ldcs(src + 32 + lane) : 0u;
         uint32_t at = 0;
         for (uint32_t w0 = 0; w0 < bw; w0 += 32) {
             const uint32_t w = w0 + lane;
-            uint32_t bits = w < bw ? __ldcs(src + w) : 0u;  // read once
+            const uint32_t nx2 = w + 64 < bw ? __ldcs(src + w + 64) : 0u;
+            uint32_t bits = cur;
+            cur = nx1;
+            nx1 = nx2;
             const uint32_t cw = __popc(bits);
             uint32_t incl = cw;
 #pragma unroll

@@ -487,6 +487,13 @@ typedef struct rambo_query_config {
                                * many chunks whose answers are copied while the
                                * next ones compute; 0 = automatic (4), 1 = one
                                * piece, copied at the end; at most 8 */
+    uint32_t answer_staging;  /* how a query's answer waits in the staging
+                               * arena before it is laid out in query order:
+                               * 0 = automatic (as its K-bit set bitmap when it
+                               * holds more IDs than the bitmap has 32-bit
+                               * words, else as its ID list); 1 = always as
+                               * the ID list; f = 2..64: as the bitmap only
+                               * when it holds more than f times that many IDs */
 } rambo_query_config_t;
 
 int rambo_get_query_config(const rambo_t *h, rambo_query_config_t *out);

@@ -513,7 +513,7 @@ __device__ __forceinline__ void qk_warp_queries(const IndexView& ix, const HashP
                     for (uint32_t w = lane; w < bw; w += 32) count += __popc(sBits[w]);
                     count = __reduce_add_sync(FULL, count);
                     // a dense answer is staged as the bitmap (fewer words)
-                    const bool as_bits = count > bw && o.bits_words == bw;
+                    const bool as_bits = count > o.bits_min && o.bits_words == bw;
                     const uint32_t words = as_bits ? bw : count;
                     if (lane == 0 && count) start = atomicAdd(&st->cursor, (unsigned long long)words);
                     start = __shfl_sync(FULL, start, 0);
@@ -1061,7 +1061,7 @@ __global__ void __launch_bounds__(QK_THREADS_MAX,
                             count += c2;
                         }
                         // a dense answer is staged as the bitmap (fewer words)
-                        const bool as_bits = count > bw && o.bits_words == bw;
+                        const bool as_bits = count > o.bits_min && o.bits_words == bw;
                         const uint32_t words = as_bits ? bw : count;
                         if (leader) *ctl_start = count ? atomicAdd(&st->cursor, (unsigned long long)words) : 0ull;
                         qk_group_sync(P, gi);

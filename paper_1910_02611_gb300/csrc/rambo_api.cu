@@ -300,6 +300,7 @@ void default_config(rambo* h) {
     h->cfg.row_load = 7;
     h->cfg.warps_per_query = 0;
     h->cfg.host_chunks = 0;
+    h->cfg.answer_staging = 0;
 }
 
 int decode_err(rambo* h, unsigned long long e) {
@@ -541,6 +542,7 @@ int resolve_tuning(rambo* h, uint64_t n, int& use_bitmap, QueryTuning& t) {
     t.set_stage = (int)h->cfg.set_stage;
     t.order = (int)h->cfg.visit_order;
     t.load_kind = (int)h->cfg.row_load;
+    t.staging = h->cfg.answer_staging;
     t.group = (int)h->cfg.warps_per_query;
     use_bitmap = (h->mem_off && t.set_stage != 1 && (h->K + 31) / 32 <= 4096) ? 1 : 0;
     const size_t spw_bytes = (size_t)query_smem_words_per_warp(h->R, h->S, h->K, use_bitmap) * 4;
@@ -688,7 +690,8 @@ int run_query_pipelined(rambo* h, BatchView b, const void* d_data, int seq, uint
         int ub = 0;
         QueryTuning t{};
         RK(resolve_tuning(h, nc, ub, t));
-        QueryOut oc{h->stage.p, h->stage.cap, h->qstart.p + q_lo[c], h->qcount.p + q_lo[c], stage_bits_words(h->K)};
+        QueryOut oc{h->stage.p, h->stage.cap, h->qstart.p + q_lo[c], h->qcount.p + q_lo[c], 0, 0};
+        set_staging(oc, h->K, h->cfg.answer_staging);
         if (c) CK(cudaMemsetAsync(&h->st->ticket, 0, sizeof(unsigned long long), s));  // a fresh work queue
         int nl = 0, n_scan = 0;
         CK(launch_query(h->view(), h->hp, bc, oc, t, ub, h->st, s, &nl));
@@ -825,7 +828,8 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
             b.perm = h->perm.p;
             h->launches += 5;
         }
-        QueryOut o{h->stage.p, h->stage.cap, h->qstart.p, h->qcount.p, stage_bits_words(h->K)};
+        QueryOut o{h->stage.p, h->stage.cap, h->qstart.p, h->qcount.p, 0, 0};
+        set_staging(o, h->K, h->cfg.answer_staging);
         size_t l2_prev = 0;
         if (h->cfg.l2_fetch_bytes) {
             CK(cudaDeviceGetLimit(&l2_prev, cudaLimitMaxL2FetchGranularity));
@@ -856,7 +860,8 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
     CK(cudaEventElapsedTime(&h->last.query_kernel_ms, h->ev[1], h->ev[2]));
     if (d.needed) *d.needed = total_ids;
     if (!d.arena && total_ids > d.ids_cap) return RAMBO_ENOSPC;
-    QueryOut o{h->stage.p, h->stage.cap, h->qstart.p, h->qcount.p, stage_bits_words(h->K)};
+    QueryOut o{h->stage.p, h->stage.cap, h->qstart.p, h->qcount.p, 0, 0};
+    set_staging(o, h->K, h->cfg.answer_staging);
     if (on_device) {
         uint32_t* d_ids;
         if (!d.arena) {
@@ -1312,6 +1317,7 @@ int rambo_set_query_config(rambo_t* h, const rambo_query_config_t* cfg) {
     if (cfg->l2_fetch_bytes && cfg->l2_fetch_bytes != 32 && cfg->l2_fetch_bytes != 64 && cfg->l2_fetch_bytes != 128)
         return RAMBO_EINVAL;
     if (cfg->host_chunks > (uint32_t)PIPE_MAX_CHUNKS) return RAMBO_EINVAL;
+    if (cfg->answer_staging > 64) return RAMBO_EINVAL;
     h->cfg = *cfg;
     return RAMBO_OK;
 }
@@ -1337,6 +1343,7 @@ int rambo_list_query_configs(const rambo_t* h, rambo_query_config_t* out, int ca
                 out[n].row_load = h->cfg.row_load;
                 out[n].warps_per_query = 0;
                 out[n].host_chunks = h->cfg.host_chunks;
+                out[n].answer_staging = h->cfg.answer_staging;
             }
             ++n;
         }
@@ -1392,6 +1399,7 @@ int rambo_autotune(rambo_t* h, int kind, const void* data, const uint64_t* offse
             cfg.row_load = keep.row_load;
             cfg.warps_per_query = keep.warps_per_query;
             cfg.host_chunks = keep.host_chunks;
+            cfg.answer_staging = keep.answer_staging;
             if (rambo_set_query_config(h, &cfg) != RAMBO_OK) continue;
             float t_min = -1.0f;
             for (int r = 0; r < reps; ++r) {

@@ -299,7 +299,22 @@ struct QueryOut {
     uint64_t* qstart;      // per query: first staged word (| QSTART_BITMAP when staged as a bitmap)
     uint32_t* qcount;      // per query: number of IDs
     uint32_t bits_words;   // ceil(K/32) when bitmap staging is allowed, else 0
+    uint32_t bits_min;     // an answer of more IDs than this is staged as the bitmap
 };
+
+// Staging form for an ID space of K sets: staging 0 = bitmap above ceil(K/32)
+// IDs, 1 = ID lists only, f >= 2 = bitmap above f * ceil(K/32) IDs.  A query
+// then stages at most bits_min words.
+inline void set_staging(QueryOut& o, uint64_t K, uint32_t staging) {
+    if (staging == 1) {
+        o.bits_words = 0;
+        o.bits_min = 0xffffffffu;
+        return;
+    }
+    o.bits_words = stage_bits_words(K);
+    const uint64_t m = (uint64_t)o.bits_words * (staging >= 2 ? staging : 1);
+    o.bits_min = m > 0xffffffffull ? 0xffffffffu : (uint32_t)m;
+}
 
 struct QueryTuning {
     int V, G;              // words per lane, lanes per key
@@ -313,6 +328,7 @@ struct QueryTuning {
     int blocks_group;      // grid of the grouped instance (0: not used)
     unsigned long long group_warps;  // its warps, the budget the group size is chosen against
     int wide;              // 1: the block-per-query kernel (R > RF or rows wider than FAST_MAX_S words)
+    uint32_t staging;      // answer staging form (see set_staging)
 };
 
 // ---------------------------------------------------------------------------

@@ -156,7 +156,8 @@ extern "C" int rambo_query_seq_batch_noalloc(rambo_t* h, const uint8_t* bases, c
     b.packed = packed;
     // validation and packing in one launch (the query kernel reports an unresolved base)
     NA_CK(launch_intake(b, k, ix.K, bases + ends[0], packed, total / 32 + 2, nullptr, st, s));
-    QueryOut o{stage, NA_STAGE_WORDS, qstart, qcount, stage_bits_words(ix.K)};
+    QueryOut o{stage, NA_STAGE_WORDS, qstart, qcount, 0, 0};
+    set_staging(o, ix.K, t.staging);
     NA_CK(launch_query(ix, hp, b, o, t, use_bitmap, st, s));
     NA_CK(launch_scan_counts(qcount, n, id_offsets, scan_tmp, NA_SCAN_WORDS, s));
     DevStatus hst;

@@ -49,6 +49,7 @@ struct rambo_plan {
     int canon = 0, skipn = 0;
     uint64_t max_q = 0, max_items = 0, max_ids = 0;
     uint64_t stage_words = 0;  // staging arena: max_ids, or less when dense answers are staged as bitmaps
+    uint32_t staging = 0;      // answer staging form at creation (see set_staging)
     int device = 0;
     size_t elem = 1;
     // device
@@ -154,7 +155,8 @@ int plan_capture(rambo_plan* p, bool timed) {
                           p->kind == 1 ? p->max_items / 32 + 2 : 0, p->d_nmask, p->st, s),
         ++n_launch;
     if (e == cudaSuccess && p->kind == 1 && p->skipn) e = launch_check_windows(b, p->st, s), ++n_launch;
-    QueryOut o{p->stage, p->stage_words, p->qstart, p->qcount, stage_bits_words(ix.K)};
+    QueryOut o{p->stage, p->stage_words, p->qstart, p->qcount, 0, 0};
+    set_staging(o, ix.K, p->staging);
     if (e == cudaSuccess) e = mark(p, 1, s, timed);
     if (e == cudaSuccess) {
         int nq = 0;
@@ -244,9 +246,11 @@ int rambo_plan_create(rambo_t* h, int kind, uint64_t max_queries, uint64_t max_i
     // a query stages at most ceil(K/32) words when the kernel keeps its set
     // bitmap (denser answers are staged as the bitmap), never more than its IDs
     p->stage_words = max_ids;
+    p->staging = t.staging;
     if (ub && !t.wide) {
-        const uint64_t bw = stage_bits_words(ix.K);
-        if (max_queries <= max_ids / bw) p->stage_words = max_queries * bw;
+        QueryOut form{};
+        set_staging(form, ix.K, t.staging);
+        if (form.bits_words && max_queries <= max_ids / form.bits_min) p->stage_words = max_queries * form.bits_min;
     }
     p->elem = kind == 0 ? 8 : 1;
     auto fail = [&](int code) {

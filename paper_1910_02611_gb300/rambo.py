@@ -46,7 +46,8 @@ class ServerStats(C.Structure):
 class QueryConfig(C.Structure):
     _fields_ = [("lanes_per_key", _u32), ("words_per_lane", _u32), ("warps_per_block", _u32),
                 ("blocks_per_sm", _u32), ("set_stage", _u32), ("visit_order", _u32), ("l2_fetch_bytes", _u32),
-                ("cluster", _u32), ("row_load", _u32), ("warps_per_query", _u32), ("host_chunks", _u32)]
+                ("cluster", _u32), ("row_load", _u32), ("warps_per_query", _u32), ("host_chunks", _u32),
+                ("answer_staging", _u32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

@@ -881,8 +881,9 @@ def test_dense_answers_staged_as_bitmaps(mods):
     assert (cnt > bw).sum() > 1000 and ((cnt > 0) & (cnt <= bw)).sum() > 1000  # both staging forms occur
     base = g.get_config()
     try:
-        for stage in (0, 1, 2, 3):
-            g.set_config(**{**base, "set_stage": stage})
+        # staging 0: bitmaps above 63 IDs; 1: ID lists only; 3: bitmaps above 189 IDs
+        for stage, staging in ((0, 0), (1, 0), (2, 0), (3, 0), (0, 1), (2, 3)):
+            g.set_config(**{**base, "set_stage": stage, "answer_staging": staging})
             ids_h, off_h = g.query(qd, qo, kind="keys")  # host output: chunked pipeline
             assert np.array_equal(off_h, roff) and np.array_equal(ids_h, rids)
             ids_d, off_d = g.query(torch.from_numpy(qd.view(np.int64)).cuda(),
@@ -894,9 +895,17 @@ def test_dense_answers_staged_as_bitmaps(mods):
     finally:
         g.set_config(**base)
     nq = 5000
-    plan = Plan(g, "keys", nq, int(qo[nq]), int(roff[nq]) + 1024)
-    plan.launch_host(qd[: int(qo[nq])], qo[: nq + 1])
-    ids_p, off_p = plan.wait()
-    assert np.array_equal(off_p, roff[: nq + 1]) and np.array_equal(ids_p, rids[: int(roff[nq])])
-    plan.close()
+    for staging in (0, 1, 3):
+        g.set_config(**{**base, "answer_staging": staging})
+        plan = Plan(g, "keys", nq, int(qo[nq]), int(roff[nq]) + 1024)
+        plan.launch_host(qd[: int(qo[nq])], qo[: nq + 1])
+        ids_p, off_p = plan.wait()
+        assert np.array_equal(off_p, roff[: nq + 1]) and np.array_equal(ids_p, rids[: int(roff[nq])])
+        plan.close()
+    g.set_config(**base)
+    from paper_1910_02611_gb300 import EINVAL, RamboError
+
+    with pytest.raises(RamboError) as e:
+        g.set_config(**{**base, "answer_staging": 65})
+    assert e.value.code == EINVAL
     g.close()

@@ -30,27 +30,46 @@ __device__ __forceinline__ uint64_t bk_find_item(const uint64_t* __restrict__ of
     return lo;
 }
 
+// Window of global row g.  With magic != 0 (all rows below 2^32, set by the
+// launcher) the quotient is the high word of magic * g, magic = ceil(2^64 /
+// rows_per_win): exact for every 32-bit g and divisor (Lemire, Kaser and
+// Kurz, "Faster remainder by direct computation", 2019).
+__device__ __forceinline__ uint32_t bk_window(uint64_t g, uint64_t rows_per_win, uint64_t magic) {
+    return magic ? (uint32_t)__umul64hi(magic, g) : (uint32_t)(g / rows_per_win);
+}
+
 // Scatter: each step, thread i of the block takes kt consecutive key
-// positions starting at p0 + i*kt, stages its records in shared memory; the
-// block counts them per window, reserves each window's share of its bucket
-// with one atomic, and writes them there.  A bucket that would overflow sets
-// *overflow instead (the caller then builds the batch another way).
+// positions starting at p0 + i*kt and stages their records (with their
+// windows) in shared memory.  The block counts the records per window, scans
+// the counts into block-local offsets, reserves each window's share of its
+// bucket with one atomic, and places every record at its window's offset in
+// a second shared array, so the records leave for their buckets as runs of
+// consecutive words (coalesced stores).  A bucket that would overflow sets
+// *overflow instead (the caller then files the chunk again).
 __global__ void __launch_bounds__(BK_THREADS) k_bucket_scatter(IndexView ix, HashParams hp, BatchView b,
                                                                 uint64_t p_lo, uint64_t p_hi, uint32_t kt,
-                                                                uint64_t rows_per_win, uint32_t n_win,
+                                                                uint64_t rows_per_win, uint64_t magic, uint32_t n_win,
                                                                 uint64_t cap, uint32_t* __restrict__ rec,
                                                                 unsigned long long* __restrict__ fill,
                                                                 unsigned long long* overflow, const DevStatus* st) {
     extern __shared__ __align__(16) unsigned char bk_smem[];
-    uint32_t* s_rec = reinterpret_cast<uint32_t*>(bk_smem);                       // [BK_TILE_RECORDS]
-    uint16_t* s_win = reinterpret_cast<uint16_t*>(s_rec + BK_TILE_RECORDS);       // [BK_TILE_RECORDS]
-    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_win + BK_TILE_RECORDS);       // [n_win]
-    unsigned long long* s_base = reinterpret_cast<unsigned long long*>(s_cnt + ((n_win + 1) & ~1u));  // [n_win]
+    uint32_t* s_rec = reinterpret_cast<uint32_t*>(bk_smem);                       // [BK_TILE_RECORDS] staged
+    uint32_t* s_srt = s_rec + BK_TILE_RECORDS;                                     // [BK_TILE_RECORDS] by window
+    unsigned long long* s_base = reinterpret_cast<unsigned long long*>(s_srt + BK_TILE_RECORDS);  // [n_win]
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_base + n_win);                // [n_win]
+    uint32_t* s_off = s_cnt + n_win;                                               // [n_win]
+    uint32_t* s_wsum = s_off + n_win;                                              // [BK_THREADS / 32]
+    uint16_t* s_win = reinterpret_cast<uint16_t*>(s_wsum + BK_THREADS / 32);       // [BK_TILE_RECORDS] staged
+    uint16_t* s_swin = s_win + BK_TILE_RECORDS;                                    // [BK_TILE_RECORDS] by window
     if (st->err != NO_ERR) return;
     const uint32_t R = ix.R, eta = ix.eta;
     const uint32_t per_key = R * eta;
     const uint32_t slots = kt * per_key;  // records a thread stages per step
     const uint64_t span = (uint64_t)kt * blockDim.x;
+    const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // each thread scans a contiguous run of the window counters
+    const uint32_t wper = (n_win + blockDim.x - 1) / blockDim.x;
+    const uint32_t wlo = min(n_win, threadIdx.x * wper), whi = min(n_win, wlo + wper);
     for (uint64_t p0 = p_lo + blockIdx.x * span; p0 < p_hi; p0 += (uint64_t)gridDim.x * span) {
         for (uint32_t w = threadIdx.x; w < n_win; w += blockDim.x) s_cnt[w] = 0;
         // this thread's keys: positions q0 .. q0 + kt
@@ -62,7 +81,7 @@ __global__ void __launch_bounds__(BK_THREADS) k_bucket_scatter(IndexView ix, Has
         // each lane walks forward from it to its own
         const uint64_t wq0 = p0 + (uint64_t)(threadIdx.x & ~31u) * kt;
         uint64_t t = 0;
-        if ((threadIdx.x & 31) == 0 && wq0 < p_hi) t = bk_find_item(b.offsets, b.n, wq0 + b.off0);
+        if (lane == 0 && wq0 < p_hi) t = bk_find_item(b.offsets, b.n, wq0 + b.off0);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (q0 < p_hi) {
             uint64_t t_end = __ldg(b.offsets + t + 1) - b.off0;
@@ -88,7 +107,7 @@ __global__ void __launch_bounds__(BK_THREADS) k_bucket_scatter(IndexView ix, Has
                     const uint32_t cell = ph[r];
                     for (uint32_t j = 0; j < eta; ++j) {
                         const uint64_t g = (uint64_t)r * ix.m + ((hp.s[r][j] * y) >> ix.shift);  // global row
-                        const uint32_t win = (uint32_t)(g / rows_per_win);
+                        const uint32_t win = bk_window(g, rows_per_win, magic);
                         const uint64_t row_in = g - (uint64_t)win * rows_per_win;
                         my_rec[nrec] = (uint32_t)(((row_in * ix.S + (cell >> 5)) << 5) | (cell & 31));
                         my_win[nrec] = (uint16_t)win;
@@ -100,16 +119,42 @@ __global__ void __launch_bounds__(BK_THREADS) k_bucket_scatter(IndexView ix, Has
         __syncthreads();
         for (uint32_t i = 0; i < nrec; ++i) atomicAdd(&s_cnt[my_win[i]], 1u);
         __syncthreads();
-        for (uint32_t w = threadIdx.x; w < n_win; w += blockDim.x) {
+        // block-local exclusive offsets of the windows, and each window's
+        // share of its bucket reserved with one atomic
+        uint32_t run = 0;
+        for (uint32_t w = wlo; w < whi; ++w) run += s_cnt[w];
+        uint32_t incl = run;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= (unsigned)off) incl += y;
+        }
+        if (lane == 31) s_wsum[wid] = incl;
+        __syncthreads();
+        uint32_t before = incl - run;
+        for (unsigned v = 0; v < wid; ++v) before += s_wsum[v];
+        for (uint32_t w = wlo; w < whi; ++w) {
             const uint32_t c = s_cnt[w];
+            s_off[w] = before;
+            before += c;
             s_base[w] = c ? atomicAdd(fill + w, (unsigned long long)c) : 0ull;
             s_cnt[w] = 0;  // reused as the running slot of each window
         }
         __syncthreads();
+        uint32_t total = 0;
+        for (unsigned v = 0; v < BK_THREADS / 32; ++v) total += s_wsum[v];
         for (uint32_t i = 0; i < nrec; ++i) {
             const uint32_t w = my_win[i];
-            const unsigned long long at = s_base[w] + atomicAdd(&s_cnt[w], 1u);
-            if (at < cap) rec[(uint64_t)w * cap + at] = my_rec[i];
+            const uint32_t at = s_off[w] + atomicAdd(&s_cnt[w], 1u);
+            s_srt[at] = my_rec[i];
+            s_swin[at] = (uint16_t)w;
+        }
+        __syncthreads();
+        // runs of one window's records go out as consecutive words
+        for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
+            const uint32_t w = s_swin[i];
+            const unsigned long long at = s_base[w] + (i - s_off[w]);
+            if (at < cap) rec[(uint64_t)w * cap + at] = s_srt[i];
             else *overflow = 1;
         }
         __syncthreads();  // staging and counters are rewritten by the next step
@@ -131,7 +176,9 @@ __global__ void __launch_bounds__(BK_THREADS) k_bucket_apply(uint32_t* __restric
 }
 
 size_t bucket_scatter_smem(uint32_t n_win) {
-    return (size_t)BK_TILE_RECORDS * 6 + (size_t)((n_win + 1) & ~1u) * 4 + (size_t)n_win * 8;
+    // records staged and by window (4 + 4 bytes each), reserved bases, counts
+    // and offsets per window, warp sums, and the records' windows (2 + 2 bytes)
+    return (size_t)BK_TILE_RECORDS * 8 + (size_t)n_win * 16 + (BK_THREADS / 32) * 4 + (size_t)BK_TILE_RECORDS * 4;
 }
 
 uint32_t bucket_keys_per_thread(uint32_t R, uint32_t eta) {
@@ -155,10 +202,17 @@ cudaError_t launch_bucket_scatter(const IndexView& ix, const HashParams& hp, con
     }
     const uint64_t span = (uint64_t)kt * BK_THREADS;
     uint64_t blocks = (p_hi - p_lo + span - 1) / span;
-    const uint64_t most = (uint64_t)num_sms * 4;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, BK_THREADS, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const uint64_t most = (uint64_t)num_sms * per_sm;
     if (blocks > most) blocks = most;
-    k_bucket_scatter<<<(unsigned)blocks, BK_THREADS, smem, s>>>(ix, hp, b, p_lo, p_hi, kt, rows_per_win, n_win, cap,
-                                                                 rec, fill, overflow, st);
+    // window quotients by multiplication when every global row is below 2^32
+    const uint64_t rows_total = (uint64_t)ix.R * ix.m;
+    const uint64_t magic =
+        (rows_total <= (1ull << 32) && rows_per_win > 1) ? ~0ull / rows_per_win + 1 : 0ull;
+    k_bucket_scatter<<<(unsigned)blocks, BK_THREADS, smem, s>>>(ix, hp, b, p_lo, p_hi, kt, rows_per_win, magic, n_win,
+                                                                 cap, rec, fill, overflow, st);
     return cudaGetLastError();
 }
 

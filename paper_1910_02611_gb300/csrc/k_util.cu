@@ -550,9 +550,11 @@ cudaError_t launch_cluster_order(const BatchView& b, uint64_t* keys, uint32_t* h
 // ---------------------------------------------------------------------------
 // gather staged result IDs into CSR order: one warp per query.  A query
 // staged as its K-bit bitmap is expanded 32 words (up to 1024 IDs) at a
-// time: lanes write their word's set bits as IDs into the warp's run in
-// shared memory at their prefix position, then the warp stores the run with
-// coalesced writes.
+// time: every lane writes its word's set bits as IDs into the warp's run in
+// shared memory at its prefix position, then the warp stores the run with
+// coalesced writes.  The prefix of the lanes' bit counts (0..32, six bits)
+// comes from six ballots, one per bit of the count, instead of a chain of
+// shuffles.
 
 constexpr int GA_THREADS = 256;
 constexpr int GA_RUN = 1024;  // IDs of 32 bitmap words
@@ -565,6 +567,7 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(QueryOut o, const uint64_
     if (n_dev) n = *n_dev;
     if (id_offsets[n] > ids_cap) return;  // the caller sees the total and reports the shortfall
     const unsigned lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;  // lanes below this one
     uint32_t* run = s_run[threadIdx.x >> 5];
     uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -602,20 +605,27 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(QueryOut o, const uint64_
             cur = nx1;
             nx1 = nx2;
             const uint32_t cw = __popc(bits);
-            uint32_t incl = cw;
+            uint32_t pos = 0, blk = 0;
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
-                if (lane >= (unsigned)off) incl += y;
+            for (int k = 0; k < 6; ++k) {
+                const unsigned m = __ballot_sync(0xffffffffu, (cw >> k) & 1u);
+                pos += (uint32_t)__popc(m & lt) << k;
+                blk += (uint32_t)__popc(m) << k;
             }
-            const uint32_t blk = __shfl_sync(0xffffffffu, incl, 31);
-            uint32_t pos = incl - cw;
             while (bits) {
                 run[pos++] = w * 32 + (__ffs(bits) - 1);
                 bits &= bits - 1;
             }
             __syncwarp();
-            for (uint32_t t = lane; t < blk; t += 32) dst[at + t] = run[t];
+            uint32_t t = lane;
+            for (; t + 96 < blk; t += 128) {
+                const uint32_t a0 = run[t], a1 = run[t + 32], a2 = run[t + 64], a3 = run[t + 96];
+                dst[at + t] = a0;
+                dst[at + t + 32] = a1;
+                dst[at + t + 64] = a2;
+                dst[at + t + 96] = a3;
+            }
+            for (; t < blk; t += 32) dst[at + t] = run[t];
             __syncwarp();  // the run is rewritten by the next 32 words
             at += blk;
         }
@@ -625,7 +635,23 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(QueryOut o, const uint64_
 cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_t n, uint32_t* ids,
                           const DevStatus* st, cudaStream_t s, const uint64_t* n_dev, uint64_t ids_cap) {
     if (n == 0) return cudaSuccess;
-    int blocks = grid_for(n * 32, GA_THREADS, 152 * 16);
+    // one resident wave: every warp strides over the queries, so a few large
+    // answers do not leave later waves waiting on them
+    static int wave[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64 && !wave[dev]) {
+        int sms = 0, per_sm = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(&k_gather),
+                                                              GA_THREADS, 0);
+        if (e != cudaSuccess) return e;
+        wave[dev] = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int most = dev < 64 ? wave[dev] : 152 * 4;
+    int blocks = grid_for(n * 32, GA_THREADS, most);
     k_gather<<<blocks, GA_THREADS, 0, s>>>(o, id_offsets, n, ids, st, n_dev, ids_cap);
     return cudaGetLastError();
 }

@@ -147,31 +147,28 @@ __device__ __forceinline__ int base_code(unsigned ch) {
     return ok ? (int)(x ^ (x >> 1)) : -1;
 }
 
-// four ASCII bytes of a little-endian word -> four 2-bit codes; *bad gets the
-// lowest byte index (0..3) holding something other than ACGTacgt, or 4
-__device__ __forceinline__ uint32_t codes4(uint32_t w, int* bad) {
-    const uint32_t u = w | 0x20202020u;
-    const uint32_t x = (u >> 1) & 0x03030303u;
-    const uint32_t c = x ^ ((x >> 1) & 0x01010101u);  // a->0 c->1 g->2 t->3 per byte
-    *bad = 4;
-#pragma unroll
-    for (int t = 3; t >= 0; --t) {
-        const uint32_t ch = (u >> (8 * t)) & 0xffu;
-        if (!((ch == 'a') | (ch == 'c') | (ch == 'g') | (ch == 't'))) *bad = t;
-    }
-    return c;
+// four ASCII bytes of a little-endian word -> the 2-bit code of each in the
+// low bits of its byte (a->0 c->1 g->2 t->3; other bytes give some code)
+__device__ __forceinline__ uint32_t codes4x(uint32_t w) {
+    const uint32_t x = ((w | 0x20202020u) >> 1) & 0x03030303u;
+    return x ^ ((x >> 1) & 0x01010101u);
 }
 
-// bits t (0..3) set for the bytes of a little-endian word outside ACGTacgt
-__device__ __forceinline__ uint32_t unresolved4(uint32_t w) {
+// 0x80 in each byte of v that is zero, exactly (no borrow between bytes)
+__device__ __forceinline__ uint32_t zero_bytes(uint32_t v) {
+    return ~((((v & 0x7f7f7f7fu) + 0x7f7f7f7fu) | v)) & 0x80808080u;
+}
+
+// 0x80 in each byte of a little-endian word that is one of ACGTacgt
+__device__ __forceinline__ uint32_t acgt4(uint32_t w) {
     const uint32_t u = w | 0x20202020u;
-    uint32_t m = 0;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const uint32_t ch = (u >> (8 * t)) & 0xffu;
-        if (!((ch == 'a') | (ch == 'c') | (ch == 'g') | (ch == 't'))) m |= 1u << t;
-    }
-    return m;
+    return zero_bytes(u ^ 0x61616161u) | zero_bytes(u ^ 0x63636363u) | zero_bytes(u ^ 0x67676767u) |
+           zero_bytes(u ^ 0x74747474u);
+}
+
+// bytes flagged 0x80 (bits 7, 15, 23, 31) -> bits 0..3
+__device__ __forceinline__ uint32_t unresolved_nibble(uint32_t m) {
+    return (((m >> 7) * 0x00204081u) >> 21) & 0xfu;
 }
 
 // Packs words [w0, n_words) with stride.  With nmask (skip-N), bit t of
@@ -187,24 +184,22 @@ __device__ __forceinline__ void pack_words(const uint8_t* __restrict__ bases, ui
         unsigned long long bad = NO_ERR;
         uint32_t um = 0;  // unresolved bases of this word
         if (aligned && p0 + 32 <= total) {
-            // two 16-byte loads, four bases per 32-bit word
+            // two 16-byte loads, four bases per 32-bit word, each word
+            // handled as four bytes at once
             const uint4* q = reinterpret_cast<const uint4*>(bases + p0);
             const uint4 lo = __ldg(q), hi = __ldg(q + 1);
             const uint32_t wd[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                int b4;
-                const uint32_t c = codes4(wd[i], &b4);
-                if (b4 < 4) {
-                    if (nmask) um |= unresolved4(wd[i]) << (4 * i);
-                    else if (bad == NO_ERR) bad = p0 + 4 * i + b4;
+                const uint32_t ok = acgt4(wd[i]);              // 0x80 in every byte that is a base
+                const uint32_t badm = ~ok & 0x80808080u;       // 0x80 in every other byte
+                if (badm) {
+                    if (nmask) um |= unresolved_nibble(badm) << (4 * i);
+                    else if (bad == NO_ERR) bad = p0 + 4 * i + ((__ffs(badm) - 1) >> 3);
                 }
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    // an unresolved byte packs as 0 (its code bits are masked out)
-                    const uint32_t code = ((um >> (4 * i + t)) & 1u) ? 0u : ((c >> (8 * t)) & 3u);
-                    v |= (uint64_t)code << (62 - 2 * (4 * i + t));
-                }
+                const uint32_t c = codes4x(wd[i]) & ((ok >> 7) * 3u);  // an unresolved byte packs as 0
+                // the four 2-bit codes, first base highest, into one byte
+                v |= (uint64_t)((c * 0x40100401u) >> 24) << (56 - 8 * i);
             }
         } else {
             for (int t = 0; t < 32; ++t) {

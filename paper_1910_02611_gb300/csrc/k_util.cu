@@ -24,6 +24,7 @@ __global__ void k_status_reset(DevStatus* st) {
     st->rows_read = 0;
     st->spare[0] = st->spare[1] = 0;
     st->stage_count[0] = st->stage_count[1] = st->stage_count[2] = st->stage_count[3] = 0;
+    st->gather_ticket = 0;
 }
 
 cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s) {
@@ -543,19 +544,23 @@ cudaError_t launch_cluster_order(const BatchView& b, uint64_t* keys, uint32_t* h
 }
 
 // ---------------------------------------------------------------------------
-// gather staged result IDs into CSR order: one warp per query.  A query
-// staged as its K-bit bitmap is expanded 32 words (up to 1024 IDs) at a
+// gather staged result IDs into CSR order: one warp per query, warps taking
+// GA_TAKE queries at a time from a work queue (answers range from nothing to
+// the whole ID space, so a fixed share per warp would leave a long tail).  A
+// query staged as its K-bit bitmap is expanded 32 words (up to 1024 IDs) at a
 // time: every lane writes its word's set bits as IDs into the warp's run in
-// shared memory at its prefix position, then the warp stores the run with
-// coalesced writes.  The prefix of the lanes' bit counts (0..32, six bits)
+// shared memory at its prefix position (by bit scans, or for dense words by
+// testing every bit position), then the warp stores the run with coalesced
+// writes.  The prefix of the lanes' bit counts (0..32, six bits)
 // comes from six ballots, one per bit of the count, instead of a chain of
 // shuffles.
 
 constexpr int GA_THREADS = 256;
 constexpr int GA_RUN = 1024;  // IDs of 32 bitmap words
+constexpr unsigned GA_TAKE = 8;  // queries per work-queue ticket
 
 __global__ void __launch_bounds__(GA_THREADS) k_gather(QueryOut o, const uint64_t* __restrict__ id_offsets, uint64_t n,
-                                                        uint32_t* __restrict__ ids, const DevStatus* st,
+                                                        uint32_t* __restrict__ ids, DevStatus* st,
                                                         const uint64_t* __restrict__ n_dev, uint64_t ids_cap) {
     __shared__ uint32_t s_run[GA_THREADS / 32][GA_RUN];
     if (st->err != NO_ERR || st->cursor > o.stage_cap) return;
@@ -564,74 +569,88 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(QueryOut o, const uint64_
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;  // lanes below this one
     uint32_t* run = s_run[threadIdx.x >> 5];
-    uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t q = warp; q < n; q += nwarps) {
-        const uint32_t c = o.qcount[q];
-        if (!c) continue;
-        const uint64_t s0 = o.qstart[q];
-        uint32_t* dst = ids + id_offsets[q];
-        if (!(s0 & QSTART_BITMAP)) {
-            // an ID list: four independent loads in flight per lane
-            const uint32_t* src = o.stage + s0;
-            uint32_t t = lane;
-            for (; t + 96 < c; t += 128) {
-                const uint32_t a0 = __ldcs(src + t), a1 = __ldcs(src + t + 32);
-                const uint32_t a2 = __ldcs(src + t + 64), a3 = __ldcs(src + t + 96);
-                dst[t] = a0;
-                dst[t + 32] = a1;
-                dst[t + 64] = a2;
-                dst[t + 96] = a3;
+    for (;;) {
+        unsigned long long q0 = 0;
+        if (lane == 0) q0 = atomicAdd(&st->gather_ticket, (unsigned long long)GA_TAKE);
+        q0 = __shfl_sync(0xffffffffu, q0, 0);
+        if (q0 >= n) break;
+        const uint64_t q1 = min((unsigned long long)n, q0 + GA_TAKE);
+        for (uint64_t q = q0; q < q1; ++q) {
+            const uint32_t c = o.qcount[q];
+            if (!c) continue;
+            const uint64_t s0 = o.qstart[q];
+            uint32_t* dst = ids + id_offsets[q];
+            if (!(s0 & QSTART_BITMAP)) {
+                // an ID list: four independent loads in flight per lane
+                const uint32_t* src = o.stage + s0;
+                uint32_t t = lane;
+                for (; t + 96 < c; t += 128) {
+                    const uint32_t a0 = __ldcs(src + t), a1 = __ldcs(src + t + 32);
+                    const uint32_t a2 = __ldcs(src + t + 64), a3 = __ldcs(src + t + 96);
+                    dst[t] = a0;
+                    dst[t + 32] = a1;
+                    dst[t + 64] = a2;
+                    dst[t + 96] = a3;
+                }
+                for (; t < c; t += 32) dst[t] = __ldcs(src + t);
+                continue;
             }
-            for (; t < c; t += 32) dst[t] = __ldcs(src + t);
-            continue;
-        }
-        // a bitmap, 32 words at a time; the words of the next two steps are
-        // loaded ahead so their latency overlaps the expansion of this one
-        const uint32_t* src = o.stage + (s0 & ~QSTART_BITMAP);
-        const uint32_t bw = o.bits_words;
-        uint32_t cur = lane < bw ? __ldcs(src + lane) : 0u;
-        uint32_t nx1 = 32 + lane < bw ? __ldcs(src + 32 + lane) : 0u;
-        uint32_t at = 0;
-        for (uint32_t w0 = 0; w0 < bw; w0 += 32) {
-            const uint32_t w = w0 + lane;
-            const uint32_t nx2 = w + 64 < bw ? __ldcs(src + w + 64) : 0u;
-            uint32_t bits = cur;
-            cur = nx1;
-            nx1 = nx2;
-            const uint32_t cw = __popc(bits);
-            uint32_t pos = 0, blk = 0;
+            // a bitmap, 32 words at a time; the words of the next two steps are
+            // loaded ahead so their latency overlaps the expansion of this one
+            const uint32_t* src = o.stage + (s0 & ~QSTART_BITMAP);
+            const uint32_t bw = o.bits_words;
+            uint32_t cur = lane < bw ? __ldcs(src + lane) : 0u;
+            uint32_t nx1 = 32 + lane < bw ? __ldcs(src + 32 + lane) : 0u;
+            uint32_t at = 0;
+            for (uint32_t w0 = 0; w0 < bw; w0 += 32) {
+                const uint32_t w = w0 + lane;
+                const uint32_t nx2 = w + 64 < bw ? __ldcs(src + w + 64) : 0u;
+                uint32_t bits = cur;
+                cur = nx1;
+                nx1 = nx2;
+                const uint32_t cw = __popc(bits);
+                uint32_t pos = 0, blk = 0;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const unsigned m = __ballot_sync(0xffffffffu, (cw >> k) & 1u);
-                pos += (uint32_t)__popc(m & lt) << k;
-                blk += (uint32_t)__popc(m) << k;
+                for (int k = 0; k < 6; ++k) {
+                    const unsigned m = __ballot_sync(0xffffffffu, (cw >> k) & 1u);
+                    pos += (uint32_t)__popc(m & lt) << k;
+                    blk += (uint32_t)__popc(m) << k;
+                }
+                if (blk > GA_RUN / 2) {
+                    // dense words: every bit position in turn, no bit scans
+#pragma unroll
+                    for (int b = 0; b < 32; ++b) {
+                        const uint32_t on = (bits >> b) & 1u;
+                        if (on) run[pos] = w * 32 + b;
+                        pos += on;
+                    }
+                } else {
+                    while (bits) {
+                        run[pos++] = w * 32 + (__ffs(bits) - 1);
+                        bits &= bits - 1;
+                    }
+                }
+                __syncwarp();
+                uint32_t t = lane;
+                for (; t + 96 < blk; t += 128) {
+                    const uint32_t a0 = run[t], a1 = run[t + 32], a2 = run[t + 64], a3 = run[t + 96];
+                    dst[at + t] = a0;
+                    dst[at + t + 32] = a1;
+                    dst[at + t + 64] = a2;
+                    dst[at + t + 96] = a3;
+                }
+                for (; t < blk; t += 32) dst[at + t] = run[t];
+                __syncwarp();  // the run is rewritten by the next 32 words
+                at += blk;
             }
-            while (bits) {
-                run[pos++] = w * 32 + (__ffs(bits) - 1);
-                bits &= bits - 1;
-            }
-            __syncwarp();
-            uint32_t t = lane;
-            for (; t + 96 < blk; t += 128) {
-                const uint32_t a0 = run[t], a1 = run[t + 32], a2 = run[t + 64], a3 = run[t + 96];
-                dst[at + t] = a0;
-                dst[at + t + 32] = a1;
-                dst[at + t + 64] = a2;
-                dst[at + t + 96] = a3;
-            }
-            for (; t < blk; t += 32) dst[at + t] = run[t];
-            __syncwarp();  // the run is rewritten by the next 32 words
-            at += blk;
         }
     }
 }
 
 cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_t n, uint32_t* ids,
-                          const DevStatus* st, cudaStream_t s, const uint64_t* n_dev, uint64_t ids_cap) {
+                          DevStatus* st, cudaStream_t s, const uint64_t* n_dev, uint64_t ids_cap) {
     if (n == 0) return cudaSuccess;
-    // one resident wave: every warp strides over the queries, so a few large
-    // answers do not leave later waves waiting on them
+    // one resident wave of warps serving the work queue
     static int wave[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -692,7 +692,10 @@ int run_query_pipelined(rambo* h, BatchView b, const void* d_data, int seq, uint
         RK(resolve_tuning(h, nc, ub, t));
         QueryOut oc{h->stage.p, h->stage.cap, h->qstart.p + q_lo[c], h->qcount.p + q_lo[c], 0, 0};
         set_staging(oc, h->K, h->cfg.answer_staging);
-        if (c) CK(cudaMemsetAsync(&h->st->ticket, 0, sizeof(unsigned long long), s));  // a fresh work queue
+        if (c) {  // fresh work queues for the chunk's query and gather kernels
+            CK(cudaMemsetAsync(&h->st->ticket, 0, sizeof(unsigned long long), s));
+            CK(cudaMemsetAsync(&h->st->gather_ticket, 0, sizeof(unsigned long long), s));
+        }
         int nl = 0, n_scan = 0;
         CK(launch_query(h->view(), h->hp, bc, oc, t, ub, h->st, s, &nl));
         // chunk c's offsets continue from the total written by chunk c - 1's scan

@@ -41,6 +41,7 @@ struct DevStatus {
     unsigned long long rows_read;    // row reads issued
     unsigned long long spare[2];
     unsigned long long stage_count[4];   // surviving queries per set stage (1 dense, 2 sparse, 3 union)
+    unsigned long long gather_ticket;    // next queries handed out to a gather warp
 };
 
 // Position multipliers s_{r,j}, passed by value so every warp reads them from
@@ -356,7 +357,7 @@ cudaError_t launch_scan_counts(const uint32_t* counts, uint64_t n, uint64_t* off
                                unsigned long long* total_out = nullptr);
 uint64_t scan_tmp_words(uint64_t n);
 cudaError_t launch_gather(const QueryOut& o, const uint64_t* id_offsets, uint64_t n, uint32_t* ids,
-                          const DevStatus* st, cudaStream_t s, const uint64_t* n_dev = nullptr,
+                          DevStatus* st, cudaStream_t s, const uint64_t* n_dev = nullptr,
                           uint64_t ids_cap = ~0ull);
 // queries: validation and (bases != NULL) packing in one launch; n_words is
 // the packed capacity (a descriptor batch packs total/32 + 2 words of it)

@@ -467,7 +467,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, keys, probed, rows_read, qk_ms, launches, n_ids = [], 0, 0, 0, [], 0, 0
+    step_ms, keys, probed, rows_read, qk_ms, launches, n_ids, staged = [], 0, 0, 0, [], 0, 0, 0
     stages = [0, 0, 0, 0]  # surviving queries by set stage: staged dense, dense, sparse, union
     for i in range(args.steps):
         flush.zero_()
@@ -486,6 +486,7 @@ def run_ours(args):
         qk_ms.append(st["query_kernel_ms"])
         launches += st["kernel_launches"]
         n_ids += st["n_results"]
+        staged += st["staged_words"]
         stages = [a + b for a, b in zip(stages, st["stage_queries"])]
     torch.cuda.synchronize()
     if dist:
@@ -502,7 +503,7 @@ def run_ours(args):
         # on the same batches through direct calls, after the timed region
         qk_timing = ("direct calls of the same batches after the timed region (graph replayed without timing "
                      "nodes)")
-        qk_ms, probed, rows_read, n_ids = [], 0, 0, 0
+        qk_ms, probed, rows_read, n_ids, staged = [], 0, 0, 0, 0
         for i in range(args.steps):
             flush.zero_()
             one_step(i)
@@ -511,6 +512,7 @@ def run_ours(args):
             rows_read += st["rows_read"]
             qk_ms.append(st["query_kernel_ms"])
             n_ids += st["n_results"]
+            staged += st["staged_words"]
     total_ms = sum(step_ms)
 
     # ---- end to end through the same call with host buffers ----
@@ -577,7 +579,7 @@ def run_ours(args):
     row_bytes = g.row_stride * 4
     sectors_per_row = (row_bytes + SECTOR - 1) // SECTOR if row_bytes <= SECTOR else -(-row_bytes // SECTOR)
     # rows read (whole sectors) plus the 4-byte write of every result ID the kernel stages
-    alg_bytes = rows_read * sectors_per_row * SECTOR + n_ids * 4
+    alg_bytes = rows_read * sectors_per_row * SECTOR + staged * 4
     qk_total = sum(qk_ms)
     achieved = alg_bytes / (qk_total / 1000) / 1e9
     # random-row ceiling on a buffer the size of the index
@@ -656,7 +658,9 @@ def run_ours(args):
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(w.name),
             "kernel": "k_query", "peak_source": peaks["source"],
-            "bytes_model": f"rows read (device counter) x {sectors_per_row} sector(s) x 32 B + 4 B per result ID written",
+            "bytes_model": f"rows read (device counter) x {sectors_per_row} sector(s) x 32 B + 4 B per staged word "
+                           "(an ID of a list-staged answer or a word of a bitmap-staged one; device counter)",
+            "staged_words_per_step": staged / args.steps,
             "rows_read_per_step": rows_read / args.steps,
             "rows_per_submitted_key": rows_read / max(keys, 1),
             "query_kernel_ms_per_step": qk_total / args.steps,

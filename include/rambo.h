@@ -436,6 +436,8 @@ typedef struct rambo_query_stats {
     uint64_t stage_queries[4];  /* queries that reached the set stage, by stage used:
                                  * [0] staged dense (large ID space), [1] dense,
                                  * [2] sparse, [3] union */
+    uint64_t staged_words;      /* 32-bit words the query kernel wrote to the
+                                 * staging arena: ID lists and set bitmaps */
 } rambo_query_stats_t;
 
 int rambo_last_query_stats(const rambo_t *h, rambo_query_stats_t *out);

@@ -745,6 +745,7 @@ int run_query_pipelined(rambo* h, BatchView b, const void* d_data, int seq, uint
     h->last.rows_read = fin.rows_read;
     h->last.n_results = prev;
     for (int i = 0; i < 4; ++i) h->last.stage_queries[i] = fin.stage_count[i];
+    h->last.staged_words = fin.cursor;
     // (the chunks' query kernels, interleaved with their scans and gathers)
     CK(cudaEventElapsedTime(&h->last.query_kernel_ms, h->ev[1], h->ev[2]));
     CK(cudaEventElapsedTime(&h->last.device_ms, h->ev[0], h->ev[3]));
@@ -860,6 +861,7 @@ int run_query(rambo* h, int seq, const void* data, const uint64_t* offsets, uint
     h->last.rows_read = h->h_st->rows_read;
     h->last.n_results = total_ids;
     for (int i = 0; i < 4; ++i) h->last.stage_queries[i] = h->h_st->stage_count[i];
+    h->last.staged_words = h->h_st->cursor;
     CK(cudaEventElapsedTime(&h->last.query_kernel_ms, h->ev[1], h->ev[2]));
     if (d.needed) *d.needed = total_ids;
     if (!d.arena && total_ids > d.ids_cap) return RAMBO_ENOSPC;

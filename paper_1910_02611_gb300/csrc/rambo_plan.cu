@@ -370,6 +370,7 @@ int rambo_plan_wait(rambo_plan_t* p, int to_host, const uint32_t** ids, const ui
     p->last.n_results = total;
     p->last.kernel_launches = (uint64_t)p->launches_per_replay;
     for (int i = 0; i < 4; ++i) p->last.stage_queries[i] = st.stage_count[i];
+    p->last.staged_words = st.cursor;
     if (p->timed) {
         PK(cudaEventElapsedTime(&p->last.query_kernel_ms, p->ev_t[1], p->ev_t[2]));
         PK(cudaEventElapsedTime(&p->last.device_ms, p->ev_t[0], p->ev_t[3]));

@@ -29,7 +29,7 @@ class RamboInfo(C.Structure):
 class QueryStats(C.Structure):
     _fields_ = [("n_queries", _u64), ("keys_submitted", _u64), ("keys_probed", _u64), ("rows_read", _u64),
                 ("n_results", _u64), ("kernel_launches", _u64), ("query_kernel_ms", C.c_float),
-                ("device_ms", C.c_float), ("stage_queries", _u64 * 4)]
+                ("device_ms", C.c_float), ("stage_queries", _u64 * 4), ("staged_words", _u64)]
 
 
 class ServerConfig(C.Structure):

@@ -549,20 +549,20 @@ cudaError_t launch_cluster_order(const BatchView& b, uint64_t* keys, uint32_t* h
 // the whole ID space, so a fixed share per warp would leave a long tail).  A
 // query staged as its K-bit bitmap is expanded 32 words (up to 1024 IDs) at a
 // time: every lane writes its word's set bits as IDs into the warp's run in
-// shared memory at its prefix position (by bit scans, or for dense words by
-// testing every bit position), then the warp stores the run with coalesced
-// writes.  The prefix of the lanes' bit counts (0..32, six bits)
+// shared memory at its prefix position, then the warp stores the run with
+// coalesced writes (32 full words need no run: their IDs are consecutive).  The prefix of the lanes' bit counts (0..32, six bits)
 // comes from six ballots, one per bit of the count, instead of a chain of
 // shuffles.
 
 constexpr int GA_THREADS = 256;
 constexpr int GA_RUN = 1024;  // IDs of 32 bitmap words
+constexpr int GA_RUN_PAD = GA_RUN + GA_RUN / 32;  // the run with one pad word per 32
 constexpr unsigned GA_TAKE = 8;  // queries per work-queue ticket
 
 __global__ void __launch_bounds__(GA_THREADS) k_gather(QueryOut o, const uint64_t* __restrict__ id_offsets, uint64_t n,
                                                         uint32_t* __restrict__ ids, DevStatus* st,
                                                         const uint64_t* __restrict__ n_dev, uint64_t ids_cap) {
-    __shared__ uint32_t s_run[GA_THREADS / 32][GA_RUN];
+    __shared__ uint32_t s_run[GA_THREADS / 32][GA_RUN_PAD];
     if (st->err != NO_ERR || st->cursor > o.stage_cap) return;
     if (n_dev) n = *n_dev;
     if (id_offsets[n] > ids_cap) return;  // the caller sees the total and reports the shortfall
@@ -616,30 +616,40 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(QueryOut o, const uint64_
                     pos += (uint32_t)__popc(m & lt) << k;
                     blk += (uint32_t)__popc(m) << k;
                 }
+                if (blk == GA_RUN) {
+                    // 32 full words: the IDs are consecutive
+                    for (uint32_t t = lane; t < GA_RUN; t += 32) dst[at + t] = w0 * 32 + t;
+                    at += blk;
+                    continue;
+                }
+                // the run is padded by one word per 32 (entry p at p + p/32), so
+                // lanes whose words are full do not all write one bank
                 if (blk > GA_RUN / 2) {
                     // dense words: every bit position in turn, no bit scans
 #pragma unroll
                     for (int b = 0; b < 32; ++b) {
                         const uint32_t on = (bits >> b) & 1u;
-                        if (on) run[pos] = w * 32 + b;
+                        if (on) run[pos + (pos >> 5)] = w * 32 + b;
                         pos += on;
                     }
                 } else {
                     while (bits) {
-                        run[pos++] = w * 32 + (__ffs(bits) - 1);
+                        run[pos + (pos >> 5)] = w * 32 + (__ffs(bits) - 1);
+                        ++pos;
                         bits &= bits - 1;
                     }
                 }
                 __syncwarp();
                 uint32_t t = lane;
                 for (; t + 96 < blk; t += 128) {
-                    const uint32_t a0 = run[t], a1 = run[t + 32], a2 = run[t + 64], a3 = run[t + 96];
+                    const uint32_t a0 = run[t + (t >> 5)], a1 = run[t + 32 + ((t + 32) >> 5)];
+                    const uint32_t a2 = run[t + 64 + ((t + 64) >> 5)], a3 = run[t + 96 + ((t + 96) >> 5)];
                     dst[at + t] = a0;
                     dst[at + t + 32] = a1;
                     dst[at + t + 64] = a2;
                     dst[at + t + 96] = a3;
                 }
-                for (; t < blk; t += 32) dst[at + t] = run[t];
+                for (; t < blk; t += 32) dst[at + t] = run[t + (t >> 5)];
                 __syncwarp();  // the run is rewritten by the next 32 words
                 at += blk;
             }

@@ -519,8 +519,9 @@ int rambo_set_build_tiling(rambo_t *h, uint64_t tile_bytes, int mode);
 int rambo_list_query_configs(const rambo_t *h, rambo_query_config_t *out, int cap);
 
 /* Autotuner: times every query-kernel configuration the handle supports
- * (lanes per key, words per lane, warps per block, visiting order) on the
- * given sample batch (kind and pointers as in the query calls), `reps` runs
+ * (lanes per key, words per lane, warps per block, visiting order, and, when
+ * warps_per_query is 0 and the set stage keeps a shared-memory bitmap, also
+ * two warps per query) on the given sample batch (kind and pointers as in the query calls), `reps` runs
  * each, keeps the configuration with the smallest device time, stores it in
  * the handle and in *best.  Results never depend on the choice. */
 int rambo_autotune(rambo_t *h, int kind, const void *data, const uint64_t *offsets, uint64_t n_queries,

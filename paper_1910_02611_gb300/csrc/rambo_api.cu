@@ -1396,15 +1396,23 @@ int rambo_autotune(rambo_t* h, int kind, const void* data, const uint64_t* offse
     const rambo_query_config_t keep = h->cfg;
     rambo_query_config_t win = keep;
     float win_ms = -1.0f;
+    // with the group size left automatic, pairs of warps sharing one query
+    // (and its shared-memory bitmap) are tried too: on large ID spaces the
+    // per-warp bitmap limits the queries in flight (document workload: 86.7
+    // against 96.5 ms a batch)
+    const uint32_t wpq_try[2] = {keep.warps_per_query, 2};
+    const int n_wpq = (keep.warps_per_query == 0 && h->mem_off) ? 2 : 1;
     for (int c = 0; c < n; ++c) {
-        for (uint32_t order = 1; order <= 2; ++order) {
+        for (int iw = 0; iw < n_wpq * 2; ++iw) {
+            const uint32_t order = 1 + (uint32_t)(iw & 1);
             rambo_query_config_t cfg = cands[c];
             cfg.visit_order = order;
             cfg.set_stage = keep.set_stage;
             cfg.row_load = keep.row_load;
-            cfg.warps_per_query = keep.warps_per_query;
+            cfg.warps_per_query = wpq_try[iw >> 1];
             cfg.host_chunks = keep.host_chunks;
             cfg.answer_staging = keep.answer_staging;
+            if ((iw >> 1) && cfg.warps_per_block < 2) continue;
             if (rambo_set_query_config(h, &cfg) != RAMBO_OK) continue;
             float t_min = -1.0f;
             for (int r = 0; r < reps; ++r) {
